@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput of the extinction-mapping hot path on synthetic Gaia-like stars.
+
+One step = the whole hot path on one catalogue: assemble the sparse
+log-extinction covariance (neighbour search + sightline quadrature), run
+`--sweeps` parallel EP sweeps from zero sites (posterior mean by PCG,
+marginal variances by multi-RHS PCG, FP64 site updates), and compute the
+final posterior marginals.  Inputs stay resident in HBM; the metric is EP
+site updates per second (stars x sweeps / step time), with covariance pairs
+per second reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (its own
+catalogue seed); the path is not sharded, so there is no data-path
+collective.  `--impl reference` times the FP64 CPU oracle on host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "EP site updates/s + sparse-cov pairs/s, plain vs mixed/learned at same error"
+UNIT = "site updates/s"
+WORKLOAD = "c2_plain_20k"
+WORKLOAD_DESC = ("20,000 stars in a 5x5 deg field, distances log-uniform 100-3000 pc, "
+                 "64 Gauss-Legendre nodes per sightline, von Karman log-density GP "
+                 "(sigma2=1, L0=20 pc, 1 mag/kpc), cutoff 60 pc with Wendland taper, "
+                 "A_obs = A_true + N(0, 0.05^2), truth from a 2 pc spectral GP draw, seed 0")
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+# algorithmic flops per node-pair evaluation of the pair quadrature:
+# separation (3), cubic lookup (7), weighted accumulate (2) + inner sum (1)
+QUAD_FLOPS_PER_NODE_PAIR = 13
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--sweeps", type=int, default=3)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--n", type=int, default=None, help="override star count (testing)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_PATH))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- oracle
+def cpu_sample(cat, n_sub, sweeps, seed=0):
+    """The FP64 oracle, as it stands, on a random sub-catalogue: covariance
+    assembly + `sweeps` EP sweeps + final posterior.  Returns timings."""
+    import oracle as O
+    from synth import catalogue_subset
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(cat["s"]), n_sub, replace=False))
+    sub = catalogue_subset(cat, idx)
+    t0 = time.perf_counter()
+    cv = O.build_cov(sub)
+    t1 = time.perf_counter()
+    O.ep_run(cv["K"], cv["m"], sub["A_obs"], sub["A_sigma"], max_sweeps=sweeps, tol=0.0)
+    t2 = time.perf_counter()
+    return dict(n=n_sub, pairs=len(cv["pairs"]) + n_sub, t_cov=t1 - t0, t_ep=t2 - t1,
+                t=t2 - t0)
+
+
+def run_reference(a):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from synth import make_catalogue
+    cat = make_catalogue(WORKLOAD, n=a.n, truth="mean")
+    n_sub = 300
+    for _ in range(a.warmup):
+        cpu_sample(cat, n_sub, a.sweeps)
+    ts = [cpu_sample(cat, n_sub, a.sweeps, seed=k) for k in range(a.steps)]
+    t = sum(r["t"] for r in ts) / len(ts)
+    value = n_sub * a.sweeps / t
+    cores = os.cpu_count()
+    sample = (f"random {n_sub}-star subset of the {WORKLOAD} catalogue per step: dense FP64 "
+              f"covariance assembly + {a.sweeps} EP sweeps + posterior (numpy/scipy; BLAS "
+              f"threads = {cores}, per-star loops single-threaded)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_stars": n_sub, "sweeps_per_step": a.sweeps},
+           "pairs_per_s": sum(r["pairs"] for r in ts) / sum(r["t_cov"] for r in ts),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def roofline_for(name, launches, ms, st, cfg_prec, panel):
+    """Algorithmic work of one launch of the dominant kernel / its mean time."""
+    pk = peaks()
+    avg_s = ms / launches / 1e3
+    n, nnz, n_pairs = st["n_stars"], st["nnz"], st["n_pairs"]
+    vb = 4 if cfg_prec == "fp32" else 8
+    if name == "k_panel_spmm":
+        flops = 2.0 * nnz * panel
+        ach = flops / avg_s / 1e12
+        peak = FP32_PEAK_TFLOPS if cfg_prec == "fp32" else 1.25
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": name,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "work_per_launch": f"2 x nnz x panel = {flops:.3e} flop"}
+    if name == "k_pair_quad":
+        q = 64
+        flops = QUAD_FLOPS_PER_NODE_PAIR * q * q * n_pairs
+        ach = flops / avg_s / 1e12
+        peak = FP32_PEAK_TFLOPS
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": name,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "work_per_launch": f"13 flop x Q^2 x unique pairs = {flops:.3e} flop"}
+    # HBM-bound sparse kernels: matrix once + vectors
+    byt = nnz * (vb + 4) + (n + 1) * 8 + 3 * n * vb
+    ach = byt / avg_s / 1e9
+    peak = pk.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": None, "kernel": name,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if pk else "fallback",
+            "work_per_launch": f"{byt:.3e} B"}
+
+
+def run_gpu(a):
+    import torch
+
+    import paper_1708_09705_gb300 as gm
+    from synth import make_catalogue
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cat = make_catalogue(WORKLOAD, n=a.n, seed=rank)
+    n = len(cat["s"])
+    prec = gm.PREC_FP32 if a.precision == "fp32" else gm.PREC_FP64
+    cfg = gm.config_from_catalogue(cat, precision=prec,
+                                   cg_tol=1e-6 if a.precision == "fp32" else 1e-10)
+    D = {k: torch.tensor(cat[k], dtype=torch.float64, device=dev)
+         for k in ("l", "b", "s", "A_obs", "A_sigma")}
+    ctx = gm.ep_init(cfg, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"])
+    zeros = torch.zeros(n, dtype=torch.float64, device=dev)
+    mu = torch.empty(n, dtype=torch.float64, device=dev)
+    var = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        ctx.set_sites(zeros, zeros)
+        ctx.build_cov()
+        if ev is not None:
+            ev.record()
+        ctx.ep_sweep(a.sweeps, 0.0)
+        ctx.get_posterior(out=(mu, var))
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    clocks = ClockSampler(local) if rank == 0 else None
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    times, covt = [], []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        step(e1)
+        e2.record()
+        e2.synchronize()
+        times.append(e0.elapsed_time(e2))
+        covt.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    kt = ctx.kernel_times()
+    ctx.profile(False)
+    st = ctx.stats()
+    if ws > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop() if clocks else None
+    t_step = sum(times) / len(times) / 1e3
+    t_cov = sum(covt) / len(covt) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_step, t_cov], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step, t_cov = tt.tolist()
+    value = ws * n * a.sweeps / t_step
+    pairs_per_s = ws * st["n_pairs"] / t_cov
+
+    # dominant kernel and its roofline
+    dom = max(kt.items(), key=lambda kv: kv[1][1])
+    panel = cfg.rhs_panel or (math.ceil(n / 32) * 32)
+    roof = roofline_for(dom[0], dom[1][0], dom[1][1], st, a.precision, panel)
+    launches = int(sum(v[0] for v in kt.values()))
+    total_ms = sum(v[1] for v in kt.values())
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        H = {k: torch.tensor(cat[k], dtype=torch.float64).pin_memory()
+             for k in ("l", "b", "s", "A_obs", "A_sigma")}
+        hm = torch.empty(n, dtype=torch.float64).pin_memory()
+        hv = torch.empty(n, dtype=torch.float64).pin_memory()
+        ctx.close()
+        et = []
+        for k in range(max(1, a.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c2 = gm.ep_init(cfg, H["l"], H["b"], H["s"], H["A_obs"], H["A_sigma"])
+            c2.build_cov()
+            c2.ep_sweep(a.sweeps, 0.0)
+            c2.get_posterior(out=(hm, hv))
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+            c2.close()
+        te = sum(et) / len(et)
+        if ws > 1:
+            tt = torch.tensor([te], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = tt.item()
+        e2e = {"value": ws * n * a.sweeps / te, "unit": UNIT, "h2d_bytes_per_step": 5 * n * 8,
+               "d2h_bytes_per_step": 2 * n * 8, "ms_per_step": 1e3 * te,
+               "includes": "ep_init from pinned host arrays (H2D, spatial sort), build_cov, "
+                           "sweeps, posterior D2H"}
+    else:
+        ctx.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu:
+        r = cpu_sample(cat, 600, a.sweeps)
+        cpu = {"value": r["n"] * a.sweeps / r["t"], "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": (f"random 600-star subset of this catalogue: dense FP64 covariance "
+                          f"assembly ({r['t_cov']:.1f} s, {r['pairs'] / r['t_cov']:.3g} pairs/s) + "
+                          f"{a.sweeps} EP sweeps + posterior ({r['t_ep']:.1f} s); BLAS threads = "
+                          f"{os.cpu_count()}, per-star loops single-threaded")}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+               "warmup": a.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
+               "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "n_stars": n,
+                          "sweeps_per_step": a.sweeps, "nnz": st["nnz"],
+                          "unique_pairs": st["n_pairs"],
+                          "precision": ("FP32 quadrature, K values, SpMV and CG; FP64 sites, "
+                                        "moments and refined mean solve") if a.precision == "fp32"
+                          else "FP64 throughout",
+                          "cg_tol": cfg.cg_tol, "variance_panel": panel,
+                          "l2": "inputs (CSR + panels) larger than L2; 256 MiB write between steps",
+                          "parallelism": f"replicas x{ws}"},
+               "pairs_per_s": pairs_per_s, "cov_ms": 1e3 * t_cov,
+               "cg_iters": {"mean": st["cg_iters_mean"], "var_last_panels": st["cg_iters_var"]},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": ck,
+               "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in
+                              sorted(kt.items(), key=lambda kv: -kv[1][1])[:8]},
+               "kernel_ms_total": total_ms}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * gmead.h -- C ABI of libgmead, the GPU hot path of Gaussian-process 3-D
+ * extinction mapping with expectation propagation (Sale & Magorrian 2018,
+ * "Large-scale three-dimensional Gaussian process extinction mapping").
+ *
+ * The library computes, on one CUDA GPU (sm_103a):
+ *   - the sparse covariance K of the stars' log-extinctions a_i = ln A_i:
+ *     the covariance of the log-density integrated along both sightlines
+ *     (Sect. 3), for a log-density whose fluctuations follow a Kolmogorov
+ *     spectrum truncated at the outer scale (Sect. 1), evaluated by
+ *     Gauss-Legendre quadrature on each sightline, with pairs whose 3-D
+ *     separation exceeds a cutoff dropped (compactly supported taper);
+ *   - parallel expectation propagation with one Gaussian site per star
+ *     (App. A.2: cavity, tilted distribution, moment matching), whose
+ *     posterior marginals come from preconditioned conjugate-gradient
+ *     solves driven by sparse matrix products;
+ *   - the posterior predictive of a at query points (Sect. 2 eq. cond_GP0,
+ *     Sect. 3.1 eq. map_dist).
+ *
+ * Conventions for every call:
+ *   - Angles in radians, distances in pc, extinctions in mag.  Returned
+ *     moments are those of the natural log of the extinction.
+ *   - Array arguments may be host or device pointers; the library detects
+ *     which with cudaPointerGetAttributes.  Inputs are copied: the caller
+ *     keeps ownership and may free them when the call returns.  Outputs go to
+ *     caller-allocated arrays of the stated length.
+ *   - Arrays are indexed in the caller's star order.  Internally the stars
+ *     are renumbered by a spatial sort; gm_get_perm exposes that order.
+ *   - Every call returns a gm_status; no C++ exception crosses the ABI.  A
+ *     human-readable detail of the last failure is kept per context
+ *     (gm_last_error).  Kernels never trap: they raise status flags that the
+ *     host reads.
+ *   - All work is issued on the context's stream.  Calls that return host
+ *     data synchronise that stream.  A context must not be used from two
+ *     threads at once.
+ */
+#ifndef GMEAD_H
+#define GMEAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gm_ctx gm_ctx;
+
+typedef enum {
+  GM_OK = 0,
+  GM_E_INVAL = 1,      /* bad argument (null pointer, size, config value)   */
+  GM_E_NOMEM = 2,      /* device allocation failed                          */
+  GM_E_CUDA = 3,       /* CUDA runtime error (detail in gm_last_error)      */
+  GM_E_NOT_SPD = 4,    /* CG met p^T B p <= 0: the covariance is not PD     */
+  GM_E_NOCONV = 5,     /* CG hit its iteration cap above tolerance          */
+  GM_E_NONFINITE = 6,  /* a NaN or Inf appeared in K, the solves or sites   */
+  GM_E_TIMEOUT = 7,    /* a bounded device wait gave up                     */
+  GM_E_STATE = 8       /* call out of order (e.g. sweep before build_cov)   */
+} gm_status;
+
+/* Arithmetic of the covariance values, quadrature and CG inner iterations.
+ * Site updates and the moments they use are always FP64. */
+enum { GM_PREC_FP64 = 0, GM_PREC_FP32 = 1 };
+/* Log-extinction moments from the density moments: lognormal moment match
+ * (K = log1p(I/(s_i s_j)), m = ln(rho_bar s) - K_ii/2) or first order. */
+enum { GM_FORM_LOGNORMAL = 0, GM_FORM_LINEAR = 1 };
+/* Sparsification: Wendland psi_{3,1} taper (keeps K positive definite) or a
+ * hard cutoff (literal dropping; may be indefinite -> GM_E_NOT_SPD). */
+enum { GM_TAPER_WENDLAND = 0, GM_TAPER_HARD = 1 };
+/* Per-star likelihood: A_obs ~ N(exp(a), sigma^2) or a_obs ~ N(a, sigma^2). */
+enum { GM_LIK_GAUSS_IN_A = 0, GM_LIK_GAUSS_IN_LNA = 1 };
+
+typedef struct {
+  double sigma2;          /* variance of the log-density GP (> 0)             */
+  double outer_scale_pc;  /* outer (injection) scale L0; k0 = 1/L0 (> 0)      */
+  double rho_bar;         /* mean extinction per pc, E[exp f] (> 0)           */
+  double cutoff_pc;       /* pairs farther apart in 3-D are dropped (> 0)     */
+  int32_t n_nodes;        /* Gauss-Legendre nodes per sightline, 2..128       */
+  int32_t form;           /* GM_FORM_*                                        */
+  int32_t taper;          /* GM_TAPER_*                                       */
+  int32_t precision;      /* GM_PREC_*                                        */
+  int32_t likelihood;     /* GM_LIK_*                                         */
+  int32_t cg_max_iter;    /* cap on CG iterations per solve (> 0)             */
+  double damping;         /* EP damping eta in (0, 1]                         */
+  double vc_floor;        /* floor on the cavity variance (>= 0)              */
+  double cg_tol;          /* CG stops at ||r|| <= cg_tol ||b|| (> 0); FP32
+                             variance panels use max(cg_tol, 1e-5)            */
+  int32_t rhs_panel;      /* right-hand sides per variance panel, 0 = auto    */
+  int32_t reserved;
+} gm_config;
+
+/* Device memory hooks.  When given, every device allocation of the context
+ * goes through alloc/free (e.g. a framework's caching allocator); when NULL,
+ * the library uses cudaMallocAsync/cudaFreeAsync on the context stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} gm_allocator;
+
+/* Counters of the last gm_build_cov / gm_ep_sweep / posterior refresh. */
+typedef struct {
+  int64_t n_stars;
+  int64_t nnz;             /* stored entries of K (both triangles + diagonal) */
+  int64_t n_pairs;         /* unique pairs integrated (i <= j)                */
+  int64_t cg_iters_mean;   /* CG iterations of the last posterior-mean solve  */
+  int64_t cg_iters_var;    /* CG iterations summed over variance panels       */
+  int64_t sites_skipped;   /* site updates skipped in the last sweep          */
+  int64_t kernel_launches; /* kernels launched by the last API call           */
+  double last_max_delta;   /* largest relative site change of the last sweep  */
+  double cg_resid_mean;    /* final relative residual of the mean solve       */
+  double cg_resid_var;     /* largest final relative residual of a variance   */
+} gm_stats;
+
+/* Fills *cfg with defaults: sigma2 1, L0 20 pc, rho_bar 1e-3 mag/pc, cutoff
+ * 3 L0, 32 nodes, lognormal form, Wendland taper, FP64, Gaussian-in-A
+ * likelihood, damping 1, cavity floor 1e-8, CG tol 1e-10 / 2000 iterations. */
+void gm_config_default(gm_config* cfg);
+
+/* Creates a context for n >= 1 stars (Sect. 3: observed (l, b), distance s
+ * known, one extinction observation per star, Sect. 4.1 eq. like_factor).
+ *   l, b        : Galactic coordinates, radians, length n
+ *   s           : distances, pc, > 0, length n
+ *   obs         : A_obs (mag) for GM_LIK_GAUSS_IN_A, or ln A_obs for
+ *                 GM_LIK_GAUSS_IN_LNA, length n
+ *   obs_sigma   : noise standard deviation of obs, > 0, length n
+ *   stream      : cudaStream_t to issue work on (NULL = legacy default)
+ *   alloc       : device-memory hooks or NULL
+ * Sites start at zero (posterior = prior).  Errors: GM_E_INVAL on bad sizes,
+ * pointers, non-finite or out-of-range values; GM_E_NOMEM; GM_E_CUDA. */
+gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n,
+                     const double* l, const double* b, const double* s,
+                     const double* obs, const double* obs_sigma, void* stream,
+                     const gm_allocator* alloc);
+
+/* Assembles K (CSR over the internal order, both triangles, rows sorted) and
+ * the prior mean m (Sect. 3): neighbour search within cutoff_pc, sightline
+ * double quadrature per unique pair, log1p and taper.  Writes the number of
+ * stored entries to *nnz_out (may be NULL).  Must precede gm_ep_sweep and
+ * gm_predict.  Reads one scalar back to size the CSR (one stream sync). */
+gm_status gm_build_cov(gm_ctx* ctx, int64_t* nnz_out);
+
+/* Runs n_sweeps parallel EP iterations (App. A.2), stopping early when the
+ * largest relative site change is below tol (tol <= 0: never early).  Each
+ * sweep: posterior mean by PCG on B = I + S^1/2 K S^1/2, marginal variances
+ * by multi-RHS PCG, then FP64 cavity / tilted / moment-matched site update
+ * for every star.  Outputs (may be NULL): sweeps done, last max change.
+ * Errors: GM_E_STATE (no K), GM_E_NOT_SPD, GM_E_NOCONV, GM_E_NONFINITE. */
+gm_status gm_ep_sweep(gm_ctx* ctx, int32_t n_sweeps, double tol,
+                      int32_t* sweeps_done, double* max_delta);
+
+/* Posterior predictive mean and variance of ln A at nq query points
+ * (l, b in radians, s in pc; Sect. 2 eq. cond_GP0 with the sites as
+ * observations).  Cross-covariances use the same quadrature, cutoff and
+ * taper as K.  mean_out, var_out: length nq, host or device. */
+gm_status gm_predict(gm_ctx* ctx, int64_t nq, const double* l, const double* b,
+                     const double* s, double* mean_out, double* var_out);
+
+/* Marginal posterior mean and variance of ln A for every star under the
+ * current sites (refreshed if the sites changed).  Length n each. */
+gm_status gm_get_posterior(gm_ctx* ctx, double* mean_out, double* var_out);
+
+/* Site natural parameters (tau, nu): site_i(a) = exp(-tau a^2/2 + nu a).
+ * gm_set_sites restores a saved state (tau >= 0, finite). Length n each. */
+gm_status gm_get_sites(gm_ctx* ctx, double* tau_out, double* nu_out);
+gm_status gm_set_sites(gm_ctx* ctx, const double* tau, const double* nu);
+
+/* Prior mean m and diagonal K_ii (length n, caller order). */
+gm_status gm_get_prior(gm_ctx* ctx, double* mean_out, double* kdiag_out);
+
+/* Internal star order: perm[k] = caller index of internal star k (length n). */
+gm_status gm_get_perm(gm_ctx* ctx, int64_t* perm_out);
+
+/* K in CSR over the internal order: row_ptr (n+1), col (nnz, int32),
+ * val (nnz, FP64, converted from the stored precision). */
+gm_status gm_get_csr(gm_ctx* ctx, int64_t* row_ptr_out, int32_t* col_out,
+                     double* val_out);
+
+gm_status gm_get_stats(gm_ctx* ctx, gm_stats* out);
+
+/* The context's cudaStream_t. */
+void* gm_stream(gm_ctx* ctx);
+
+/* Per-kernel timing.  gm_profile(ctx, 1) makes every later launch record a
+ * CUDA event pair on the context stream; totals per kernel name accumulate
+ * until gm_profile(ctx, 0), which also clears them.  gm_kernel_time_count
+ * returns the number of distinct kernels timed so far; gm_kernel_time
+ * returns the k-th one's name (static string), launch count and summed
+ * device time in ms.  Timing adds two event records per launch. */
+gm_status gm_profile(gm_ctx* ctx, int32_t enable);
+int32_t gm_kernel_time_count(gm_ctx* ctx);
+gm_status gm_kernel_time(gm_ctx* ctx, int32_t k, const char** name, int64_t* launches,
+                         double* total_ms);
+
+const char* gm_status_str(gm_status s);
+const char* gm_last_error(gm_ctx* ctx);
+void gm_destroy(gm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GMEAD_H */

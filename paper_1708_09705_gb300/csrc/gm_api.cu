@@ -1,0 +1,655 @@
+// C ABI of libgmead (declared in include/gmead.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+gm_status set_error(gm_ctx* c, gm_status st, const std::string& msg) {
+  if (c) c->last_error = std::string(gm_status_str(st)) + ": " + msg;
+  return st;
+}
+
+gm_status cuda_fail(gm_ctx* c, cudaError_t e, const char* what) {
+  if (c) c->last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GM_E_NOMEM : GM_E_CUDA;
+}
+
+void* dev_alloc(gm_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->has_alloc) {
+    p = c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->owned.push_back(Buffer{p, bytes});
+  return p;
+}
+
+static void raw_free(gm_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  if (c->has_alloc)
+    c->alloc.free(p, bytes, (void*)c->stream, c->alloc.user);
+  else
+    cudaFreeAsync(p, c->stream);
+}
+
+void dev_free_now(gm_ctx* c, void* p, size_t bytes) {
+  for (size_t k = 0; k < c->owned.size(); ++k) {
+    if (c->owned[k].p == p) {
+      c->owned.erase(c->owned.begin() + k);
+      break;
+    }
+  }
+  raw_free(c, p, bytes);
+}
+
+bool ensure(gm_ctx* c, Buffer& b, size_t bytes) {
+  if (b.p && b.bytes >= bytes) return true;
+  if (b.p) dev_free_now(c, b.p, b.bytes);
+  b.p = dev_alloc(c, bytes);
+  b.bytes = b.p ? bytes : 0;
+  return b.p != nullptr;
+}
+
+// ---------------------------------------------------------------- timing
+static cudaEvent_t prof_event(gm_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void prof_begin(gm_ctx* c, const char* name) {
+  cudaEvent_t a = prof_event(c), b = prof_event(c);
+  if (!a || !b) return;
+  cudaEventRecord(a, c->stream);
+  c->prof_recs.push_back({name, a, b});
+  c->prof_pending = name;
+}
+
+void prof_end(gm_ctx* c) {
+  if (!c->prof_recs.empty()) cudaEventRecord(c->prof_recs.back().b, c->stream);
+  c->prof_pending = nullptr;
+}
+
+void prof_collect(gm_ctx* c) {
+  if (c->prof_recs.empty()) return;
+  cudaEventSynchronize(c->prof_recs.back().b);
+  for (auto& r : c->prof_recs) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0;
+    }
+    bool found = false;
+    for (auto& acc : c->prof_acc)
+      if (std::strcmp(acc.name, r.name) == 0) {
+        acc.launches++;
+        acc.ms += ms;
+        found = true;
+        break;
+      }
+    if (!found) c->prof_acc.push_back({r.name, 1, (double)ms});
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_recs.clear();
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Copies n doubles from a host or device pointer into device memory.
+static gm_status copy_in(gm_ctx* c, double* dst, const void* src, size_t bytes) {
+  cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+  return GM_OK;
+}
+
+// Copies device data out to a host or device pointer and waits.
+static gm_status copy_out(gm_ctx* c, void* dst, const void* src, size_t bytes) {
+  cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(dst, src, bytes, k, c->stream));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  return GM_OK;
+}
+
+static gm_status read_flags(gm_ctx* c) {
+  unsigned* h = (unsigned*)c->h_pinned;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                   c->stream));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  unsigned f = *h;
+  if (f) GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream));
+  if (f & kFlagNonFinite) return set_error(c, GM_E_NONFINITE, "non-finite value in a kernel");
+  if (f & kFlagNotSPD)
+    return set_error(c, GM_E_NOT_SPD, "CG found p^T B p <= 0: covariance not positive definite");
+  if (f & kFlagTimeout) return set_error(c, GM_E_TIMEOUT, "bounded device wait expired");
+  return GM_OK;
+}
+
+// element-wise kernels for the API layer
+__global__ void k_scatter_ext(int64_t n, const int64_t* __restrict__ perm,
+                              const double* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[k]] = src[k];
+}
+
+__global__ void k_gather_ext(int64_t n, const int64_t* __restrict__ perm,
+                             const double* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src[perm[k]];
+}
+
+__global__ void k_check_inputs(int64_t n, const double* __restrict__ s,
+                               const double* __restrict__ obs, const double* __restrict__ sig,
+                               const double* __restrict__ l, const double* __restrict__ b,
+                               unsigned* __restrict__ bad) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    bool ok = isfinite(s[k]) && s[k] > 0 && isfinite(obs[k]) && isfinite(sig[k]) && sig[k] > 0 &&
+              isfinite(l[k]) && isfinite(b[k]);
+    if (!ok) atomicOr(bad, 1u);
+  }
+}
+
+__global__ void k_check_sites(int64_t n, const double* __restrict__ tau,
+                              const double* __restrict__ nu, unsigned* __restrict__ bad) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    if (!(isfinite(tau[k]) && tau[k] >= 0 && isfinite(nu[k]))) atomicOr(bad, 1u);
+}
+
+template <typename T>
+__global__ void k_to_double(int64_t n, const T* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = (double)src[k];
+}
+
+__global__ void k_query_mean(int64_t n, double log_rho_bar, int form, double sigma2,
+                             const double* __restrict__ s, const double* __restrict__ kss,
+                             double* __restrict__ m) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    m[k] = log_rho_bar + log(s[k]) - (form == GM_FORM_LOGNORMAL ? 0.5 * kss[k] : 0.5 * sigma2);
+}
+
+static int eb(gm_ctx* c, int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * sm_count(c)));
+}
+
+static gm_status validate(const gm_config* f) {
+  if (!(f->sigma2 > 0) || !(f->outer_scale_pc > 0) || !(f->rho_bar > 0) || !(f->cutoff_pc > 0))
+    return GM_E_INVAL;
+  if (!std::isfinite(f->sigma2) || !std::isfinite(f->outer_scale_pc) ||
+      !std::isfinite(f->rho_bar) || !std::isfinite(f->cutoff_pc))
+    return GM_E_INVAL;
+  if (f->n_nodes < 2 || f->n_nodes > kMaxNodes) return GM_E_INVAL;
+  if (f->form != GM_FORM_LOGNORMAL && f->form != GM_FORM_LINEAR) return GM_E_INVAL;
+  if (f->taper != GM_TAPER_WENDLAND && f->taper != GM_TAPER_HARD) return GM_E_INVAL;
+  if (f->precision != GM_PREC_FP64 && f->precision != GM_PREC_FP32) return GM_E_INVAL;
+  if (f->likelihood != GM_LIK_GAUSS_IN_A && f->likelihood != GM_LIK_GAUSS_IN_LNA)
+    return GM_E_INVAL;
+  if (!(f->damping > 0 && f->damping <= 1)) return GM_E_INVAL;
+  if (!(f->vc_floor >= 0) || !(f->cg_tol > 0) || f->cg_max_iter <= 0) return GM_E_INVAL;
+  if (f->rhs_panel < 0) return GM_E_INVAL;
+  return GM_OK;
+}
+
+}  // namespace gm
+
+using namespace gm;
+
+extern "C" {
+
+void gm_config_default(gm_config* f) {
+  if (!f) return;
+  std::memset(f, 0, sizeof(*f));
+  f->sigma2 = 1.0;
+  f->outer_scale_pc = 20.0;
+  f->rho_bar = 1e-3;
+  f->cutoff_pc = 60.0;
+  f->n_nodes = 32;
+  f->form = GM_FORM_LOGNORMAL;
+  f->taper = GM_TAPER_WENDLAND;
+  f->precision = GM_PREC_FP64;
+  f->likelihood = GM_LIK_GAUSS_IN_A;
+  f->cg_max_iter = 2000;
+  f->damping = 1.0;
+  f->vc_floor = 1e-8;
+  f->cg_tol = 1e-10;
+  f->rhs_panel = 0;
+}
+
+const char* gm_status_str(gm_status s) {
+  switch (s) {
+    case GM_OK: return "GM_OK";
+    case GM_E_INVAL: return "GM_E_INVAL";
+    case GM_E_NOMEM: return "GM_E_NOMEM";
+    case GM_E_CUDA: return "GM_E_CUDA";
+    case GM_E_NOT_SPD: return "GM_E_NOT_SPD";
+    case GM_E_NOCONV: return "GM_E_NOCONV";
+    case GM_E_NONFINITE: return "GM_E_NONFINITE";
+    case GM_E_TIMEOUT: return "GM_E_TIMEOUT";
+    case GM_E_STATE: return "GM_E_STATE";
+  }
+  return "GM_E_UNKNOWN";
+}
+
+const char* gm_last_error(gm_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+void* gm_stream(gm_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n, const double* l,
+                     const double* b, const double* s, const double* obs,
+                     const double* obs_sigma, void* stream, const gm_allocator* alloc) {
+  if (!out || !cfg) return GM_E_INVAL;
+  *out = nullptr;
+  if (n < 1 || n >= (1ll << 31) || !l || !b || !s || !obs || !obs_sigma) return GM_E_INVAL;
+  if (validate(cfg) != GM_OK) return GM_E_INVAL;
+  if (alloc && (!alloc->alloc || !alloc->free)) return GM_E_INVAL;
+  gm_ctx* c = new (std::nothrow) gm_ctx();
+  if (!c) return GM_E_NOMEM;
+  c->cfg = *cfg;
+  c->n = n;
+  c->stream = (cudaStream_t)stream;
+  if (alloc) {
+    c->alloc = *alloc;
+    c->has_alloc = true;
+  }
+  c->stats.n_stars = n;
+  gm_status st = GM_OK;
+  auto fail = [&](gm_status e) {
+    *out = c;  // keep the context so that the caller can read gm_last_error
+    return e;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(cuda_fail(c, cudaGetLastError(), "cudaGetDevice"));
+  if (cudaMallocHost(&c->h_pinned, 1 << 16) != cudaSuccess)
+    return fail(cuda_fail(c, cudaGetLastError(), "cudaMallocHost"));
+  const size_t nb = (size_t)n * sizeof(double);
+  c->perm = (int64_t*)dev_alloc(c, (size_t)n * sizeof(int64_t));
+  for (double** p : {&c->s, &c->ux, &c->uy, &c->uz, &c->obs, &c->obs_sigma, &c->tau, &c->nu,
+                     &c->mu, &c->var, &c->alpha, &c->kdiag, &c->prior_m})
+    *p = (double*)dev_alloc(c, nb);
+  c->row_ptr = (int64_t*)dev_alloc(c, (size_t)(n + 1) * sizeof(int64_t));
+  c->diag_pos = (int64_t*)dev_alloc(c, (size_t)n * sizeof(int64_t));
+  c->d_flags = (unsigned*)dev_alloc(c, 16);
+  c->gl_zeta = (double*)dev_alloc(c, kMaxNodes * sizeof(double));
+  c->gl_w = (double*)dev_alloc(c, kMaxNodes * sizeof(double));
+  c->gh_x = (double*)dev_alloc(c, kGH * sizeof(double));
+  c->gh_wx = (double*)dev_alloc(c, kGH * sizeof(double));
+  for (void* p : {(void*)c->perm, (void*)c->s, (void*)c->tau, (void*)c->prior_m, (void*)c->row_ptr,
+                  (void*)c->diag_pos, (void*)c->d_flags, (void*)c->gl_zeta, (void*)c->gh_wx,
+                  (void*)c->ux, (void*)c->uy, (void*)c->uz, (void*)c->obs, (void*)c->obs_sigma,
+                  (void*)c->nu, (void*)c->mu, (void*)c->var, (void*)c->alpha, (void*)c->kdiag,
+                  (void*)c->gl_w, (void*)c->gh_x})
+    if (!p) return fail(set_error(c, GM_E_NOMEM, "context arrays"));
+  if (cudaMemsetAsync(c->d_flags, 0, 16, c->stream) != cudaSuccess)
+    return fail(cuda_fail(c, cudaGetLastError(), "memset"));
+  // quadrature rules
+  {
+    std::vector<double> x(c->cfg.n_nodes), w(c->cfg.n_nodes), z(c->cfg.n_nodes), v(c->cfg.n_nodes);
+    gauss_legendre(c->cfg.n_nodes, x.data(), w.data());
+    for (int q = 0; q < c->cfg.n_nodes; ++q) {
+      z[q] = 0.5 * (1.0 + x[q]);
+      v[q] = 0.5 * w[q];
+    }
+    std::vector<double> hx(kGH), hw(kGH);
+    gauss_hermite(kGH, hx.data(), hw.data());
+    double* hp = (double*)c->h_pinned;
+    std::memcpy(hp, z.data(), z.size() * sizeof(double));
+    std::memcpy(hp + 128, v.data(), v.size() * sizeof(double));
+    std::memcpy(hp + 256, hx.data(), kGH * sizeof(double));
+    std::memcpy(hp + 384, hw.data(), kGH * sizeof(double));
+    cudaMemcpyAsync(c->gl_zeta, hp, z.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->gl_w, hp + 128, v.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->gh_x, hp + 256, kGH * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->gh_wx, hp + 384, kGH * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return fail(cuda_fail(c, cudaGetLastError(), "rule upload"));
+  }
+  // inputs (caller order) -> device scratch
+  double* in[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  const double* src[5] = {l, b, s, obs, obs_sigma};
+  for (int k = 0; k < 5; ++k) {
+    in[k] = (double*)dev_alloc(c, nb);
+    if (!in[k]) return fail(set_error(c, GM_E_NOMEM, "input staging"));
+    st = copy_in(c, in[k], src[k], nb);
+    if (st != GM_OK) return fail(st);
+  }
+  GM_PROF(c, "k_check_inputs");
+  k_check_inputs<<<eb(c, n), 256, 0, c->stream>>>(n, in[2], in[3], in[4], in[0], in[1], c->d_flags);
+  {
+    unsigned* h = (unsigned*)c->h_pinned;
+    cudaMemcpyAsync(h, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return fail(cuda_fail(c, cudaGetLastError(), "input check"));
+    if (*h) return fail(set_error(c, GM_E_INVAL, "non-finite input, s <= 0 or obs_sigma <= 0"));
+  }
+  st = geometry_init(c, in[0], in[1], in[2], in[3], in[4]);
+  if (st != GM_OK) return fail(st);
+  for (int k = 4; k >= 0; --k) dev_free_now(c, in[k], nb);
+  st = phi_points_init(c);
+  if (st != GM_OK) return fail(st);
+  cudaMemsetAsync(c->tau, 0, nb, c->stream);
+  cudaMemsetAsync(c->nu, 0, nb, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return fail(cuda_fail(c, cudaGetLastError(), "init"));
+  *out = c;
+  return GM_OK;
+}
+
+gm_status gm_build_cov(gm_ctx* c, int64_t* nnz_out) {
+  if (!c) return GM_E_INVAL;
+  c->launches = 0;
+  gm_status st = neighbour_csr(c, c->n, c->s, c->ux, c->uy, c->uz, true, c->row_ptr, c->col_buf,
+                               &c->nnz, c->diag_pos);
+  if (st != GM_OK) return st;
+  c->col = (int32_t*)c->col_buf.p;
+  const size_t vs = c->cfg.precision == GM_PREC_FP32 ? sizeof(float) : sizeof(double);
+  if (!ensure(c, c->val_buf, std::max<int64_t>(c->nnz, 1) * vs))
+    return set_error(c, GM_E_NOMEM, "CSR values");
+  c->val = c->val_buf.p;
+  st = pair_quadrature(c, c->n, c->s, c->ux, c->uy, c->uz, c->row_ptr, c->col, c->nnz, c->val, true);
+  if (st != GM_OK) return st;
+  st = read_flags(c);
+  if (st != GM_OK) return st;
+  prof_collect(c);
+  c->built = true;
+  c->post_valid = false;
+  c->stats.nnz = c->nnz;
+  c->stats.n_pairs = (c->nnz + c->n) / 2;
+  c->stats.kernel_launches = c->launches;
+  if (nnz_out) *nnz_out = c->nnz;
+  return GM_OK;
+}
+
+gm_status gm_ep_sweep(gm_ctx* c, int32_t n_sweeps, double tol, int32_t* sweeps_done,
+                      double* max_delta) {
+  if (!c || n_sweeps < 0) return GM_E_INVAL;
+  if (!c->built) return set_error(c, GM_E_STATE, "gm_build_cov must precede gm_ep_sweep");
+  c->launches = 0;
+  int done = 0;
+  double delta = 0;
+  for (; done < n_sweeps;) {
+    gm_status st = GM_OK;
+    if (!c->post_valid) {
+      st = refresh_posterior(c);
+      if (st == GM_OK) st = read_flags(c);
+      if (st != GM_OK) return st;
+    }
+    int64_t skipped = 0;
+    st = site_update(c, &delta, &skipped);
+    if (st == GM_OK) st = read_flags(c);
+    if (st != GM_OK) return st;
+    prof_collect(c);
+    c->post_valid = false;
+    c->stats.sites_skipped = skipped;
+    c->stats.last_max_delta = delta;
+    ++done;
+    if (tol > 0 && delta < tol) break;
+  }
+  c->stats.kernel_launches = c->launches;
+  if (sweeps_done) *sweeps_done = done;
+  if (max_delta) *max_delta = delta;
+  return GM_OK;
+}
+
+static gm_status ensure_posterior(gm_ctx* c) {
+  if (!c->built) return set_error(c, GM_E_STATE, "gm_build_cov must come first");
+  if (c->post_valid) return GM_OK;
+  gm_status st = refresh_posterior(c);
+  if (st == GM_OK) st = read_flags(c);
+  return st;
+}
+
+gm_status gm_get_posterior(gm_ctx* c, double* mean_out, double* var_out) {
+  if (!c) return GM_E_INVAL;
+  c->launches = 0;
+  gm_status st = ensure_posterior(c);
+  if (st != GM_OK) return st;
+  double* tmp = (double*)dev_alloc(c, 2 * c->n * sizeof(double));
+  if (!tmp) return set_error(c, GM_E_NOMEM, "posterior staging");
+  GM_PROF(c, "k_scatter_ext");
+  k_scatter_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->mu, tmp);
+  GM_PROF(c, "k_scatter_ext");
+  k_scatter_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->var, tmp + c->n);
+  GM_LAUNCH_CHECK(c);
+  if (mean_out && (st = copy_out(c, mean_out, tmp, c->n * sizeof(double))) != GM_OK) return st;
+  if (var_out && (st = copy_out(c, var_out, tmp + c->n, c->n * sizeof(double))) != GM_OK) return st;
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  dev_free_now(c, tmp, 2 * c->n * sizeof(double));
+  c->stats.kernel_launches = c->launches;
+  return GM_OK;
+}
+
+gm_status gm_get_prior(gm_ctx* c, double* mean_out, double* kdiag_out) {
+  if (!c) return GM_E_INVAL;
+  if (!c->built) return set_error(c, GM_E_STATE, "gm_build_cov must come first");
+  double* tmp = (double*)dev_alloc(c, 2 * c->n * sizeof(double));
+  if (!tmp) return set_error(c, GM_E_NOMEM, "prior staging");
+  GM_PROF(c, "k_scatter_ext");
+  k_scatter_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->prior_m, tmp);
+  GM_PROF(c, "k_scatter_ext");
+  k_scatter_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->kdiag, tmp + c->n);
+  GM_LAUNCH_CHECK(c);
+  gm_status st;
+  if (mean_out && (st = copy_out(c, mean_out, tmp, c->n * sizeof(double))) != GM_OK) return st;
+  if (kdiag_out && (st = copy_out(c, kdiag_out, tmp + c->n, c->n * sizeof(double))) != GM_OK) return st;
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  dev_free_now(c, tmp, 2 * c->n * sizeof(double));
+  return GM_OK;
+}
+
+gm_status gm_get_sites(gm_ctx* c, double* tau_out, double* nu_out) {
+  if (!c) return GM_E_INVAL;
+  double* tmp = (double*)dev_alloc(c, 2 * c->n * sizeof(double));
+  if (!tmp) return set_error(c, GM_E_NOMEM, "site staging");
+  GM_PROF(c, "k_scatter_ext");
+  k_scatter_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->tau, tmp);
+  GM_PROF(c, "k_scatter_ext");
+  k_scatter_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->nu, tmp + c->n);
+  GM_LAUNCH_CHECK(c);
+  gm_status st;
+  if (tau_out && (st = copy_out(c, tau_out, tmp, c->n * sizeof(double))) != GM_OK) return st;
+  if (nu_out && (st = copy_out(c, nu_out, tmp + c->n, c->n * sizeof(double))) != GM_OK) return st;
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  dev_free_now(c, tmp, 2 * c->n * sizeof(double));
+  return GM_OK;
+}
+
+gm_status gm_set_sites(gm_ctx* c, const double* tau, const double* nu) {
+  if (!c || !tau || !nu) return GM_E_INVAL;
+  const size_t nb = c->n * sizeof(double);
+  double* tmp = (double*)dev_alloc(c, 2 * nb);
+  if (!tmp) return set_error(c, GM_E_NOMEM, "site staging");
+  gm_status st = copy_in(c, tmp, tau, nb);
+  if (st == GM_OK) st = copy_in(c, tmp + c->n, nu, nb);
+  if (st != GM_OK) return st;
+  GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned), c->stream));
+  GM_PROF(c, "k_check_sites");
+  k_check_sites<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, tmp, tmp + c->n, c->d_flags + 1);
+  GM_LAUNCH_CHECK(c);
+  unsigned* h = (unsigned*)c->h_pinned;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  if (*h) {
+    dev_free_now(c, tmp, 2 * nb);
+    return set_error(c, GM_E_INVAL, "sites must be finite with tau >= 0");
+  }
+  GM_PROF(c, "k_gather_ext");
+  k_gather_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, tmp, c->tau);
+  GM_PROF(c, "k_gather_ext");
+  k_gather_ext<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, tmp + c->n, c->nu);
+  GM_LAUNCH_CHECK(c);
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  dev_free_now(c, tmp, 2 * nb);
+  c->post_valid = false;
+  return GM_OK;
+}
+
+gm_status gm_get_perm(gm_ctx* c, int64_t* perm_out) {
+  if (!c || !perm_out) return GM_E_INVAL;
+  return copy_out(c, perm_out, c->perm, c->n * sizeof(int64_t));
+}
+
+gm_status gm_get_csr(gm_ctx* c, int64_t* row_ptr_out, int32_t* col_out, double* val_out) {
+  if (!c) return GM_E_INVAL;
+  if (!c->built) return set_error(c, GM_E_STATE, "gm_build_cov must come first");
+  gm_status st;
+  if (row_ptr_out && (st = copy_out(c, row_ptr_out, c->row_ptr, (c->n + 1) * sizeof(int64_t))) != GM_OK)
+    return st;
+  if (col_out && (st = copy_out(c, col_out, c->col, c->nnz * sizeof(int32_t))) != GM_OK) return st;
+  if (val_out) {
+    double* tmp = (double*)dev_alloc(c, std::max<int64_t>(c->nnz, 1) * sizeof(double));
+    if (!tmp) return set_error(c, GM_E_NOMEM, "CSR staging");
+    GM_PROF(c, "k_to_double");
+    if (c->cfg.precision == GM_PREC_FP32)
+      k_to_double<float><<<eb(c, c->nnz), 256, 0, c->stream>>>(c->nnz, (const float*)c->val, tmp);
+    else
+      k_to_double<double><<<eb(c, c->nnz), 256, 0, c->stream>>>(c->nnz, (const double*)c->val, tmp);
+    GM_LAUNCH_CHECK(c);
+    st = copy_out(c, val_out, tmp, c->nnz * sizeof(double));
+    dev_free_now(c, tmp, std::max<int64_t>(c->nnz, 1) * sizeof(double));
+    if (st != GM_OK) return st;
+  }
+  return GM_OK;
+}
+
+gm_status gm_get_stats(gm_ctx* c, gm_stats* out) {
+  if (!c || !out) return GM_E_INVAL;
+  *out = c->stats;
+  return GM_OK;
+}
+
+gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, const double* s,
+                     double* mean_out, double* var_out) {
+  if (!c || nq < 0 || (nq > 0 && (!l || !b || !s || !mean_out || !var_out))) return GM_E_INVAL;
+  if (nq == 0) return GM_OK;
+  c->launches = 0;
+  gm_status st = ensure_posterior(c);
+  if (st != GM_OK) return st;
+  const size_t nb = nq * sizeof(double);
+  // query arrays: l, b, s, ux, uy, uz, kss, mq, mean, var
+  double* q = (double*)dev_alloc(c, 10 * nb);
+  int64_t* qptr = (int64_t*)dev_alloc(c, (nq + 1) * sizeof(int64_t));
+  if (!q || !qptr) return set_error(c, GM_E_NOMEM, "query arrays");
+  double *ql = q, *qb = q + nq, *qs = q + 2 * nq, *ux = q + 3 * nq, *uy = q + 4 * nq,
+         *uz = q + 5 * nq, *kss = q + 6 * nq, *mq = q + 7 * nq, *mean = q + 8 * nq,
+         *var = q + 9 * nq;
+  if ((st = copy_in(c, ql, l, nb)) != GM_OK || (st = copy_in(c, qb, b, nb)) != GM_OK ||
+      (st = copy_in(c, qs, s, nb)) != GM_OK)
+    return st;
+  GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned), c->stream));
+  GM_PROF(c, "k_check_inputs");
+  k_check_inputs<<<eb(c, nq), 256, 0, c->stream>>>(nq, qs, qs, qs, ql, qb, c->d_flags + 1);
+  GM_LAUNCH_CHECK(c);
+  {
+    unsigned* h = (unsigned*)c->h_pinned;
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    if (*h) return set_error(c, GM_E_INVAL, "query distances must be finite and > 0");
+  }
+  st = unit_vectors(c, nq, ql, qb, ux, uy, uz);
+  if (st != GM_OK) return st;
+  Buffer qcol;
+  int64_t qnnz = 0;
+  st = neighbour_csr(c, nq, qs, ux, uy, uz, false, qptr, qcol, &qnnz, nullptr);
+  if (st != GM_OK) return st;
+  const size_t vs = c->cfg.precision == GM_PREC_FP32 ? sizeof(float) : sizeof(double);
+  void* qval = dev_alloc(c, std::max<int64_t>(qnnz, 1) * vs);
+  if (!qval) return set_error(c, GM_E_NOMEM, "query values");
+  st = pair_quadrature(c, nq, qs, ux, uy, uz, qptr, (const int32_t*)qcol.p, qnnz, qval, false);
+  if (st == GM_OK) st = self_quadrature(c, nq, qs, kss);
+  if (st != GM_OK) return st;
+  // prior mean at the queries
+  // m_q = ln(rho_bar s_q) - k_qq/2 (lognormal) or - sigma2/2 (linear)
+  GM_PROF(c, "k_query_mean");
+  k_query_mean<<<eb(c, nq), 256, 0, c->stream>>>(nq, std::log(c->cfg.rho_bar), c->cfg.form,
+                                                 c->cfg.sigma2, qs, kss, mq);
+  GM_LAUNCH_CHECK(c);
+  st = csr_dot_alpha(c, nq, qptr, (const int32_t*)qcol.p, qval, c->alpha, mq, mean);
+  if (st != GM_OK) return st;
+  int64_t it = 0;
+  double res = 0;
+  st = panel_variances(c, nq, qptr, (const int32_t*)qcol.p, qval, kss, var, &it, &res);
+  if (st == GM_OK) st = read_flags(c);
+  if (st != GM_OK) return st;
+  if ((st = copy_out(c, mean_out, mean, nb)) != GM_OK) return st;
+  if ((st = copy_out(c, var_out, var, nb)) != GM_OK) return st;
+  dev_free_now(c, qval, std::max<int64_t>(qnnz, 1) * vs);
+  dev_free_now(c, qcol.p, qcol.bytes);
+  dev_free_now(c, qptr, (nq + 1) * sizeof(int64_t));
+  dev_free_now(c, q, 10 * nb);
+  c->stats.kernel_launches = c->launches;
+  return GM_OK;
+}
+
+gm_status gm_profile(gm_ctx* c, int32_t enable) {
+  if (!c) return GM_E_INVAL;
+  prof_collect(c);
+  c->prof_on = enable != 0;
+  if (enable == 0) c->prof_acc.clear();
+  return GM_OK;
+}
+
+int32_t gm_kernel_time_count(gm_ctx* c) {
+  if (!c) return 0;
+  prof_collect(c);
+  return (int32_t)c->prof_acc.size();
+}
+
+gm_status gm_kernel_time(gm_ctx* c, int32_t k, const char** name, int64_t* launches,
+                         double* total_ms) {
+  if (!c || k < 0 || k >= (int32_t)c->prof_acc.size()) return GM_E_INVAL;
+  if (name) *name = c->prof_acc[k].name;
+  if (launches) *launches = c->prof_acc[k].launches;
+  if (total_ms) *total_ms = c->prof_acc[k].ms;
+  return GM_OK;
+}
+
+void gm_destroy(gm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  prof_collect(c);
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
+  c->prof_pool.clear();
+  workspace_free(c);
+  for (auto& b : c->owned) {
+    if (c->has_alloc)
+      c->alloc.free(b.p, b.bytes, (void*)c->stream, c->alloc.user);
+    else
+      cudaFreeAsync(b.p, c->stream);
+  }
+  c->owned.clear();
+  cudaStreamSynchronize(c->stream);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+}
+
+}  // extern "C"
+

@@ -1,0 +1,430 @@
+// Geometry, spatial ordering and the neighbour CSR (the sparsity pattern of
+// the covariance: pairs whose 3-D separation is within the cutoff).
+//
+// Stars are renumbered by a stable sort on the id of the grid cell that
+// holds them (cell edge >= cutoff), so that each cell owns a contiguous range
+// of internal indices and a row's neighbours, visited cell by cell in
+// increasing cell id, come out in increasing column order.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+// ------------------------------------------------------------ unit vectors
+__global__ void k_unit_vectors(int64_t n, const double* __restrict__ l,
+                               const double* __restrict__ b, double* __restrict__ ux,
+                               double* __restrict__ uy, double* __restrict__ uz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double sl, cl, sb, cb;
+    sincos(l[i], &sl, &cl);
+    sincos(b[i], &sb, &cb);
+    ux[i] = cb * cl;
+    uy[i] = cb * sl;
+    uz[i] = sb;
+  }
+}
+
+// Bounding box of star positions (single block, fixed reduction order).
+__global__ void k_bbox(int64_t n, const double* __restrict__ s, const double* __restrict__ ux,
+                       const double* __restrict__ uy, const double* __restrict__ uz,
+                       double* __restrict__ out /* 6: min xyz, max xyz */) {
+  __shared__ double sh[6][1024];
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    double p[3] = {s[i] * ux[i], s[i] * uy[i], s[i] * uz[i]};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], p[d]);
+      hi[d] = fmax(hi[d], p[d]);
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    sh[d][threadIdx.x] = lo[d];
+    sh[d + 3][threadIdx.x] = hi[d];
+  }
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int d = 0; d < 3; ++d) {
+        sh[d][threadIdx.x] = fmin(sh[d][threadIdx.x], sh[d][threadIdx.x + w]);
+        sh[d + 3][threadIdx.x] = fmax(sh[d + 3][threadIdx.x], sh[d + 3][threadIdx.x + w]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+struct Grid {
+  int gx, gy, gz;
+  double ox, oy, oz, inv_cell;
+};
+
+__device__ __forceinline__ void cell_coords(const Grid& g, double x, double y, double z,
+                                            int* cx, int* cy, int* cz) {
+  int a = (int)floor((x - g.ox) * g.inv_cell);
+  int b = (int)floor((y - g.oy) * g.inv_cell);
+  int c = (int)floor((z - g.oz) * g.inv_cell);
+  *cx = min(max(a, 0), g.gx - 1);
+  *cy = min(max(b, 0), g.gy - 1);
+  *cz = min(max(c, 0), g.gz - 1);
+}
+
+__global__ void k_cell_keys(int64_t n, int64_t n_pad, Grid g, const double* __restrict__ s,
+                            const double* __restrict__ ux, const double* __restrict__ uy,
+                            const double* __restrict__ uz, unsigned long long* __restrict__ keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      int cx, cy, cz;
+      cell_coords(g, s[i] * ux[i], s[i] * uy[i], s[i] * uz[i], &cx, &cy, &cz);
+      unsigned long long id = ((unsigned long long)cx * g.gy + cy) * g.gz + cz;
+      keys[i] = (id << 32) | (unsigned long long)i;
+    } else {
+      keys[i] = ~0ull;
+    }
+  }
+}
+
+// Bitonic sort, global compare-exchange pass for stride j >= 1024.
+__global__ void k_bitonic_global(unsigned long long* a, int64_t n_pad, int64_t k, int64_t j) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = i ^ j;
+    if (p > i) {
+      bool asc = (i & k) == 0;
+      unsigned long long x = a[i], y = a[p];
+      if ((x > y) == asc) {
+        a[i] = y;
+        a[p] = x;
+      }
+    }
+  }
+}
+
+// Bitonic sort, all strides j < 1024 of phase k inside one 1024-element tile.
+__global__ void k_bitonic_shared(unsigned long long* a, int64_t n_pad, int64_t k, int64_t j0) {
+  __shared__ unsigned long long t[1024];
+  int64_t base = (int64_t)blockIdx.x * 1024;
+  for (int q = threadIdx.x; q < 1024; q += blockDim.x) t[q] = a[base + q];
+  __syncthreads();
+  for (int64_t j = j0; j > 0; j >>= 1) {
+    for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
+      int p = q ^ (int)j;
+      if (p > q) {
+        bool asc = ((base + q) & k) == 0;
+        unsigned long long x = t[q], y = t[p];
+        if ((x > y) == asc) {
+          t[q] = y;
+          t[p] = x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < 1024; q += blockDim.x) a[base + q] = t[q];
+}
+
+// Apply the sorted order: internal star k <- caller star (key & 0xffffffff).
+__global__ void k_apply_perm(int64_t n, const unsigned long long* __restrict__ keys,
+                             const double* __restrict__ s_in, const double* __restrict__ ux_in,
+                             const double* __restrict__ uy_in, const double* __restrict__ uz_in,
+                             const double* __restrict__ obs_in, const double* __restrict__ sig_in,
+                             int64_t* __restrict__ perm, double* __restrict__ s,
+                             double* __restrict__ ux, double* __restrict__ uy,
+                             double* __restrict__ uz, double* __restrict__ obs,
+                             double* __restrict__ sig, int32_t* __restrict__ cell_of) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long key = keys[k];
+    int64_t i = (int64_t)(key & 0xffffffffull);
+    perm[k] = i;
+    s[k] = s_in[i];
+    ux[k] = ux_in[i];
+    uy[k] = uy_in[i];
+    uz[k] = uz_in[i];
+    obs[k] = obs_in[i];
+    sig[k] = sig_in[i];
+    cell_of[k] = (int32_t)(key >> 32);
+  }
+}
+
+// cell_start[c] = first internal index whose cell id >= c.
+__global__ void k_cell_start(int64_t n, int64_t n_cells, const int32_t* __restrict__ cell_of,
+                             int32_t* __restrict__ cell_start) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t prev = k == 0 ? -1 : cell_of[k - 1];
+    int64_t cur = k == n ? n_cells : cell_of[k];
+    for (int64_t c = prev + 1; c <= cur; ++c) cell_start[c] = (int32_t)k;
+  }
+}
+
+// ------------------------------------------------------------ neighbours
+// d^2 between a row point (s_r, u_r) and star j, in FP64 by the chord form
+// (s_r - s_j)^2 + s_r s_j |u_r - u_j|^2, which is the squared 3-D distance.
+__device__ __forceinline__ double dist2(double sr, double xr, double yr, double zr, double sj,
+                                        double xj, double yj, double zj) {
+  double dx = xr - xj, dy = yr - yj, dz = zr - zj;
+  double ds = sr - sj;
+  return fma(ds, ds, sr * sj * fma(dx, dx, fma(dy, dy, dz * dz)));
+}
+
+template <bool kFill>
+__global__ void k_neighbours(int64_t n_rows, Grid g, double cut2, const double* __restrict__ rs,
+                             const double* __restrict__ rux, const double* __restrict__ ruy,
+                             const double* __restrict__ ruz, const double* __restrict__ s,
+                             const double* __restrict__ ux, const double* __restrict__ uy,
+                             const double* __restrict__ uz, const int32_t* __restrict__ cell_start,
+                             int64_t* __restrict__ count_or_ptr, int32_t* __restrict__ col,
+                             int64_t* __restrict__ diag_pos, bool self) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n_rows; r += nwarps) {
+    const double sr = rs[r], xr = rux[r], yr = ruy[r], zr = ruz[r];
+    int cx, cy, cz;
+    cell_coords(g, sr * xr, sr * yr, sr * zr, &cx, &cy, &cz);
+    int64_t pos = kFill ? count_or_ptr[r] : 0;
+    int64_t cnt = 0;
+    for (int dx = -1; dx <= 1; ++dx) {
+      int ax = cx + dx;
+      if (ax < 0 || ax >= g.gx) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        int ay = cy + dy;
+        if (ay < 0 || ay >= g.gy) continue;
+        // the three z-neighbours are consecutive cells: one contiguous range
+        int z0 = max(cz - 1, 0), z1 = min(cz + 1, g.gz - 1);
+        int64_t c0 = ((int64_t)ax * g.gy + ay) * g.gz + z0;
+        int64_t c1 = ((int64_t)ax * g.gy + ay) * g.gz + z1 + 1;
+        int32_t j0 = cell_start[c0], j1 = cell_start[c1];
+        for (int32_t jb = j0; jb < j1; jb += 32) {
+          int32_t j = jb + lane;
+          bool in = false;
+          if (j < j1) in = dist2(sr, xr, yr, zr, s[j], ux[j], uy[j], uz[j]) <= cut2;
+          unsigned m = __ballot_sync(0xffffffffu, in);
+          if (kFill) {
+            if (in) {
+              int64_t p = pos + cnt + __popc(m & ((1u << lane) - 1u));
+              col[p] = j;
+              if (self && j == r) diag_pos[r] = p;
+            }
+          }
+          cnt += __popc(m);
+        }
+      }
+    }
+    if (!kFill && lane == 0) count_or_ptr[r] = cnt;
+  }
+}
+
+// ------------------------------------------------------------ scan (int64)
+// Exclusive scan of n counts into out[0..n] in three passes over 1024-element
+// tiles (tile scan, scan of tile sums by one block, offset add).
+__device__ __forceinline__ int64_t block_excl_scan_1024(int64_t v, int64_t* sh, int64_t* total) {
+  int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int64_t add = t >= off ? sh[t - off] : 0;
+    __syncthreads();
+    sh[t] += add;
+    __syncthreads();
+  }
+  int64_t incl = sh[t];
+  *total = sh[1023];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(int64_t n, const int64_t* __restrict__ in,
+                                                     int64_t* __restrict__ out,
+                                                     int64_t* __restrict__ tile_sums) {
+  __shared__ int64_t sh[1024];
+  int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+  int64_t v = i < n ? in[i] : 0;
+  int64_t tot;
+  int64_t ex = block_excl_scan_1024(v, sh, &tot);
+  if (i < n) out[i] = ex;
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t n_tiles, int64_t* __restrict__ sums,
+                                                    int64_t* __restrict__ grand) {
+  __shared__ int64_t sh[1024];
+  int64_t carry = 0;
+  for (int64_t b = 0; b < n_tiles; b += 1024) {
+    int64_t i = b + threadIdx.x;
+    int64_t v = i < n_tiles ? sums[i] : 0;
+    int64_t tot;
+    int64_t ex = block_excl_scan_1024(v, sh, &tot);
+    if (i < n_tiles) sums[i] = ex + carry;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void k_scan_add(int64_t n, int64_t* __restrict__ out, const int64_t* __restrict__ sums,
+                           const int64_t* __restrict__ grand) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == n)
+      out[n] = *grand;
+    else
+      out[i] += sums[i / 1024];
+  }
+}
+
+// ------------------------------------------------------------ host side
+static Grid grid_of(const gm_ctx* c) {
+  Grid g;
+  g.gx = c->gx;
+  g.gy = c->gy;
+  g.gz = c->gz;
+  g.ox = c->org[0];
+  g.oy = c->org[1];
+  g.oz = c->org[2];
+  g.inv_cell = 1.0 / c->cell;
+  return g;
+}
+
+gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const double* s,
+                        const double* obs, const double* sig) {
+  const int64_t n = c->n;
+  cudaStream_t st = c->stream;
+  const int sms = sm_count(c);
+  const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * sms);
+  // caller-order scratch
+  double* ux_in = (double*)dev_alloc(c, n * sizeof(double));
+  double* uy_in = (double*)dev_alloc(c, n * sizeof(double));
+  double* uz_in = (double*)dev_alloc(c, n * sizeof(double));
+  double* bbox = (double*)dev_alloc(c, 8 * sizeof(double));
+  if (!ux_in || !uy_in || !uz_in || !bbox) return set_error(c, GM_E_NOMEM, "geometry scratch");
+  GM_PROF(c, "k_unit_vectors");
+  k_unit_vectors<<<blocks, 256, 0, st>>>(n, l, b, ux_in, uy_in, uz_in);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_bbox");
+  k_bbox<<<1, 1024, 0, st>>>(n, s, ux_in, uy_in, uz_in, bbox);
+  GM_LAUNCH_CHECK(c);
+  double hb[6];
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  // grid with cell edge >= cutoff and at most 2^26 cells
+  double cell = c->cfg.cutoff_pc;
+  for (int it = 0; it < 64; ++it) {
+    double ext[3];
+    int64_t tot = 1;
+    int dims[3];
+    for (int d = 0; d < 3; ++d) {
+      ext[d] = hb[d + 3] - hb[d];
+      dims[d] = (int)std::min<double>(std::floor(ext[d] / cell) + 1.0, 1 << 26);
+      tot *= dims[d];
+    }
+    if (tot <= (1ll << 26)) {
+      c->gx = dims[0];
+      c->gy = dims[1];
+      c->gz = dims[2];
+      break;
+    }
+    cell *= 1.26;
+  }
+  c->cell = cell;
+  for (int d = 0; d < 3; ++d) c->org[d] = hb[d];
+  const int64_t n_cells = (int64_t)c->gx * c->gy * c->gz;
+  Grid g = grid_of(c);
+
+  int64_t n_pad = 1024;
+  while (n_pad < n) n_pad <<= 1;
+  unsigned long long* keys = (unsigned long long*)dev_alloc(c, n_pad * sizeof(unsigned long long));
+  int32_t* cell_of = (int32_t*)dev_alloc(c, n * sizeof(int32_t));
+  c->cell_start = (int32_t*)dev_alloc(c, (n_cells + 1) * sizeof(int32_t));
+  if (!keys || !cell_of || !c->cell_start) return set_error(c, GM_E_NOMEM, "cell grid");
+  const int kb = (int)std::min<int64_t>(ceil_div(n_pad, 256), 16 * sms);
+  GM_PROF(c, "k_cell_keys");
+  k_cell_keys<<<kb, 256, 0, st>>>(n, n_pad, g, s, ux_in, uy_in, uz_in, keys);
+  GM_LAUNCH_CHECK(c);
+  for (int64_t k = 2; k <= n_pad; k <<= 1) {
+    int64_t j = k >> 1;
+    for (; j >= 1024; j >>= 1) {
+      GM_PROF(c, "k_bitonic_global");
+      k_bitonic_global<<<kb, 256, 0, st>>>(keys, n_pad, k, j);
+      GM_LAUNCH_CHECK(c);
+    }
+    GM_PROF(c, "k_bitonic_shared");
+    k_bitonic_shared<<<(unsigned)(n_pad / 1024), 512, 0, st>>>(keys, n_pad, k, j);
+    GM_LAUNCH_CHECK(c);
+  }
+  GM_PROF(c, "k_apply_perm");
+  k_apply_perm<<<blocks, 256, 0, st>>>(n, keys, s, ux_in, uy_in, uz_in, obs, sig, c->perm, c->s,
+                                       c->ux, c->uy, c->uz, c->obs, c->obs_sigma, cell_of);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_cell_start");
+  k_cell_start<<<blocks, 256, 0, st>>>(n, n_cells, cell_of, c->cell_start);
+  GM_LAUNCH_CHECK(c);
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  dev_free_now(c, keys, n_pad * sizeof(unsigned long long));
+  dev_free_now(c, cell_of, n * sizeof(int32_t));
+  dev_free_now(c, bbox, 8 * sizeof(double));
+  dev_free_now(c, uz_in, n * sizeof(double));
+  dev_free_now(c, uy_in, n * sizeof(double));
+  dev_free_now(c, ux_in, n * sizeof(double));
+  return GM_OK;
+}
+
+gm_status unit_vectors(gm_ctx* c, int64_t n, const double* l, const double* b, double* ux,
+                       double* uy, double* uz) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * sm_count(c)));
+  GM_PROF(c, "k_unit_vectors");
+  k_unit_vectors<<<blocks, 256, 0, c->stream>>>(n, l, b, ux, uy, uz);
+  GM_LAUNCH_CHECK(c);
+  return GM_OK;
+}
+
+gm_status neighbour_csr(gm_ctx* c, int64_t n_rows, const double* rs, const double* rux,
+                        const double* ruy, const double* ruz, bool self, int64_t* row_ptr,
+                        Buffer& col_buf, int64_t* nnz_out, int64_t* diag_pos) {
+  cudaStream_t st = c->stream;
+  const int sms = sm_count(c);
+  Grid g = grid_of(c);
+  const double cut2 = c->cfg.cutoff_pc * c->cfg.cutoff_pc;
+  int64_t* counts = (int64_t*)dev_alloc(c, (n_rows + 1) * sizeof(int64_t));
+  int64_t n_tiles = ceil_div(n_rows + 1, 1024);
+  int64_t* sums = (int64_t*)dev_alloc(c, (n_tiles + 1) * sizeof(int64_t));
+  if (!counts || !sums) return set_error(c, GM_E_NOMEM, "neighbour counts");
+  const int wb = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 32 * sms);
+  GM_PROF(c, "k_neighbours");
+  k_neighbours<false><<<wb, 256, 0, st>>>(n_rows, g, cut2, rs, rux, ruy, ruz, c->s, c->ux, c->uy,
+                                          c->uz, c->cell_start, counts, nullptr, nullptr, self);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_scan_tiles");
+  k_scan_tiles<<<(unsigned)ceil_div(n_rows, 1024), 1024, 0, st>>>(n_rows, counts, row_ptr, sums);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_scan_sums");
+  k_scan_sums<<<1, 1024, 0, st>>>(ceil_div(n_rows, 1024), sums, sums + n_tiles);
+  GM_LAUNCH_CHECK(c);
+  const int ab = (int)std::min<int64_t>(ceil_div(n_rows + 1, 256), 8 * sms);
+  GM_PROF(c, "k_scan_add");
+  k_scan_add<<<ab, 256, 0, st>>>(n_rows, row_ptr, sums, sums + n_tiles);
+  GM_LAUNCH_CHECK(c);
+  int64_t nnz = 0;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(&nnz, row_ptr + n_rows, sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, st));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  if (nnz >= (1ll << 40)) return set_error(c, GM_E_NOMEM, "neighbour count overflow");
+  if (!ensure(c, col_buf, std::max<int64_t>(nnz, 1) * sizeof(int32_t)))
+    return set_error(c, GM_E_NOMEM, "CSR column indices");
+  GM_PROF(c, "k_neighbours");
+  k_neighbours<true><<<wb, 256, 0, st>>>(n_rows, g, cut2, rs, rux, ruy, ruz, c->s, c->ux, c->uy,
+                                         c->uz, c->cell_start, row_ptr, (int32_t*)col_buf.p,
+                                         diag_pos, self);
+  GM_LAUNCH_CHECK(c);
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  dev_free_now(c, sums, (n_tiles + 1) * sizeof(int64_t));
+  dev_free_now(c, counts, (n_rows + 1) * sizeof(int64_t));
+  *nnz_out = nnz;
+  return GM_OK;
+}
+
+}  // namespace gm

@@ -1,0 +1,228 @@
+// Internal declarations of libgmead (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gmead.h"
+
+namespace gm {
+
+// ---------------------------------------------------------------- constants
+constexpr int kWarp = 32;
+constexpr int kGH = 64;          // Gauss-Hermite nodes of the tilted rule
+constexpr int kMaxNodes = 128;   // Gauss-Legendre nodes per sightline (max)
+
+// Device status flags (OR-ed by kernels, read by the host after a call).
+enum : unsigned {
+  kFlagNonFinite = 1u,
+  kFlagNotSPD = 2u,
+  kFlagTimeout = 4u,
+};
+
+// Log-spaced cubic table of g(x), x = r^2 / L0^2.  Segment k >= 0 covers
+// [x_lo(k), x_lo(k+1)) with x_lo(k) = 2^(emin + k / 2^m) * (1 + (k mod 2^m)/2^m),
+// i.e. 2^m equal sub-intervals per octave; the segment of x is read from the
+// exponent and leading mantissa bits of x.  Index n_real holds zeros (g beyond
+// 2^emax is below 1e-19 and dropped).  Arguments below 2^emin are clamped
+// (the error there is < 1e-10 of g(0)).
+struct TableGeom {
+  int m;        // log2(segments per octave)
+  int emin;     // first octave exponent
+  int emax;     // end octave exponent (exclusive)
+  __host__ __device__ int n_real() const { return (emax - emin) << m; }
+  __host__ __device__ int n_pts() const { return 3 * n_real() + 1; }
+};
+constexpr TableGeom kTabF32{4, -100, 11};
+constexpr TableGeom kTabF64{7, -100, 11};
+
+// ---------------------------------------------------------------- context
+struct Buffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Workspace;  // solver scratch, see gm_solve.cu
+
+// Four doubles, 32-byte aligned (one FP64 table segment).
+struct alignas(32) D4 {
+  double x, y, z, w;
+};
+
+}  // namespace gm
+
+struct gm_ctx {
+  gm_config cfg{};
+  int64_t n = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  gm_allocator alloc{};
+  bool has_alloc = false;
+  std::string last_error;
+  gm_stats stats{};
+  int64_t launches = 0;   // kernels launched during the current API call
+
+  // owned device allocations (freed at destroy)
+  std::vector<gm::Buffer> owned;
+
+  // ---- stars, internal (spatially sorted) order
+  int64_t* perm = nullptr;     // internal -> caller index
+  double* s = nullptr;         // distance
+  double* ux = nullptr;        // unit vector components
+  double* uy = nullptr;
+  double* uz = nullptr;
+  double* obs = nullptr;
+  double* obs_sigma = nullptr;
+
+  // ---- cell grid (cell edge >= cutoff)
+  int gx = 0, gy = 0, gz = 0;
+  double org[3] = {0, 0, 0};
+  double cell = 0;
+  int32_t* cell_start = nullptr;  // gx*gy*gz + 1
+
+  // ---- covariance, CSR over internal order
+  bool built = false;
+  int64_t nnz = 0;
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  void* val = nullptr;         // double (FP64) or float (FP32)
+  gm::Buffer col_buf, val_buf;
+  int64_t* diag_pos = nullptr;
+  double* kdiag = nullptr;
+  double* prior_m = nullptr;
+
+  // ---- quadrature tables
+  double* gl_zeta = nullptr;   // Q nodes on [0,1]
+  double* gl_w = nullptr;      // Q weights (sum 1)
+  double* gh_x = nullptr;      // Gauss-Hermite nodes
+  double* gh_wx = nullptr;     // weights * exp(x^2)
+  double* phi_pts = nullptr;   // phi at table points (hyperparameter-free)
+  void* gtab = nullptr;        // cubic coefficients of g (float4 / double4)
+  double gtab_sigma2 = -1;
+  int gtab_form = -1;
+
+  // ---- EP state
+  double* tau = nullptr;
+  double* nu = nullptr;
+  double* mu = nullptr;        // posterior mean for (tau, nu) when post_valid
+  double* var = nullptr;
+  double* alpha = nullptr;     // mu = m + K alpha
+  bool post_valid = false;
+
+  // ---- status flags and pinned readback
+  unsigned* d_flags = nullptr;
+  void* h_pinned = nullptr;    // 64 KB pinned host scratch
+
+  gm::Workspace* ws = nullptr;
+
+  // ---- optional per-kernel timing (CUDA events on the context stream)
+  bool prof_on = false;
+  const char* prof_pending = nullptr;
+  struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  struct ProfAcc {
+    const char* name;
+    int64_t launches;
+    double ms;
+  };
+  std::vector<ProfAcc> prof_acc;
+};
+
+namespace gm {
+
+// ---------------------------------------------------------------- helpers
+gm_status set_error(gm_ctx* c, gm_status st, const std::string& msg);
+gm_status cuda_fail(gm_ctx* c, cudaError_t e, const char* what);
+
+void* dev_alloc(gm_ctx* c, size_t bytes);            // owned until destroy
+void dev_free_now(gm_ctx* c, void* p, size_t bytes);
+bool ensure(gm_ctx* c, Buffer& b, size_t bytes);      // grow-only scratch
+
+#define GM_CUDA_CHECK(ctx, expr)                                   \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return ::gm::cuda_fail((ctx), _e, #expr); \
+  } while (0)
+
+// Timing hooks: GM_PROF(ctx, "name") before a launch records a start event
+// when profiling is on; GM_LAUNCH_CHECK records the matching stop event.
+void prof_begin(gm_ctx* c, const char* name);
+void prof_end(gm_ctx* c);
+void prof_collect(gm_ctx* c);  // after a stream sync: fold records into totals
+
+#define GM_PROF(ctx, name) \
+  do {                      \
+    if ((ctx)->prof_on) ::gm::prof_begin((ctx), (name)); \
+  } while (0)
+
+#define GM_LAUNCH_CHECK(ctx)                                      \
+  do {                                                            \
+    (ctx)->launches++;                                            \
+    if ((ctx)->prof_pending) ::gm::prof_end(ctx);                 \
+    cudaError_t _e = cudaGetLastError();                          \
+    if (_e != cudaSuccess) return ::gm::cuda_fail((ctx), _e, "kernel launch"); \
+  } while (0)
+
+inline int sm_count(gm_ctx* c) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
+  return v > 0 ? v : 1;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------- host rules
+// Gauss-Legendre on [-1,1] and Gauss-Hermite (weight exp(-x^2)) by Newton
+// iteration on the three-term recurrences (gm_rules.cpp).
+void gauss_legendre(int n, double* x, double* w);
+void gauss_hermite(int n, double* x, double* w_times_expx2);
+
+// ---------------------------------------------------------------- stages
+gm_status geometry_init(gm_ctx* c, const double* l, const double* b,
+                        const double* s, const double* obs, const double* sig);
+gm_status unit_vectors(gm_ctx* c, int64_t n, const double* l, const double* b, double* ux,
+                       double* uy, double* uz);
+// Rows = the given positions (internal stars or queries), columns = stars.
+// Counts neighbours within the cutoff of each row, scans to row_ptr (n_rows+1)
+// and fills sorted column indices.  `self` marks rows that are the stars
+// themselves (diag_pos is then filled).
+gm_status neighbour_csr(gm_ctx* c, int64_t n_rows, const double* rs,
+                        const double* rux, const double* ruy, const double* ruz,
+                        bool self, int64_t* row_ptr, Buffer& col_buf,
+                        int64_t* nnz_out, int64_t* diag_pos);
+gm_status phi_points_init(gm_ctx* c);
+gm_status gtab_update(gm_ctx* c);
+// Pair quadrature for CSR entries; symmetric mode computes j >= i and
+// mirrors.  Writes values (double or float per precision) and, in symmetric
+// mode, K_ii and the prior mean.
+gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs,
+                          const double* rux, const double* ruy, const double* ruz,
+                          const int64_t* row_ptr, const int32_t* col, int64_t nnz,
+                          void* val, bool symmetric);
+// Diagonal-only quadrature (query self-covariance) into kss (FP64).
+gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* kss);
+
+// Posterior of the current sites: mu, var, alpha (gm_solve.cu).
+gm_status refresh_posterior(gm_ctx* c);
+// Variances k_rr - v_r^T B^-1 v_r for rows of an arbitrary CSR over stars
+// (v_r = S^1/2 k_r); used for the stars themselves and for queries.
+gm_status panel_variances(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
+                          const int32_t* col, const void* val, const double* kdiag_rows,
+                          double* var_out, int64_t* iters_out, double* resid_out);
+gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
+                        const int32_t* col, const void* val, const double* alpha,
+                        const double* base, double* out);
+
+// EP site update over all stars (gm_site.cu).
+gm_status site_update(gm_ctx* c, double* max_delta, int64_t* skipped);
+
+void workspace_free(gm_ctx* c);
+
+}  // namespace gm

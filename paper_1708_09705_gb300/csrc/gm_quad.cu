@@ -1,0 +1,459 @@
+// Covariance of log-extinctions by sightline double quadrature (Sect. 3).
+//
+// For stars i, j at distances s_i, s_j in directions u_i, u_j the density
+// covariance is integrated along both sightlines:
+//   R_ij = (1 / s_i s_j) int_0^{s_i} int_0^{s_j} g(|t u_i - t' u_j|) dt dt',
+// g = expm1(sigma2 phi(r / L0)) (lognormal moment match of rho = exp f) or
+// sigma2 phi (first-order form), where phi is the correlation of a
+// Kolmogorov spectrum truncated at the outer scale L0 (Sect. 1):
+//   phi(x) = 2^(2/3) / Gamma(1/3) x^(1/3) K_(1/3)(x).
+// Then K_ij = log1p(R_ij) (or R_ij) times the Wendland taper of the 3-D star
+// separation, and m_i = ln(rho_bar s_i) - K_ii / 2.
+//
+// phi is evaluated once per context on the GPU from the integral
+// representation K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt (trapezoid
+// rule, exponentially convergent), at the nodes of a log-spaced cubic table
+// in x^2 = r^2 / L0^2; each build refits the table of g for the current
+// sigma2 and the quadrature kernels interpolate it.  The separation is taken
+// in the cancellation-free chord form r^2 = (t - t')^2 + t t' |u_i - u_j|^2.
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+// ------------------------------------------------------------ phi table
+__device__ __forceinline__ double seg_lo(const TableGeom g, int k) {
+  int oct = k >> g.m, sub = k & ((1 << g.m) - 1);
+  return ldexp(1.0 + (double)sub / (double)(1 << g.m), g.emin + oct);
+}
+
+// phi(rho) for rho > 0 by the trapezoid rule with step h = 0.1 in t.
+__device__ double phi_of_rho(double rho, double cnorm) {
+  const double h = 0.1;
+  double sum = 0.5 * exp(-rho);  // t = 0 term: exp(-rho) cosh(0)
+  for (int k = 1; k < 4000; ++k) {
+    double t = k * h;
+    double e = exp(t * (1.0 / 3.0));
+    double ei = 1.0 / e;
+    double ch3 = 0.5 * (e + ei);                 // cosh(t/3)
+    double ch = 0.5 * (e * e * e + ei * ei * ei);  // cosh(t)
+    double term = exp(-rho * ch) * ch3;
+    sum += term;
+    // remaining terms are below 1e-20 of the sum once rho (cosh t - 1)
+    // exceeds t/3 + 50
+    if (rho * (ch - 1.0) > t * (1.0 / 3.0) + 50.0) break;
+  }
+  return cnorm * cbrt(rho) * (h * sum);
+}
+
+__global__ void k_phi_points(TableGeom g, double cnorm, double* __restrict__ out) {
+  const int np = g.n_pts();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    int k = p / 3, q = p - 3 * k;
+    double x;
+    if (k >= g.n_real()) {
+      x = ldexp(1.0, g.emax);
+    } else {
+      double lo = seg_lo(g, k);
+      double H = ldexp(1.0 / (double)(1 << g.m), g.emin + (k >> g.m));
+      x = lo + H * (double)q / 3.0;
+    }
+    out[p] = phi_of_rho(sqrt(x), cnorm);
+  }
+}
+
+// Cubic through g at the four equispaced nodes of each segment, as
+// coefficients of the local offset d = x - x_lo (Newton forward differences).
+template <typename T4>
+__global__ void k_gtab(TableGeom g, const double* __restrict__ phi, double sigma2, int form,
+                       T4* __restrict__ tab) {
+  const int nr = g.n_real();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nr; k += gridDim.x * blockDim.x) {
+    T4 o;
+    if (k == nr) {
+      o.x = o.y = o.z = o.w = 0;
+    } else {
+      double v[4];
+      for (int q = 0; q < 4; ++q) {
+        double c = sigma2 * phi[3 * k + q];
+        v[q] = form == GM_FORM_LOGNORMAL ? expm1(c) : c;
+      }
+      double d1 = v[1] - v[0], d2 = v[2] - 2 * v[1] + v[0], d3 = v[3] - 3 * v[2] + 3 * v[1] - v[0];
+      double c0 = v[0], c1 = d1 - 0.5 * d2 + d3 / 3.0, c2 = 0.5 * d2 - 0.5 * d3, c3 = d3 / 6.0;
+      double H = ldexp(1.0 / (double)(1 << g.m), g.emin + (k >> g.m));
+      double sc = 3.0 / H;
+      o.x = c0;
+      o.y = c1 * sc;
+      o.z = c2 * sc * sc;
+      o.w = c3 * sc * sc * sc;
+    }
+    tab[k] = o;
+  }
+}
+
+// ------------------------------------------------------------ g lookup
+struct TabF32 {
+  int base;      // float bits of 2^emin
+  int shift;     // 23 - m
+  int last;      // index of the zero segment
+  float xmin;
+};
+struct TabF64 {
+  int base;      // high word of 2^emin
+  int shift;     // 20 - m
+  int last;
+  double xmin;
+};
+
+__device__ __forceinline__ float g_lookup(const float4* __restrict__ tab, const TabF32& t, float x) {
+  x = fmaxf(x, t.xmin);
+  int bits = __float_as_int(x);
+  int k = min((bits - t.base) >> t.shift, t.last);
+  float xlo = __int_as_float(bits & ~((1 << t.shift) - 1));
+  float d = x - xlo;  // exact: x and xlo are within a factor 2
+  float4 c = tab[k];
+  return fmaf(d, fmaf(d, fmaf(d, c.w, c.z), c.y), c.x);
+}
+
+__device__ __forceinline__ double g_lookup(const D4* __restrict__ tab, const TabF64& t,
+                                           double x) {
+  x = fmax(x, t.xmin);
+  int hi = __double2hiint(x);
+  int k = min((hi - t.base) >> t.shift, t.last);
+  double xlo = __hiloint2double(hi & ~((1 << t.shift) - 1), 0);
+  double d = x - xlo;
+  const double2* p = reinterpret_cast<const double2*>(tab + k);
+  double2 a = __ldg(p), b = __ldg(p + 1);
+  return fma(d, fma(d, fma(d, b.y, b.x), a.y), a.x);
+}
+
+__device__ __forceinline__ double wendland(double h) {
+  if (h >= 1.0) return 0.0;
+  double u = 1.0 - h, u2 = u * u;
+  return u2 * u2 * (4.0 * h + 1.0);
+}
+
+struct QuadParams {
+  double inv_L0;
+  double inv_cut;
+  double log_rho_bar;
+  double sigma2;
+  int Q;
+  int form;
+  int taper;
+  int symmetric;
+};
+
+// One warp per CSR entry (i, j): lanes own the nodes q' of sightline j,
+// loop over the nodes q of sightline i, and the warp sums the products.
+// In symmetric mode entries with j < i are left for k_mirror.
+template <typename T, int KPL>
+__global__ void __launch_bounds__(256) k_pair_quad(
+    QuadParams P, int64_t n_rows, const double* __restrict__ rs, const double* __restrict__ rux,
+    const double* __restrict__ ruy, const double* __restrict__ ruz, const double* __restrict__ s,
+    const double* __restrict__ ux, const double* __restrict__ uy, const double* __restrict__ uz,
+    const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
+    T* __restrict__ val, const double* __restrict__ gl_zeta, const double* __restrict__ gl_w,
+    const void* __restrict__ gtab, TabF32 tf, TabF64 td, double* __restrict__ kdiag,
+    double* __restrict__ prior_m, unsigned* __restrict__ flags) {
+  extern __shared__ unsigned char smem[];
+  typedef typename std::conditional<sizeof(T) == 4, float4, D4>::type T4;
+  T* zq = reinterpret_cast<T*>(smem);
+  T* wq = zq + kMaxNodes;
+  const T4* tab;
+  if (sizeof(T) == 4) {
+    // the FP32 table lives in shared memory
+    float4* st = reinterpret_cast<float4*>(smem + 2 * kMaxNodes * sizeof(T));
+    const float4* gt = reinterpret_cast<const float4*>(gtab);
+    for (int k = threadIdx.x; k <= tf.last; k += blockDim.x) st[k] = gt[k];
+    tab = reinterpret_cast<const T4*>(st);
+  } else {
+    tab = reinterpret_cast<const T4*>(gtab);
+  }
+  for (int q = threadIdx.x; q < P.Q; q += blockDim.x) {
+    zq[q] = (T)gl_zeta[q];
+    wq[q] = (T)gl_w[q];
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < nnz; e += nwarps) {
+    // row of entry e: last r with row_ptr[r] <= e
+    int64_t lo = 0, hi = n_rows;
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (row_ptr[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int64_t i = lo;
+    const int32_t j = col[e];
+    if (P.symmetric && j < i) continue;
+    const double si = rs[i], sj = s[j];
+    const double dx = rux[i] - ux[j], dy = ruy[i] - uy[j], dz = ruz[i] - uz[j];
+    const double chord2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const T a = (T)(si * P.inv_L0), b = (T)(sj * P.inv_L0), c2 = (T)chord2;
+    // this lane's nodes on sightline j
+    T tp[KPL], ctp[KPL], wp[KPL];
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) {
+      int q = lane + 32 * k;
+      bool ok = q < P.Q;
+      tp[k] = ok ? b * zq[q] : (T)0;
+      ctp[k] = c2 * tp[k];
+      wp[k] = ok ? wq[q] : (T)0;
+    }
+    T acc = 0;
+    for (int q = 0; q < P.Q; ++q) {
+      const T t = a * zq[q];
+      T inner = 0;
+#pragma unroll
+      for (int k = 0; k < KPL; ++k) {
+        T d = t - tp[k];
+        T x = d * d + t * ctp[k];
+        T gv;
+        if (sizeof(T) == 4)
+          gv = (T)g_lookup(reinterpret_cast<const float4*>(tab), tf, (float)x);
+        else
+          gv = (T)g_lookup(reinterpret_cast<const D4*>(tab), td, (double)x);
+        inner += wp[k] * gv;
+      }
+      acc += wq[q] * inner;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      double R = (double)acc;
+      double K = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
+      if (P.taper == GM_TAPER_WENDLAND) {
+        double ds = si - sj;
+        double d = sqrt(fma(ds, ds, si * sj * chord2));
+        K *= wendland(d * P.inv_cut);
+      }
+      if (!isfinite(K)) atomicOr(flags, kFlagNonFinite);
+      val[e] = (T)K;
+      if (P.symmetric && j == i) {
+        kdiag[i] = (double)(T)K;
+        prior_m[i] = P.log_rho_bar + log(si) -
+                     (P.form == GM_FORM_LOGNORMAL ? 0.5 * (double)(T)K : 0.5 * P.sigma2);
+      }
+    }
+  }
+}
+
+// Lower-triangle entries copy their transpose (rows are sorted).
+template <typename T>
+__global__ void k_mirror(int64_t n, const int64_t* __restrict__ row_ptr,
+                         const int32_t* __restrict__ col, int64_t nnz, T* __restrict__ val) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (row_ptr[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int32_t i = (int32_t)lo, j = col[e];
+    if (j >= i) continue;
+    int64_t a = row_ptr[j], b = row_ptr[j + 1];  // search i in row j
+    while (b - a > 1) {
+      int64_t mid = (a + b) >> 1;
+      if (col[mid] <= i) a = mid; else b = mid;
+    }
+    val[e] = val[a];
+  }
+}
+
+// Self-covariance k_qq of query points (FP64, same rule as the diagonal).
+template <typename T, int KPL>
+__global__ void k_self_quad(QuadParams P, int64_t n_rows, const double* __restrict__ rs,
+                            const double* __restrict__ gl_zeta, const double* __restrict__ gl_w,
+                            const void* __restrict__ gtab, TabF32 tf, TabF64 td,
+                            double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n_rows; r += nwarps) {
+    const T a = (T)(rs[r] * P.inv_L0);
+    T tp[KPL], wp[KPL];
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) {
+      int q = lane + 32 * k;
+      bool ok = q < P.Q;
+      tp[k] = ok ? a * (T)gl_zeta[q] : (T)0;
+      wp[k] = ok ? (T)gl_w[q] : (T)0;
+    }
+    T acc = 0;
+    for (int q = 0; q < P.Q; ++q) {
+      const T t = a * (T)gl_zeta[q];
+      T inner = 0;
+#pragma unroll
+      for (int k = 0; k < KPL; ++k) {
+        T d = t - tp[k];
+        T x = d * d;
+        T gv;
+        if (sizeof(T) == 4)
+          gv = (T)g_lookup(reinterpret_cast<const float4*>(gtab), tf, (float)x);
+        else
+          gv = (T)g_lookup(reinterpret_cast<const D4*>(gtab), td, (double)x);
+        inner += wp[k] * gv;
+      }
+      acc += (T)gl_w[q] * inner;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      double R = (double)acc;
+      double K = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
+      out[r] = (double)(T)K;
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side
+static TabF32 tab_f32() {
+  TabF32 t;
+  float xmin = ldexpf(1.0f, kTabF32.emin);
+  t.base = *reinterpret_cast<int*>(&xmin);
+  t.shift = 23 - kTabF32.m;
+  t.last = kTabF32.n_real();
+  t.xmin = xmin;
+  return t;
+}
+
+static TabF64 tab_f64() {
+  TabF64 t;
+  double xmin = std::ldexp(1.0, kTabF64.emin);
+  long long bits = *reinterpret_cast<long long*>(&xmin);
+  t.base = (int)(bits >> 32);
+  t.shift = 20 - kTabF64.m;
+  t.last = kTabF64.n_real();
+  t.xmin = xmin;
+  return t;
+}
+
+static const TableGeom& tab_geom(const gm_ctx* c) {
+  return c->cfg.precision == GM_PREC_FP32 ? kTabF32 : kTabF64;
+}
+
+gm_status phi_points_init(gm_ctx* c) {
+  const TableGeom& g = tab_geom(c);
+  c->phi_pts = (double*)dev_alloc(c, g.n_pts() * sizeof(double));
+  size_t tb = (size_t)(g.n_real() + 1) * (c->cfg.precision == GM_PREC_FP32 ? 16 : 32);
+  c->gtab = dev_alloc(c, tb);
+  if (!c->phi_pts || !c->gtab) return set_error(c, GM_E_NOMEM, "phi table");
+  const double cnorm = std::pow(2.0, 2.0 / 3.0) / std::tgamma(1.0 / 3.0);
+  int blocks = (int)std::min<int64_t>(ceil_div(g.n_pts(), 128), 4 * sm_count(c));
+  GM_PROF(c, "k_phi_points");
+  k_phi_points<<<blocks, 128, 0, c->stream>>>(g, cnorm, c->phi_pts);
+  GM_LAUNCH_CHECK(c);
+  c->gtab_sigma2 = -1;
+  return GM_OK;
+}
+
+gm_status gtab_update(gm_ctx* c) {
+  if (c->gtab_sigma2 == c->cfg.sigma2 && c->gtab_form == c->cfg.form) return GM_OK;
+  const TableGeom& g = tab_geom(c);
+  int blocks = (int)std::min<int64_t>(ceil_div(g.n_real() + 1, 256), 4 * sm_count(c));
+  GM_PROF(c, "k_gtab");
+  if (c->cfg.precision == GM_PREC_FP32)
+    k_gtab<float4><<<blocks, 256, 0, c->stream>>>(g, c->phi_pts, c->cfg.sigma2, c->cfg.form,
+                                                  (float4*)c->gtab);
+  else
+    k_gtab<D4><<<blocks, 256, 0, c->stream>>>(g, c->phi_pts, c->cfg.sigma2, c->cfg.form,
+                                                   (D4*)c->gtab);
+  GM_LAUNCH_CHECK(c);
+  c->gtab_sigma2 = c->cfg.sigma2;
+  c->gtab_form = c->cfg.form;
+  return GM_OK;
+}
+
+static QuadParams quad_params(const gm_ctx* c, bool symmetric) {
+  QuadParams P;
+  P.inv_L0 = 1.0 / c->cfg.outer_scale_pc;
+  P.inv_cut = 1.0 / c->cfg.cutoff_pc;
+  P.log_rho_bar = std::log(c->cfg.rho_bar);
+  P.sigma2 = c->cfg.sigma2;
+  P.Q = c->cfg.n_nodes;
+  P.form = c->cfg.form;
+  P.taper = c->cfg.taper;
+  P.symmetric = symmetric ? 1 : 0;
+  return P;
+}
+
+template <typename T, int KPL>
+static void launch_pair(gm_ctx* c, const QuadParams& P, int64_t n_rows, const double* rs,
+                        const double* rux, const double* ruy, const double* ruz,
+                        const int64_t* row_ptr, const int32_t* col, int64_t nnz, void* val) {
+  size_t smem = 2 * kMaxNodes * sizeof(T);
+  if (sizeof(T) == 4) smem += (size_t)(kTabF32.n_real() + 1) * sizeof(float4);
+  auto kern = k_pair_quad<T, KPL>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  int blocks = std::max(1, per_sm) * sm_count(c);
+  blocks = (int)std::min<int64_t>(blocks, std::max<int64_t>(1, ceil_div(nnz * 32, 256)));
+  GM_PROF(c, "k_pair_quad");
+  kern<<<blocks, 256, smem, c->stream>>>(P, n_rows, rs, rux, ruy, ruz, c->s, c->ux, c->uy, c->uz,
+                                         row_ptr, col, nnz, (T*)val, c->gl_zeta, c->gl_w, c->gtab,
+                                         tab_f32(), tab_f64(), c->kdiag, c->prior_m, c->d_flags);
+}
+
+gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, const double* rux,
+                          const double* ruy, const double* ruz, const int64_t* row_ptr,
+                          const int32_t* col, int64_t nnz, void* val, bool symmetric) {
+  if (nnz == 0) return GM_OK;
+  gm_status st = gtab_update(c);
+  if (st != GM_OK) return st;
+  QuadParams P = quad_params(c, symmetric);
+  const int Q = c->cfg.n_nodes;
+  const bool f32 = c->cfg.precision == GM_PREC_FP32;
+  if (Q <= 32) {
+    if (f32) launch_pair<float, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+    else launch_pair<double, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+  } else if (Q <= 64) {
+    if (f32) launch_pair<float, 2>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+    else launch_pair<double, 2>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+  } else {
+    if (f32) launch_pair<float, 4>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+    else launch_pair<double, 4>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+  }
+  GM_LAUNCH_CHECK(c);
+  if (symmetric) {
+    int blocks = (int)std::min<int64_t>(ceil_div(nnz, 256), 16 * sm_count(c));
+    GM_PROF(c, "k_mirror");
+    if (f32) k_mirror<float><<<blocks, 256, 0, c->stream>>>(n_rows, row_ptr, col, nnz, (float*)val);
+    else k_mirror<double><<<blocks, 256, 0, c->stream>>>(n_rows, row_ptr, col, nnz, (double*)val);
+    GM_LAUNCH_CHECK(c);
+  }
+  return GM_OK;
+}
+
+gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* kss) {
+  if (n_rows == 0) return GM_OK;
+  gm_status st = gtab_update(c);
+  if (st != GM_OK) return st;
+  QuadParams P = quad_params(c, false);
+  const int Q = c->cfg.n_nodes;
+  const bool f32 = c->cfg.precision == GM_PREC_FP32;
+  int blocks = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 8 * sm_count(c));
+#define GM_SELF(T, K)                                                                     \
+  k_self_quad<T, K><<<blocks, 256, 0, c->stream>>>(P, n_rows, rs, c->gl_zeta, c->gl_w, \
+                                                    c->gtab, tab_f32(), tab_f64(), kss)
+  GM_PROF(c, "k_self_quad");
+  if (Q <= 32) {
+    if (f32) GM_SELF(float, 1); else GM_SELF(double, 1);
+  } else if (Q <= 64) {
+    if (f32) GM_SELF(float, 2); else GM_SELF(double, 2);
+  } else {
+    if (f32) GM_SELF(float, 4); else GM_SELF(double, 4);
+  }
+#undef GM_SELF
+  GM_LAUNCH_CHECK(c);
+  return GM_OK;
+}
+
+}  // namespace gm

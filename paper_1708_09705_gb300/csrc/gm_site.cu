@@ -1,0 +1,169 @@
+// EP site update, one thread per star, FP64 (App. A.2).
+//
+// For star i with posterior marginal N(mu_i, Sigma_ii) and site (tau_i, nu_i):
+//   cavity (eq. cavity):  tau_c = 1/Sigma_ii - tau_i, nu_c = mu_i/Sigma_ii - nu_i,
+//     with the cavity variance floored (Sect. 5); tau_c <= 0 skips the star;
+//   tilted (eq. tilted):  N(a; mu_c, v_c) * L_i(a), L_i the star's likelihood;
+//   moment matching (eq. KL1'): mean mh and variance vh of the tilted give
+//     tau_new = 1/vh - tau_c, nu_new = mh/vh - nu_c;
+//   damped replacement; an update with tau_new < 0 is skipped.
+// Gaussian-in-ln-A likelihood: the tilted is Gaussian (closed form).
+// Gaussian-in-A likelihood: mode and curvature of the tilted log-density by
+// safeguarded Newton ascent, then a 64-node Gauss-Hermite rule centred at the
+// mode and scaled by the curvature.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+struct SiteParams {
+  double damping;
+  double vc_floor;
+  int lik;
+};
+
+__device__ __forceinline__ double log_tilted(double a, double mc, double vc, double obs,
+                                             double s2) {
+  double ea = exp(a);
+  double u = a - mc, w = obs - ea;
+  return -0.5 * u * u / vc - 0.5 * w * w / s2;
+}
+
+__device__ void tilted_gauss_in_a(double mc, double vc, double obs, double s2,
+                                  const double* __restrict__ ghx, const double* __restrict__ ghw,
+                                  double* mh, double* vh) {
+  double a;
+  if (obs > 0) {
+    double aL = log(obs), vL = s2 / (obs * obs);
+    a = (mc / vc + aL / vL) / (1.0 / vc + 1.0 / vL);
+  } else {
+    a = mc;
+  }
+  for (int it = 0; it < 100; ++it) {
+    double ea = exp(a);
+    double gr = -(a - mc) / vc + (obs - ea) * ea / s2;
+    double H = -1.0 / vc + (obs * ea - 2.0 * ea * ea) / s2;
+    double step = H < 0 ? -gr / H : gr * vc;
+    step = fmax(-1.0, fmin(1.0, step));
+    double h0 = log_tilted(a, mc, vc, obs, s2);
+    int k = 0;
+    while (log_tilted(a + step, mc, vc, obs, s2) < h0 && k < 60) {
+      step *= 0.5;
+      ++k;
+    }
+    a += step;
+    if (fabs(step) <= 1e-14 * (1.0 + fabs(a))) break;
+  }
+  double ea = exp(a);
+  double H = -1.0 / vc + (obs * ea - 2.0 * ea * ea) / s2;
+  double sh = H < 0 ? 1.0 / sqrt(-H) : sqrt(vc);
+  double h0 = log_tilted(a, mc, vc, obs, s2);
+  const double sc = 1.4142135623730951 * sh;
+  // moments about the mode, then shifted
+  double S0 = 0, S1 = 0, S2 = 0;
+  for (int k = 0; k < kGH; ++k) {
+    double y = sc * ghx[k];
+    double wk = ghw[k] * exp(log_tilted(a + y, mc, vc, obs, s2) - h0);
+    S0 += wk;
+    S1 += wk * y;
+    S2 += wk * y * y;
+  }
+  double m1 = S1 / S0;
+  *mh = a + m1;
+  *vh = S2 / S0 - m1 * m1;
+}
+
+__global__ void k_site_update(int64_t n, SiteParams P, const double* __restrict__ mu,
+                              const double* __restrict__ var, const double* __restrict__ obs,
+                              const double* __restrict__ sig, double* __restrict__ tau,
+                              double* __restrict__ nu, const double* __restrict__ gh_x,
+                              const double* __restrict__ gh_w, double* __restrict__ part_delta,
+                              unsigned long long* __restrict__ skipped,
+                              unsigned* __restrict__ flags) {
+  __shared__ double ghx[kGH], ghw[kGH];
+  __shared__ double sh[32];
+  for (int k = threadIdx.x; k < kGH; k += blockDim.x) {
+    ghx[k] = gh_x[k];
+    ghw[k] = gh_w[k];
+  }
+  __syncthreads();
+  double dmax = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double t0 = tau[i], n0 = nu[i];
+    const double S = var[i], m = mu[i];
+    double tc = 1.0 / S - t0;
+    double ncv = m / S - n0;
+    bool skip = !(tc > 0) || !isfinite(tc) || !isfinite(ncv);
+    double t_new = t0, n_new = n0;
+    if (!skip) {
+      const double mc = ncv / tc;
+      const double vc = fmax(1.0 / tc, P.vc_floor);
+      tc = 1.0 / vc;
+      ncv = mc / vc;
+      const double s2 = sig[i] * sig[i];
+      double mh, vh;
+      if (P.lik == GM_LIK_GAUSS_IN_LNA) {
+        vh = 1.0 / (1.0 / vc + 1.0 / s2);
+        mh = vh * (mc / vc + obs[i] / s2);
+      } else {
+        tilted_gauss_in_a(mc, vc, obs[i], s2, ghx, ghw, &mh, &vh);
+      }
+      t_new = 1.0 / vh - tc;
+      n_new = mh / vh - ncv;
+      if (!(t_new >= 0) || !isfinite(n_new) || !isfinite(t_new)) skip = true;
+    }
+    if (skip) {
+      atomicAdd(skipped, 1ull);
+      continue;
+    }
+    const double tn = (1.0 - P.damping) * t0 + P.damping * t_new;
+    const double nn = (1.0 - P.damping) * n0 + P.damping * n_new;
+    tau[i] = tn;
+    nu[i] = nn;
+    double dt = fabs(tn - t0) / (1.0 + fabs(t0));
+    double dn = fabs(nn - n0) / (1.0 + fabs(n0));
+    dmax = fmax(dmax, fmax(dt, dn));
+  }
+  // block max (fixed order)
+  for (int off = 16; off > 0; off >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, sh[w]);
+    if (!isfinite(v)) atomicOr(flags, kFlagNonFinite);
+    part_delta[blockIdx.x] = v;
+  }
+}
+
+gm_status site_update(gm_ctx* c, double* max_delta, int64_t* skipped) {
+  const int64_t n = c->n;
+  cudaStream_t st = c->stream;
+  const int G = (int)std::min<int64_t>(ceil_div(n, 128), 4 * sm_count(c));
+  double* part = (double*)dev_alloc(c, (G + 1) * sizeof(double) + sizeof(unsigned long long));
+  if (!part) return set_error(c, GM_E_NOMEM, "site partials");
+  unsigned long long* cnt = (unsigned long long*)(part + G);
+  GM_CUDA_CHECK(c, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+  SiteParams P{c->cfg.damping, c->cfg.vc_floor, c->cfg.likelihood};
+  GM_PROF(c, "k_site_update");
+  k_site_update<<<G, 128, 0, st>>>(n, P, c->mu, c->var, c->obs, c->obs_sigma, c->tau, c->nu,
+                                   c->gh_x, c->gh_wx, part, cnt, c->d_flags);
+  GM_LAUNCH_CHECK(c);
+  double* hp = (double*)c->h_pinned;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(hp, part, (G + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  double m = 0;
+  for (int k = 0; k < G; ++k) m = std::fmax(m, hp[k]);
+  unsigned long long sk;
+  std::memcpy(&sk, hp + G, sizeof(sk));
+  *max_delta = m;
+  *skipped = (int64_t)sk;
+  dev_free_now(c, part, (G + 1) * sizeof(double) + sizeof(unsigned long long));
+  return GM_OK;
+}
+
+}  // namespace gm
