@@ -86,7 +86,10 @@ typedef struct {
   double cg_tol;          /* CG stops at ||r|| <= cg_tol ||b|| (> 0); FP32
                              variance panels use max(cg_tol, 1e-5)            */
   int32_t rhs_panel;      /* right-hand sides per variance panel, 0 = auto    */
-  int32_t reserved;
+  int32_t warm_start;     /* 1: start each sweep's variance CG from the
+                             previous sweep's solutions (same results within
+                             cg_tol; resume from saved sites is then equal
+                             within cg_tol, not bit for bit); 0: cold start   */
 } gm_config;
 
 /* Device memory hooks.  When given, every device allocation of the context
@@ -114,7 +117,8 @@ typedef struct {
 
 /* Fills *cfg with defaults: sigma2 1, L0 20 pc, rho_bar 1e-3 mag/pc, cutoff
  * 3 L0, 32 nodes, lognormal form, Wendland taper, FP64, Gaussian-in-A
- * likelihood, damping 1, cavity floor 1e-8, CG tol 1e-10 / 2000 iterations. */
+ * likelihood, damping 1, cavity floor 1e-8, CG tol 1e-10 / 2000 iterations,
+ * automatic panel width, warm-started variance solves. */
 void gm_config_default(gm_config* cfg);
 
 /* Creates a context for n >= 1 stars (Sect. 3: observed (l, b), distance s

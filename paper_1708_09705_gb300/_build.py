@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libgmead.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["gm_api.cu", "gm_geometry.cu", "gm_quad.cu", "gm_solve.cu", "gm_site.cu"]
+CU_SOURCES = ["gm_api.cu", "gm_geometry.cu", "gm_quad.cu", "gm_solve.cu", "gm_site.cu",
+              "gm_tiles.cu"]
 CPP_SOURCES = ["gm_rules.cpp"]
 
 

@@ -75,6 +75,7 @@ static cudaEvent_t prof_event(gm_ctx* c) {
 }
 
 void prof_begin(gm_ctx* c, const char* name) {
+  if (c->prof_pending) prof_end(c);  // two launches before one check
   cudaEvent_t a = prof_event(c), b = prof_event(c);
   if (!a || !b) return;
   cudaEventRecord(a, c->stream);
@@ -216,7 +217,7 @@ static gm_status validate(const gm_config* f) {
     return GM_E_INVAL;
   if (!(f->damping > 0 && f->damping <= 1)) return GM_E_INVAL;
   if (!(f->vc_floor >= 0) || !(f->cg_tol > 0) || f->cg_max_iter <= 0) return GM_E_INVAL;
-  if (f->rhs_panel < 0) return GM_E_INVAL;
+  if (f->rhs_panel < 0 || (f->warm_start != 0 && f->warm_start != 1)) return GM_E_INVAL;
   return GM_OK;
 }
 
@@ -243,6 +244,7 @@ void gm_config_default(gm_config* f) {
   f->vc_floor = 1e-8;
   f->cg_tol = 1e-10;
   f->rhs_panel = 0;
+  f->warm_start = 1;
 }
 
 const char* gm_status_str(gm_status s) {
@@ -375,6 +377,10 @@ gm_status gm_build_cov(gm_ctx* c, int64_t* nnz_out) {
     return set_error(c, GM_E_NOMEM, "CSR values");
   c->val = c->val_buf.p;
   st = pair_quadrature(c, c->n, c->s, c->ux, c->uy, c->uz, c->row_ptr, c->col, c->nnz, c->val, true);
+  if (st != GM_OK) return st;
+  c->t_nblk = 0;
+  c->warm_R = 0;
+  st = tiles_build(c);
   if (st != GM_OK) return st;
   st = read_flags(c);
   if (st != GM_OK) return st;
@@ -509,6 +515,7 @@ gm_status gm_set_sites(gm_ctx* c, const double* tau, const double* nu) {
   GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
   dev_free_now(c, tmp, 2 * nb);
   c->post_valid = false;
+  c->warm_R = 0;
   return GM_OK;
 }
 
@@ -596,6 +603,7 @@ gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, co
   if (st != GM_OK) return st;
   int64_t it = 0;
   double res = 0;
+  c->warm_R = 0;  // the query panels overwrite the saved star solutions
   st = panel_variances(c, nq, qptr, (const int32_t*)qcol.p, qval, kss, var, &it, &res);
   if (st == GM_OK) st = read_flags(c);
   if (st != GM_OK) return st;

@@ -290,6 +290,42 @@ static Grid grid_of(const gm_ctx* c) {
   return g;
 }
 
+gm_status sort_u64(gm_ctx* c, unsigned long long* keys, int64_t n_pad) {
+  cudaStream_t st = c->stream;
+  const int kb = (int)std::min<int64_t>(ceil_div(n_pad, 256), 16 * sm_count(c));
+  for (int64_t k = 2; k <= n_pad; k <<= 1) {
+    int64_t j = k >> 1;
+    for (; j >= 1024; j >>= 1) {
+      GM_PROF(c, "k_bitonic_global");
+      k_bitonic_global<<<kb, 256, 0, st>>>(keys, n_pad, k, j);
+      GM_LAUNCH_CHECK(c);
+    }
+    GM_PROF(c, "k_bitonic_shared");
+    k_bitonic_shared<<<(unsigned)(n_pad / 1024), 512, 0, st>>>(keys, n_pad, k, j);
+    GM_LAUNCH_CHECK(c);
+  }
+  return GM_OK;
+}
+
+gm_status scan_i64(gm_ctx* c, const int64_t* in, int64_t* out, int64_t n) {
+  cudaStream_t st = c->stream;
+  const int64_t n_tiles = ceil_div(n + 1, 1024);
+  int64_t* sums = (int64_t*)dev_alloc(c, (n_tiles + 1) * sizeof(int64_t));
+  if (!sums) return set_error(c, GM_E_NOMEM, "scan partials");
+  GM_PROF(c, "k_scan_tiles");
+  k_scan_tiles<<<(unsigned)ceil_div(n, 1024), 1024, 0, st>>>(n, in, out, sums);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_scan_sums");
+  k_scan_sums<<<1, 1024, 0, st>>>(ceil_div(n, 1024), sums, sums + n_tiles);
+  GM_LAUNCH_CHECK(c);
+  const int ab = (int)std::min<int64_t>(ceil_div(n + 1, 256), 8 * sm_count(c));
+  GM_PROF(c, "k_scan_add");
+  k_scan_add<<<ab, 256, 0, st>>>(n, out, sums, sums + n_tiles);
+  GM_LAUNCH_CHECK(c);
+  dev_free_now(c, sums, (n_tiles + 1) * sizeof(int64_t));
+  return GM_OK;
+}
+
 gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const double* s,
                         const double* obs, const double* sig) {
   const int64_t n = c->n;
@@ -345,16 +381,9 @@ gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const doubl
   GM_PROF(c, "k_cell_keys");
   k_cell_keys<<<kb, 256, 0, st>>>(n, n_pad, g, s, ux_in, uy_in, uz_in, keys);
   GM_LAUNCH_CHECK(c);
-  for (int64_t k = 2; k <= n_pad; k <<= 1) {
-    int64_t j = k >> 1;
-    for (; j >= 1024; j >>= 1) {
-      GM_PROF(c, "k_bitonic_global");
-      k_bitonic_global<<<kb, 256, 0, st>>>(keys, n_pad, k, j);
-      GM_LAUNCH_CHECK(c);
-    }
-    GM_PROF(c, "k_bitonic_shared");
-    k_bitonic_shared<<<(unsigned)(n_pad / 1024), 512, 0, st>>>(keys, n_pad, k, j);
-    GM_LAUNCH_CHECK(c);
+  {
+    gm_status sst = sort_u64(c, keys, n_pad);
+    if (sst != GM_OK) return sst;
   }
   GM_PROF(c, "k_apply_perm");
   k_apply_perm<<<blocks, 256, 0, st>>>(n, keys, s, ux_in, uy_in, uz_in, obs, sig, c->perm, c->s,
@@ -390,24 +419,16 @@ gm_status neighbour_csr(gm_ctx* c, int64_t n_rows, const double* rs, const doubl
   Grid g = grid_of(c);
   const double cut2 = c->cfg.cutoff_pc * c->cfg.cutoff_pc;
   int64_t* counts = (int64_t*)dev_alloc(c, (n_rows + 1) * sizeof(int64_t));
-  int64_t n_tiles = ceil_div(n_rows + 1, 1024);
-  int64_t* sums = (int64_t*)dev_alloc(c, (n_tiles + 1) * sizeof(int64_t));
-  if (!counts || !sums) return set_error(c, GM_E_NOMEM, "neighbour counts");
+  if (!counts) return set_error(c, GM_E_NOMEM, "neighbour counts");
   const int wb = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 32 * sms);
   GM_PROF(c, "k_neighbours");
   k_neighbours<false><<<wb, 256, 0, st>>>(n_rows, g, cut2, rs, rux, ruy, ruz, c->s, c->ux, c->uy,
                                           c->uz, c->cell_start, counts, nullptr, nullptr, self);
   GM_LAUNCH_CHECK(c);
-  GM_PROF(c, "k_scan_tiles");
-  k_scan_tiles<<<(unsigned)ceil_div(n_rows, 1024), 1024, 0, st>>>(n_rows, counts, row_ptr, sums);
-  GM_LAUNCH_CHECK(c);
-  GM_PROF(c, "k_scan_sums");
-  k_scan_sums<<<1, 1024, 0, st>>>(ceil_div(n_rows, 1024), sums, sums + n_tiles);
-  GM_LAUNCH_CHECK(c);
-  const int ab = (int)std::min<int64_t>(ceil_div(n_rows + 1, 256), 8 * sms);
-  GM_PROF(c, "k_scan_add");
-  k_scan_add<<<ab, 256, 0, st>>>(n_rows, row_ptr, sums, sums + n_tiles);
-  GM_LAUNCH_CHECK(c);
+  {
+    gm_status sst = scan_i64(c, counts, row_ptr, n_rows);
+    if (sst != GM_OK) return sst;
+  }
   int64_t nnz = 0;
   GM_CUDA_CHECK(c, cudaMemcpyAsync(&nnz, row_ptr + n_rows, sizeof(int64_t),
                                    cudaMemcpyDeviceToHost, st));
@@ -421,7 +442,6 @@ gm_status neighbour_csr(gm_ctx* c, int64_t n_rows, const double* rs, const doubl
                                          diag_pos, self);
   GM_LAUNCH_CHECK(c);
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
-  dev_free_now(c, sums, (n_tiles + 1) * sizeof(int64_t));
   dev_free_now(c, counts, (n_rows + 1) * sizeof(int64_t));
   *nnz_out = nnz;
   return GM_OK;

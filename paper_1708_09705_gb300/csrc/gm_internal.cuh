@@ -91,6 +91,10 @@ struct gm_ctx {
   void* val = nullptr;         // double (FP64) or float (FP32)
   gm::Buffer col_buf, val_buf;
   int64_t* diag_pos = nullptr;
+  // row-block tiles of K (FP32 mode): 32-row blocks, union columns, values
+  gm::Buffer t_bptr, t_ucol, t_val;
+  int64_t t_nblk = 0;
+  int64_t t_union = 0;
   double* kdiag = nullptr;
   double* prior_m = nullptr;
 
@@ -111,6 +115,7 @@ struct gm_ctx {
   double* var = nullptr;
   double* alpha = nullptr;     // mu = m + K alpha
   bool post_valid = false;
+  int64_t warm_R = 0;          // panel width of saved variance solutions (0 = none)
 
   // ---- status flags and pinned readback
   unsigned* d_flags = nullptr;
@@ -187,6 +192,10 @@ void gauss_hermite(int n, double* x, double* w_times_expx2);
 // ---------------------------------------------------------------- stages
 gm_status geometry_init(gm_ctx* c, const double* l, const double* b,
                         const double* s, const double* obs, const double* sig);
+// Ascending bitonic sort of n_pad (a power of two >= 1024) 64-bit keys.
+gm_status sort_u64(gm_ctx* c, unsigned long long* keys, int64_t n_pad);
+// Exclusive scan of n counts: out[0..n], out[n] = total.
+gm_status scan_i64(gm_ctx* c, const int64_t* in, int64_t* out, int64_t n);
 gm_status unit_vectors(gm_ctx* c, int64_t n, const double* l, const double* b, double* ux,
                        double* uy, double* uz);
 // Rows = the given positions (internal stars or queries), columns = stars.
@@ -208,6 +217,11 @@ gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs,
                           void* val, bool symmetric);
 // Diagonal-only quadrature (query self-covariance) into kss (FP64).
 gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* kss);
+
+// Row-block tiles of K for the FP32 variance panels (gm_tiles.cu).
+gm_status tiles_build(gm_ctx* c);
+gm_status panel_spmm_tiled(gm_ctx* c, int64_t n, int R, int nbx, const float* dv, const float* P,
+                           const float* PD, float* Q, double* part_pq);
 
 // Posterior of the current sites: mu, var, alpha (gm_solve.cu).
 gm_status refresh_posterior(gm_ctx* c);

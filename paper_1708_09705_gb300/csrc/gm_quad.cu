@@ -66,11 +66,13 @@ __global__ void k_phi_points(TableGeom g, double cnorm, double* __restrict__ out
   }
 }
 
-// Cubic through g at the four equispaced nodes of each segment, as
-// coefficients of the local offset d = x - x_lo (Newton forward differences).
+// Cubic through g at the four equispaced nodes of each segment (Newton
+// forward differences).  FP32 tables hold coefficients of the normalised
+// offset v = (x - x_lo) / H in [0, 1) (all O(1)); FP64 tables hold
+// coefficients of the absolute offset d = x - x_lo (its range covers 1/H^3).
 template <typename T4>
 __global__ void k_gtab(TableGeom g, const double* __restrict__ phi, double sigma2, int form,
-                       T4* __restrict__ tab) {
+                       int normalised, T4* __restrict__ tab) {
   const int nr = g.n_real();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= nr; k += gridDim.x * blockDim.x) {
     T4 o;
@@ -83,9 +85,10 @@ __global__ void k_gtab(TableGeom g, const double* __restrict__ phi, double sigma
         v[q] = form == GM_FORM_LOGNORMAL ? expm1(c) : c;
       }
       double d1 = v[1] - v[0], d2 = v[2] - 2 * v[1] + v[0], d3 = v[3] - 3 * v[2] + 3 * v[1] - v[0];
+      // p(w) = c0 + c1 w + c2 w^2 + c3 w^3 with w = 3 v
       double c0 = v[0], c1 = d1 - 0.5 * d2 + d3 / 3.0, c2 = 0.5 * d2 - 0.5 * d3, c3 = d3 / 6.0;
       double H = ldexp(1.0 / (double)(1 << g.m), g.emin + (k >> g.m));
-      double sc = 3.0 / H;
+      double sc = normalised ? 3.0 : 3.0 / H;
       o.x = c0;
       o.y = c1 * sc;
       o.z = c2 * sc * sc;
@@ -109,14 +112,15 @@ struct TabF64 {
   double xmin;
 };
 
+// v = position of x inside its segment, in [0, 1): the mantissa bits below
+// the segment index, placed in the mantissa of a float in [1, 2), minus 1.
 __device__ __forceinline__ float g_lookup(const float4* __restrict__ tab, const TabF32& t, float x) {
   x = fmaxf(x, t.xmin);
   int bits = __float_as_int(x);
   int k = min((bits - t.base) >> t.shift, t.last);
-  float xlo = __int_as_float(bits & ~((1 << t.shift) - 1));
-  float d = x - xlo;  // exact: x and xlo are within a factor 2
+  float v = __int_as_float(((bits << (23 - t.shift)) & 0x007fffff) | 0x3f800000) - 1.0f;
   float4 c = tab[k];
-  return fmaf(d, fmaf(d, fmaf(d, c.w, c.z), c.y), c.x);
+  return fmaf(v, fmaf(v, fmaf(v, c.w, c.z), c.y), c.x);
 }
 
 __device__ __forceinline__ double g_lookup(const D4* __restrict__ tab, const TabF64& t,
@@ -360,10 +364,10 @@ gm_status gtab_update(gm_ctx* c) {
   int blocks = (int)std::min<int64_t>(ceil_div(g.n_real() + 1, 256), 4 * sm_count(c));
   GM_PROF(c, "k_gtab");
   if (c->cfg.precision == GM_PREC_FP32)
-    k_gtab<float4><<<blocks, 256, 0, c->stream>>>(g, c->phi_pts, c->cfg.sigma2, c->cfg.form,
+    k_gtab<float4><<<blocks, 256, 0, c->stream>>>(g, c->phi_pts, c->cfg.sigma2, c->cfg.form, 1,
                                                   (float4*)c->gtab);
   else
-    k_gtab<D4><<<blocks, 256, 0, c->stream>>>(g, c->phi_pts, c->cfg.sigma2, c->cfg.form,
+    k_gtab<D4><<<blocks, 256, 0, c->stream>>>(g, c->phi_pts, c->cfg.sigma2, c->cfg.form, 0,
                                                    (D4*)c->gtab);
   GM_LAUNCH_CHECK(c);
   c->gtab_sigma2 = c->cfg.sigma2;

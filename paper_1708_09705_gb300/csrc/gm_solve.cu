@@ -296,18 +296,33 @@ __global__ void __launch_bounds__(kBT) k_refine_resid(int64_t n, const double* _
 // (warp-strided), y over 32-column chunks; lane = column within the chunk.
 // Column partials: part[(bx) * R + c].
 
-// Right-hand sides v_c = d o k_{r0+c} scattered from CSR rows (rows of K for
-// the stars, query rows for prediction); x = 0; p = M^-1 v; partial rz, bb.
+// Right-hand sides scattered from CSR rows (rows of K for the stars, query
+// rows for prediction).  Column c solves for row r = r0 + c:
+//   v_r = d o k_r                  (k_rr - v_r^T B^-1 v_r = Sigma_rr), or, for
+//   e_r when `unit` marks r        ((B^-1)_rr = y_r, Sigma_rr = (1 - y_r) / tau_r).
+// The unit form is used for stars whose own site dominates (tau_r K_rr >= 1):
+// there the cavity precision tau_r y_r / (1 - y_r) keeps the relative accuracy
+// of y_r, whereas 1/Sigma_rr - tau_r would cancel.
+__device__ __forceinline__ bool unit_rhs(const double* __restrict__ tau,
+                                         const double* __restrict__ kd, int64_t r) {
+  return tau != nullptr && tau[r] * kd[r] >= 1.0;
+}
+
 template <typename TA, typename TV>
 __global__ void k_panel_rhs(int64_t r0, int64_t n_cols, int R, const int64_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col, const TA* __restrict__ val,
-                            const TV* __restrict__ dv, TV* __restrict__ Rr) {
+                            const TV* __restrict__ dv, const double* __restrict__ tau,
+                            const double* __restrict__ kd, TV* __restrict__ Rr) {
   // one warp per right-hand side
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = warp; c < n_cols; c += nw) {
     const int64_t r = r0 + c;
+    if (unit_rhs(tau, kd, r)) {
+      if (lane == 0) Rr[r * R + c] = (TV)1;
+      continue;
+    }
     for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
       int32_t j = col[e];
       Rr[(int64_t)j * R + c] = dv[j] * (TV)val[e];
@@ -337,6 +352,60 @@ __global__ void __launch_bounds__(kBT) k_panel_init(int64_t n, int R, const TV* 
     PD[k] = dv[i] * zi;
     rz += (double)ri * (double)zi;
     bb += (double)ri * (double)ri;
+  }
+  sh_rz[wib][lane] = rz;
+  sh_bb[wib][lane] = bb;
+  __syncthreads();
+  if (wib == 0) {
+    double a = 0, b = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += sh_rz[k][lane];
+      b += sh_bb[k][lane];
+    }
+    part_rz[(int64_t)blockIdx.x * R + c] = a;
+    part_bb[(int64_t)blockIdx.x * R + c] = b;
+  }
+}
+
+// Warm start: PD = d o X (so that the panel product gives Q = B X).
+template <typename TV>
+__global__ void __launch_bounds__(kBT) k_panel_scale(int64_t n, int R, const TV* __restrict__ dv,
+                                                     const TV* __restrict__ X, TV* __restrict__ PD) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = blockIdx.y * 32 + lane;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = w; i < n; i += nw) {
+    int64_t k = i * R + c;
+    PD[k] = dv[i] * X[k];
+  }
+}
+
+// Warm start: with Rr = v (the right-hand sides) and Q = B X0, set the
+// residual Rr = v - Q, P = M^-1 Rr, PD = d o P; partial rz and ||v||^2.
+template <typename TV>
+__global__ void __launch_bounds__(kBT) k_panel_init_warm(int64_t n, int R, const TV* __restrict__ minv,
+                                                         const TV* __restrict__ dv,
+                                                         TV* __restrict__ Rr, const TV* __restrict__ Q,
+                                                         TV* __restrict__ P, TV* __restrict__ PD,
+                                                         double* __restrict__ part_rz,
+                                                         double* __restrict__ part_bb) {
+  __shared__ double sh_rz[8][32], sh_bb[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = blockIdx.y * 32 + lane;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double rz = 0, bb = 0;
+  for (int64_t i = w; i < n; i += nw) {
+    int64_t k = i * R + c;
+    TV v = Rr[k];
+    TV ri = v - Q[k];
+    TV zi = minv[i] * ri;
+    Rr[k] = ri;
+    P[k] = zi;
+    PD[k] = dv[i] * zi;
+    rz += (double)ri * (double)zi;
+    bb += (double)v * (double)v;
   }
   sh_rz[wib][lane] = rz;
   sh_bb[wib][lane] = bb;
@@ -519,27 +588,32 @@ __global__ void __launch_bounds__(kBT) k_panel_update2(int64_t n, int R, const T
   }
 }
 
-// var_r = k_rr - v_r^T y_r, v_r = d o k_r (row r of the rows-CSR); relative
-// residual of the column is reported through resid (max).
+// Sigma_rr from the solution column: k_rr - v_r^T y (v_r = d o k_r) or
+// (1 - y_r) / tau_r for unit right-hand sides.
 template <typename TA, typename TV>
 __global__ void k_panel_final(int64_t r0, int64_t n_cols, int R, const int64_t* __restrict__ row_ptr,
                               const int32_t* __restrict__ col, const TA* __restrict__ val,
                               const double* __restrict__ d64, const TV* __restrict__ X,
-                              const double* __restrict__ kdiag_rows, double* __restrict__ var_out,
-                              unsigned* __restrict__ flags) {
+                              const double* __restrict__ kdiag_rows, const double* __restrict__ tau,
+                              double* __restrict__ var_out, unsigned* __restrict__ flags) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = warp; c < n_cols; c += nw) {
     const int64_t r = r0 + c;
-    double acc = 0;
-    for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
-      int32_t j = col[e];
-      acc += d64[j] * (double)val[e] * (double)X[(int64_t)j * R + c];
+    double v;
+    if (unit_rhs(tau, kdiag_rows, r)) {
+      v = (1.0 - (double)X[r * R + c]) / tau[r];
+    } else {
+      double acc = 0;
+      for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
+        int32_t j = col[e];
+        acc += d64[j] * (double)val[e] * (double)X[(int64_t)j * R + c];
+      }
+      acc = warp_sum(acc);
+      v = kdiag_rows[r] - acc;
     }
-    acc = warp_sum(acc);
     if (lane == 0) {
-      double v = kdiag_rows[r] - acc;
       if (!isfinite(v)) atomicOr(flags, kFlagNonFinite);
       var_out[r] = v;
     }
@@ -704,10 +778,28 @@ static gm_status posterior_mean(gm_ctx* c, int64_t* iters, double* resid) {
   return GM_OK;
 }
 
+// Panel product Q = P + d o (K PD) with the tiled kernel when available.
+template <typename TA, typename TV>
+static gm_status panel_product(gm_ctx* c, int64_t n, int64_t R, int nbx, dim3 grid, const TV* dv,
+                               const TV* P, const TV* PD, TV* Q, double* pa) {
+  if (sizeof(TV) == 4 && c->t_nblk > 0)
+    return panel_spmm_tiled(c, n, (int)R, nbx, (const float*)dv, (const float*)P,
+                            (const float*)PD, (float*)Q, pa);
+  GM_PROF(c, "k_panel_spmm");
+  k_panel_spmm<TA, TV><<<grid, kBT, 0, c->stream>>>(n, (int)R, c->row_ptr, c->col,
+                                                    (const TA*)c->val, dv, P, PD, Q, pa);
+  GM_LAUNCH_CHECK(c);
+  return GM_OK;
+}
+
+// stars: the rows are the stars themselves (unit right-hand sides allowed,
+// and the solutions may seed the next call: warm start when the previous
+// call solved the stars in one panel of the same width).
 template <typename TA, typename TV>
 static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                         const void* val, const double* kdiag_rows, double* var_out,
-                        int64_t* iters_out, double* resid_out) {
+                        int64_t* iters_out, double* resid_out, bool stars) {
+  const bool warm = stars;
   Workspace& ws = W(c);
   const int64_t n = c->n;
   cudaStream_t st = c->stream;
@@ -751,23 +843,38 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     const int64_t ncols = std::min<int64_t>(R, n_rows - r0);
     GM_CUDA_CHECK(c, cudaMemsetAsync(Rr, 0, pbytes, st));
     GM_PROF(c, "k_panel_rhs");
-    k_panel_rhs<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col, (const TA*)val, dv, Rr);
+    k_panel_rhs<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col, (const TA*)val, dv,
+                                            warm ? c->tau : nullptr, kdiag_rows, Rr);
     GM_LAUNCH_CHECK(c);
-    GM_PROF(c, "k_panel_init");
-    k_panel_init<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, X, Rr, P, PD, pa, pb);
-    GM_LAUNCH_CHECK(c);
+    const bool use_warm = warm && c->cfg.warm_start && c->warm_R == R && n_rows <= R;
+    if (use_warm) {
+      GM_PROF(c, "k_panel_scale");
+      k_panel_scale<TV><<<grid, kBT, 0, st>>>(n, (int)R, dv, X, PD);
+      GM_LAUNCH_CHECK(c);
+      gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, X, PD, Q, pa);
+      if (ss != GM_OK) return ss;
+      GM_PROF(c, "k_panel_init_warm");
+      k_panel_init_warm<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, Rr, Q, P, PD, pa, pb);
+      GM_LAUNCH_CHECK(c);
+    } else {
+      GM_PROF(c, "k_panel_init");
+      k_panel_init<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, X, Rr, P, PD, pa, pb);
+      GM_LAUNCH_CHECK(c);
+    }
     GM_CUDA_CHECK(c, cudaMemsetAsync(n_active, 0, sizeof(int), st));
     GM_PROF(c, "k_panel_reduce");
     k_panel_reduce<<<redb, 256, 0, st>>>(0, nbx, (int)R, ncols, tol2, 0, max_it, pa, pb, scal,
                                          active, n_active, c->d_flags);
     GM_LAUNCH_CHECK(c);
     const int check = 8;
-    int it = 1;
-    for (; it <= max_it; ++it) {
-      GM_PROF(c, "k_panel_spmm");
-      k_panel_spmm<TA, TV><<<grid, kBT, 0, st>>>(n, (int)R, c->row_ptr, c->col, (const TA*)c->val,
-                                                 dv, P, PD, Q, pa);
-      GM_LAUNCH_CHECK(c);
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(hn, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+    int it = *hn == 0 ? 0 : 1;  // no active column (all right-hand sides zero): no iteration
+    for (; it >= 1 && it <= max_it; ++it) {
+      {
+        gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, P, PD, Q, pa);
+        if (ss != GM_OK) return ss;
+      }
       GM_PROF(c, "k_panel_reduce");
       k_panel_reduce<<<redb, 256, 0, st>>>(1, nbx, (int)R, ncols, tol2, it, max_it, pa, nullptr,
                                            scal, active, n_active, c->d_flags);
@@ -792,8 +899,8 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     total_it += std::min(it, max_it);
     GM_PROF(c, "k_panel_final");
     k_panel_final<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col, (const TA*)val,
-                                              (const double*)ws.d64.p, X, kdiag_rows, var_out,
-                                              c->d_flags);
+                                              (const double*)ws.d64.p, X, kdiag_rows,
+                                              warm ? c->tau : nullptr, var_out, c->d_flags);
     GM_LAUNCH_CHECK(c);
   }
   // worst relative residual over the last panel's columns
@@ -806,6 +913,7 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     if (h[k] > 0) worst = std::max(worst, std::sqrt(h[R + k] / h[k]));
   *iters_out = total_it;
   *resid_out = worst;
+  c->warm_R = (warm && n_rows <= R) ? R : 0;
   return GM_OK;
 }
 
@@ -836,11 +944,13 @@ gm_status refresh_posterior(gm_ctx* c) {
   if (c->cfg.precision == GM_PREC_FP32) {
     s = posterior_mean<float, float>(c, &it_m, &res_m);
     if (s == GM_OK)
-      s = panels<float, float>(c, c->n, c->row_ptr, c->col, c->val, c->kdiag, c->var, &it_v, &res_v);
+      s = panels<float, float>(c, c->n, c->row_ptr, c->col, c->val, c->kdiag, c->var, &it_v, &res_v,
+                               true);
   } else {
     s = posterior_mean<double, double>(c, &it_m, &res_m);
     if (s == GM_OK)
-      s = panels<double, double>(c, c->n, c->row_ptr, c->col, c->val, c->kdiag, c->var, &it_v, &res_v);
+      s = panels<double, double>(c, c->n, c->row_ptr, c->col, c->val, c->kdiag, c->var, &it_v,
+                                 &res_v, true);
   }
   if (s != GM_OK) return s;
   c->stats.cg_iters_mean = it_m;
@@ -857,8 +967,10 @@ gm_status panel_variances(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, con
   gm_status s = prepare_precond(c);
   if (s != GM_OK) return s;
   if (c->cfg.precision == GM_PREC_FP32)
-    return panels<float, float>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out, resid_out);
-  return panels<double, double>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out, resid_out);
+    return panels<float, float>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out,
+                                resid_out, false);
+  return panels<double, double>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out,
+                                resid_out, false);
 }
 
 gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,

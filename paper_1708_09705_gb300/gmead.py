@@ -45,7 +45,7 @@ class Config(C.Structure):
                 ("cutoff_pc", C.c_double), ("n_nodes", C.c_int32), ("form", C.c_int32),
                 ("taper", C.c_int32), ("precision", C.c_int32), ("likelihood", C.c_int32),
                 ("cg_max_iter", C.c_int32), ("damping", C.c_double), ("vc_floor", C.c_double),
-                ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("reserved", C.c_int32)]
+                ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("warm_start", C.c_int32)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -39,6 +39,7 @@ def test_status_strings_and_defaults(L):
     cfg = gm.default_config()
     assert cfg.sigma2 == 1.0 and cfg.outer_scale_pc == 20.0 and cfg.cutoff_pc == 60.0
     assert cfg.precision == gm.PREC_FP64 and cfg.taper == gm.TAPER_WENDLAND
+    assert cfg.warm_start == 1 and cfg.rhs_panel == 0
     assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2
 
 
@@ -52,7 +53,7 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
     # null array
     assert L.gm_ep_init(C.byref(h), C.byref(cfg), 4, x, None, x, x, x, None, None) == 1
     for field, bad in (("sigma2", -1.0), ("n_nodes", 1), ("damping", 0.0), ("cg_tol", 0.0),
-                       ("precision", 7), ("outer_scale_pc", float("nan"))):
+                       ("precision", 7), ("outer_scale_pc", float("nan")), ("warm_start", 2)):
         c2 = gm.default_config(**{field: bad})
         assert L.gm_ep_init(C.byref(h), C.byref(c2), 4, x, x, x, x, x, None, None) == 1, field
     assert not h.value

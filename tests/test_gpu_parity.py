@@ -223,8 +223,9 @@ def test_isolated_and_coincident_sightlines(gm):
 
 
 def test_rerun_is_bit_identical_and_resume_matches(gm, c1):
+    """Cold-started solves: reruns and save/restore are bit-identical."""
     def run(n):
-        with init(gm, c1, precision=gm.PREC_FP64) as ctx:
+        with init(gm, c1, precision=gm.PREC_FP64, warm_start=0) as ctx:
             ctx.build_cov()
             ctx.ep_sweep(n)
             return ctx.get_sites(), ctx.get_posterior()
@@ -232,7 +233,7 @@ def test_rerun_is_bit_identical_and_resume_matches(gm, c1):
     (t2, n2), (m2, v2) = run(4)
     assert np.array_equal(t1, t2) and np.array_equal(m1, m2) and np.array_equal(v1, v2)
     (ta, na), _ = run(2)
-    with init(gm, c1, precision=gm.PREC_FP64) as ctx:
+    with init(gm, c1, precision=gm.PREC_FP64, warm_start=0) as ctx:
         ctx.build_cov()
         ctx.set_sites(ta, na)
         ctx.ep_sweep(2)
@@ -240,6 +241,20 @@ def test_rerun_is_bit_identical_and_resume_matches(gm, c1):
         mb, vb = ctx.get_posterior()
     assert np.array_equal(tb, t1) and np.array_equal(nb, n1)
     assert np.array_equal(mb, m1) and np.array_equal(vb, v1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_warm_started_variances_agree_with_cold(gm, c1, prec):
+    p = gm.PREC_FP64 if prec == "fp64" else gm.PREC_FP32
+    out = []
+    for warm in (0, 1):
+        with init(gm, c1, precision=p, warm_start=warm) as ctx:
+            ctx.build_cov()
+            ctx.ep_sweep(4)
+            out.append(ctx.get_posterior())
+    rtol = 1e-8 if prec == "fp64" else 2e-3
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=rtol, atol=rtol)
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=rtol)
 
 
 def test_call_order_and_bad_sites(gm, c1):
