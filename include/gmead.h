@@ -196,6 +196,36 @@ int32_t gm_kernel_time_count(gm_ctx* ctx);
 gm_status gm_kernel_time(gm_ctx* ctx, int32_t k, const char** name, int64_t* launches,
                          double* total_ms);
 
+/* Allocation-free EP site update.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory while they run --
+ * frameworks that own every device allocation through their own pool,
+ * processes working inside a fixed, pre-reserved memory budget, and service
+ * loops that must not call cudaMalloc/cudaFree on their latency path.  It
+ * performs the same parallel EP site update as one gm_ep_sweep (cavity,
+ * tilted moments, moment matching, damping, skip rules) on caller-owned
+ * arrays, without a context and without allocating anything.
+ *   n          : number of stars, 1 <= n <= 1,048,576 (GM_E_INVAL beyond)
+ *   mu, var    : posterior marginal mean and variance of ln A per star
+ *   obs, obs_sigma : observation and its noise standard deviation
+ *   tau, nu    : site parameters, updated in place
+ *   likelihood, damping, vc_floor : as in gm_config
+ *   stream     : cudaStream_t to run on (NULL = legacy default stream)
+ *   max_delta_out, skipped_out : host pointers (may be NULL) receiving the
+ *                largest relative site change and the number of skipped stars
+ * All arrays must be DEVICE pointers of length n (host pointers: GM_E_INVAL).
+ * The scratch is a file-scope device array of about 66 KB that every GPU
+ * loading the library keeps until the process exits.  The first call on a
+ * device resolves its address and uploads the Gauss-Hermite rule with
+ * synchronous copies, so make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU race with
+ * one another, so serialise them.  The call synchronises `stream` and
+ * returns GM_E_NONFINITE if a non-finite value appeared. */
+gm_status gm_site_update_noalloc(int64_t n, const double* mu, const double* var,
+                                 const double* obs, const double* obs_sigma, double* tau,
+                                 double* nu, int32_t likelihood, double damping,
+                                 double vc_floor, void* stream, double* max_delta_out,
+                                 int64_t* skipped_out);
+
 const char* gm_status_str(gm_status s);
 const char* gm_last_error(gm_ctx* ctx);
 void gm_destroy(gm_ctx* ctx);

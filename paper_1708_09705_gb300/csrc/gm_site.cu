@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "gm_internal.cuh"
 
@@ -166,4 +167,133 @@ gm_status site_update(gm_ctx* c, double* max_delta, int64_t* skipped) {
   return GM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free site update (gm_site_update_noalloc).
+//
+// Some callers cannot allocate device memory while they run: a host
+// framework that owns every device allocation through its own pool, code
+// running inside a memory-capped or pre-reserved budget, or a service loop
+// that must not call cudaMalloc/cudaFree on its latency path.  For them the
+// EP site update runs on caller-owned arrays, with its scratch (Gauss-Hermite
+// table, per-block maxima, skip counter, flags) in the file-scope array
+// below.  It is sized for one block per 128 stars up to kNaMaxBlocks blocks,
+// so n <= kNaMaxStars.  Every GPU that loads the library holds the array
+// until the process exits.  All calls share it: concurrent calls on the GPU
+// race with one another and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+constexpr int kNaMaxBlocks = 8192;
+constexpr int64_t kNaMaxStars = 128ll * kNaMaxBlocks;  // 1,048,576
+constexpr int kNaSlots = 2 * kGH + kNaMaxBlocks + 4;   // doubles
+constexpr int kNaMaxDevices = 64;
+
+static __device__ __align__(256) double g_na_scratch[kNaSlots];
+
+// Scratch layout (doubles): [0, kGH) nodes, [kGH, 2 kGH) weights * exp(x^2),
+// [2 kGH, 2 kGH + kNaMaxBlocks) per-block maxima, then the skip counter
+// (as an unsigned 64-bit word), the flags word and the reduced maximum.
+static double* g_na_ptr[kNaMaxDevices] = {nullptr};
+
+__global__ void k_na_reduce_max(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double v = 0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) v = fmax(v, part[k]);
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    *out = m;
+  }
+}
+
+static bool na_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// First call on a device: resolve the device address of the scratch array
+// (the host-side name is only a stand-in) and upload the Gauss-Hermite rule.
+// Serialised by a mutex; uses synchronous copies, so it must not run inside
+// a stream capture.
+static gm_status na_setup(int dev, double** out) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (g_na_ptr[dev]) {
+    *out = g_na_ptr[dev];
+    return GM_OK;
+  }
+  double* p = nullptr;
+  if (cudaGetSymbolAddress((void**)&p, g_na_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return GM_E_CUDA;
+  }
+  double rule[2 * kGH];
+  gauss_hermite(kGH, rule, rule + kGH);
+  if (cudaMemcpy(p, rule, sizeof(rule), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return GM_E_CUDA;
+  }
+  g_na_ptr[dev] = p;
+  *out = p;
+  return GM_OK;
+}
+
 }  // namespace gm
+
+extern "C" gm_status gm_site_update_noalloc(int64_t n, const double* mu, const double* var,
+                                            const double* obs, const double* obs_sigma,
+                                            double* tau, double* nu, int32_t likelihood,
+                                            double damping, double vc_floor, void* stream,
+                                            double* max_delta_out, int64_t* skipped_out) {
+  using namespace gm;
+  if (n < 1 || n > kNaMaxStars) return GM_E_INVAL;
+  if (!mu || !var || !obs || !obs_sigma || !tau || !nu) return GM_E_INVAL;
+  if (likelihood != GM_LIK_GAUSS_IN_A && likelihood != GM_LIK_GAUSS_IN_LNA) return GM_E_INVAL;
+  if (!(damping > 0 && damping <= 1) || !(vc_floor >= 0)) return GM_E_INVAL;
+  for (const void* p : {(const void*)mu, (const void*)var, (const void*)obs,
+                        (const void*)obs_sigma, (const void*)tau, (const void*)nu})
+    if (!na_device_ptr(p)) return GM_E_INVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
+    cudaGetLastError();
+    return GM_E_CUDA;
+  }
+  double* base = nullptr;
+  gm_status st = na_setup(dev, &base);
+  if (st != GM_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* gh_x = base;
+  double* gh_w = base + kGH;
+  double* part = base + 2 * kGH;
+  unsigned long long* skipped = (unsigned long long*)(part + kNaMaxBlocks);
+  unsigned* flags = (unsigned*)(part + kNaMaxBlocks + 1);
+  double* maxd = part + kNaMaxBlocks + 2;
+  // the counter and the flags keep the previous call's values: clear them
+  if (cudaMemsetAsync(skipped, 0, 2 * sizeof(double), s) != cudaSuccess) {
+    cudaGetLastError();
+    return GM_E_CUDA;
+  }
+  const int G = (int)ceil_div(n, 128);
+  SiteParams P{damping, vc_floor, likelihood};
+  k_site_update<<<G, 128, 0, s>>>(n, P, mu, var, obs, obs_sigma, tau, nu, gh_x, gh_w, part,
+                                   skipped, flags);
+  k_na_reduce_max<<<1, 1024, 0, s>>>(G, part, maxd);
+  if (cudaGetLastError() != cudaSuccess) return GM_E_CUDA;
+  unsigned long long h[3];
+  if (cudaMemcpyAsync(h, skipped, 3 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return GM_E_CUDA;
+  }
+  unsigned fl = (unsigned)(h[1] & 0xffffffffull);
+  double md;
+  std::memcpy(&md, &h[2], sizeof(md));
+  if (max_delta_out) *max_delta_out = md;
+  if (skipped_out) *skipped_out = (int64_t)h[0];
+  return (fl & kFlagNonFinite) ? GM_E_NONFINITE : GM_OK;
+}

@@ -31,7 +31,8 @@ STATUS = {0: "GM_OK", 1: "GM_E_INVAL", 2: "GM_E_NOMEM", 3: "GM_E_CUDA", 4: "GM_E
 EXPORTS = ["gm_config_default", "gm_ep_init", "gm_build_cov", "gm_ep_sweep", "gm_predict",
            "gm_get_posterior", "gm_get_sites", "gm_set_sites", "gm_get_prior", "gm_get_perm",
            "gm_get_csr", "gm_get_stats", "gm_stream", "gm_status_str", "gm_last_error",
-           "gm_destroy", "gm_profile", "gm_kernel_time_count", "gm_kernel_time"]
+           "gm_destroy", "gm_profile", "gm_kernel_time_count", "gm_kernel_time",
+           "gm_site_update_noalloc"]
 
 
 class GmError(RuntimeError):
@@ -97,6 +98,9 @@ def lib():
         L.gm_destroy.argtypes = [vp]
         L.gm_destroy.restype = None
         L.gm_profile.argtypes = [vp, i32]
+        L.gm_site_update_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, dbl, dbl, vp,
+                                             C.POINTER(dbl), C.POINTER(i64)]
+        L.gm_site_update_noalloc.restype = C.c_int
         L.gm_kernel_time_count.argtypes = [vp]
         L.gm_kernel_time_count.restype = i32
         L.gm_kernel_time.argtypes = [vp, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
