@@ -179,7 +179,9 @@ def roofline_for(name, launches, ms, st, cfg_prec, panel):
     avg_s = ms / launches / 1e3
     n, nnz, n_pairs = st["n_stars"], st["nnz"], st["n_pairs"]
     vb = 4 if cfg_prec == "fp32" else 8
-    if name == "k_panel_spmm":
+    if name in ("k_panel_spmm", "k_panel_spmm_tiled"):
+        # algorithmic work: one FMA per stored entry and panel column (the
+        # tiles' zero slots are not counted)
         flops = 2.0 * nnz * panel
         ach = flops / avg_s / 1e12
         peak = FP32_PEAK_TFLOPS if cfg_prec == "fp32" else 1.25

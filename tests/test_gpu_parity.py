@@ -187,6 +187,29 @@ def test_predict_matches_oracle(gm, c1, c1_oracle, c1_ep5):
 
 
 # ------------------------------------------------------------------ edges
+def test_skip_rule_matches_oracle(gm):
+    """The 600 nearest stars of the 5x5 deg field include weak positive
+    observations whose tilted distribution is wider than the cavity (the
+    likelihood is not log-concave there): both sides skip the same updates,
+    sweep by sweep, and end with the same sites."""
+    cat = make_catalogue("c2_plain_20k", truth="mean")
+    sub = catalogue_subset(cat, np.sort(np.argsort(cat["s"])[:600]))
+    cv = O.build_cov(sub)
+    tau, nu = np.zeros(600), np.zeros(600)
+    with init(gm, sub, precision=gm.PREC_FP64) as ctx:
+        ctx.build_cov()
+        total = 0
+        for sweep in range(3):
+            tau, nu, _, sk, _, _ = O.ep_sweep(cv["K"], cv["m"], sub["A_obs"], sub["A_sigma"], tau, nu)
+            ctx.ep_sweep(1)
+            assert ctx.stats()["sites_skipped"] == sk, sweep
+            total += sk
+        tg, ng = ctx.get_sites()
+    assert total > 0
+    np.testing.assert_allclose(tg, tau, rtol=1e-6)
+    np.testing.assert_allclose(ng, nu, rtol=1e-6, atol=1e-6)
+
+
 def test_single_star(gm):
     cat = catalogue_subset(make_catalogue("c1_plain_400"), np.arange(1))
     with init(gm, cat, precision=gm.PREC_FP64) as ctx:
@@ -323,4 +346,6 @@ def test_bench_workload_full_size_fp32(gm):
     assert np.all(np.isfinite(mu)) and np.all(var > 0)
     assert np.all(var <= kd * (1 + 1e-5))
     assert st["cg_resid_mean"] <= 1e-6 * 1.01
-    assert st["sites_skipped"] == 0
+    # updates with a negative site precision are skipped: only stars with
+    # weak positive observations (non-log-concave likelihood) can do this
+    assert st["sites_skipped"] < 0.01 * 20000
