@@ -63,6 +63,7 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="override star count (testing)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-forms", action="store_true")
     return p.parse_args()
 
 
@@ -208,6 +209,56 @@ def roofline_for(name, launches, ms, st, cfg_prec, panel):
             "work_per_launch": f"{byt:.3e} B"}
 
 
+def forms_comparison(gm, torch, dev, n_sub, sweeps):
+    """Plain FP64 (error reference), FP32 and FP32 + learned surrogate on a
+    smaller draw of the same workload: throughput and posterior error."""
+    from synth import make_catalogue
+    cat = make_catalogue(WORKLOAD, n=n_sub, truth="mean", seed=7)
+    D = {k: torch.tensor(cat[k], dtype=torch.float64, device=dev)
+         for k in ("l", "b", "s", "A_obs", "A_sigma")}
+    out = {}
+    ref = None
+    forms = [("plain_fp64", dict(precision=gm.PREC_FP64, cg_tol=1e-10)),
+             ("plain_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6)),
+             ("learned_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
+                                   cov_source=gm.COV_SURROGATE))]
+    for name, kw in forms:
+        cfg = gm.config_from_catalogue(cat, **kw)
+        with gm.ep_init(cfg, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"]) as ctx:
+            train_s = None
+            if kw.get("cov_source") == gm.COV_SURROGATE:
+                t0 = time.perf_counter()
+                st = ctx.surrogate_train(n_pairs=1_000_000, steps=3000, batch=4096, lr=2e-3)
+                torch.cuda.synchronize()
+                train_s = time.perf_counter() - t0
+            ctx.build_cov()  # warm
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            ctx.build_cov()
+            e1.record()
+            ctx.ep_sweep(sweeps, 0.0)
+            mu, var = ctx.get_posterior()
+            e2.record()
+            e2.synchronize()
+            st = ctx.stats()
+            t_cov = e0.elapsed_time(e1) / 1e3
+            t_all = e0.elapsed_time(e2) / 1e3
+        if ref is None:
+            ref = mu
+        rec = {"site_updates_per_s": n_sub * sweeps / t_all,
+               "pairs_per_s": st["n_pairs"] / t_cov,
+               "max_abs_err_mean_lnA_vs_fp64": float(np.max(np.abs(mu - ref)))}
+        if train_s is not None:
+            rec.update(train_s=train_s, surrogate_val_rmse=st["surrogate_val_rmse"],
+                       surrogate_gate_frac=st["surrogate_gate_frac"],
+                       surrogate_fallback_pairs=st["surrogate_fallback"],
+                       unique_pairs=st["n_pairs"])
+        out[name] = rec
+    return {"stars": n_sub, "sweeps": sweeps, "forms": out,
+            "equal_error_bar": "1e-3 in mean ln A vs the FP64 plain form"}
+
+
 def run_gpu(a):
     import torch
 
@@ -316,6 +367,10 @@ def run_gpu(a):
     else:
         ctx.close()
 
+    forms = None
+    if rank == 0 and not a.no_forms:
+        forms = forms_comparison(gm, torch, dev, 4000, a.sweeps)
+
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu:
         r = cpu_sample(cat, 600, a.sweeps)
@@ -342,7 +397,7 @@ def run_gpu(a):
                "pairs_per_s": pairs_per_s, "cov_ms": 1e3 * t_cov,
                "cg_iters": {"mean": st["cg_iters_mean"], "var_last_panels": st["cg_iters_var"]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": ck,
+               "clocks": ck, "forms": forms,
                "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in
                               sorted(kt.items(), key=lambda kv: -kv[1][1])[:8]},
                "kernel_ms_total": total_ms}

@@ -67,6 +67,9 @@ enum { GM_FORM_LOGNORMAL = 0, GM_FORM_LINEAR = 1 };
 /* Sparsification: Wendland psi_{3,1} taper (keeps K positive definite) or a
  * hard cutoff (literal dropping; may be indefinite -> GM_E_NOT_SPD). */
 enum { GM_TAPER_WENDLAND = 0, GM_TAPER_HARD = 1 };
+/* Source of the covariance entries: the sightline quadrature, or the learned
+ * surrogate (gm_surrogate_*) with quadrature fallback beyond the gate. */
+enum { GM_COV_QUADRATURE = 0, GM_COV_SURROGATE = 1 };
 /* Per-star likelihood: A_obs ~ N(exp(a), sigma^2) or a_obs ~ N(a, sigma^2). */
 enum { GM_LIK_GAUSS_IN_A = 0, GM_LIK_GAUSS_IN_LNA = 1 };
 
@@ -90,6 +93,10 @@ typedef struct {
                              previous sweep's solutions (same results within
                              cg_tol; resume from saved sites is then equal
                              within cg_tol, not bit for bit); 0: cold start   */
+  int32_t cov_source;     /* GM_COV_QUADRATURE or GM_COV_SURROGATE            */
+  int32_t reserved;
+  double surrogate_gate;  /* surrogate entries whose estimated relative error
+                             exceeds this are recomputed by quadrature         */
 } gm_config;
 
 /* Device memory hooks.  When given, every device allocation of the context
@@ -113,12 +120,17 @@ typedef struct {
   double last_max_delta;   /* largest relative site change of the last sweep  */
   double cg_resid_mean;    /* final relative residual of the mean solve       */
   double cg_resid_var;     /* largest final relative residual of a variance   */
+  int64_t surrogate_fallback; /* entries recomputed by quadrature (last build) */
+  double surrogate_loss;   /* final training loss (last gm_surrogate_train)    */
+  double surrogate_val_rmse; /* RMSE of ln K on fresh pairs, tensor-core path  */
+  double surrogate_gate_frac; /* fraction of those pairs above the gate        */
 } gm_stats;
 
 /* Fills *cfg with defaults: sigma2 1, L0 20 pc, rho_bar 1e-3 mag/pc, cutoff
  * 3 L0, 32 nodes, lognormal form, Wendland taper, FP64, Gaussian-in-A
  * likelihood, damping 1, cavity floor 1e-8, CG tol 1e-10 / 2000 iterations,
- * automatic panel width, warm-started variance solves. */
+ * automatic panel width, warm-started variance solves, quadrature entries,
+ * surrogate gate 1e-3. */
 void gm_config_default(gm_config* cfg);
 
 /* Creates a context for n >= 1 stars (Sect. 3: observed (l, b), distance s
@@ -136,6 +148,24 @@ gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n,
                      const double* l, const double* b, const double* s,
                      const double* obs, const double* obs_sigma, void* stream,
                      const gm_allocator* alloc);
+
+/* Creates a context holding n_fields independent fields (sky fields /
+ * sub-catalogues, Sect. 4.1) that are solved together: stars of different
+ * fields are never neighbours, so K is block diagonal, and every kernel of
+ * the build and of the sweeps runs over all fields in one launch (the
+ * variance solves of all fields as one packed multi-panel CG, replayed from
+ * a CUDA graph).  Arguments as gm_ep_init, plus
+ *   field_id     : field of each star, 0 <= id < n_fields (int32, host or
+ *                  device, length n; NULL only when n_fields == 1)
+ *   field_L0     : outer scale per field (host, length n_fields; NULL = cfg)
+ *   field_cutoff : cutoff per field (host, length n_fields; NULL = cfg)
+ * Several fields require GM_PREC_FP32 and the quadrature source, and
+ * gm_predict is not available for them (GM_E_STATE). */
+gm_status gm_ep_init_fields(gm_ctx** out, const gm_config* cfg, int64_t n, const double* l,
+                            const double* b, const double* s, const double* obs,
+                            const double* obs_sigma, int32_t n_fields, const int32_t* field_id,
+                            const double* field_L0, const double* field_cutoff, void* stream,
+                            const gm_allocator* alloc);
 
 /* Assembles K (CSR over the internal order, both triangles, rows sorted) and
  * the prior mean m (Sect. 3): neighbour search within cutoff_pc, sightline
@@ -195,6 +225,42 @@ gm_status gm_profile(gm_ctx* ctx, int32_t enable);
 int32_t gm_kernel_time_count(gm_ctx* ctx);
 gm_status gm_kernel_time(gm_ctx* ctx, int32_t k, const char** name, int64_t* launches,
                          double* total_ms);
+
+/* Covariance surrogate (no counterpart in the paper, which evaluates every
+ * entry by the sightline integral of Sect. 3): an MLP with 5 inputs (the
+ * pair's scale-free geometry ln(min(s)/L0)/4, ln(max(s)/L0)/4,
+ * ln(1e-3 + |u_i - u_j| sqrt(s_i s_j)/L0)/4, sigma2 and ln(L0/20 pc)), three
+ * hidden layers of 64 SiLU units and 2 outputs: y = ln K (K = log1p(R)
+ * before the taper) and e, an estimate of ln |y - y_true|.  It runs on the
+ * tensor cores with BF16 operands and FP32 accumulation.
+ * Parameters are FP32, gm_surrogate_param_count() of them, laid out as
+ * W1[5][64], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64][2], b4[2]
+ * (W[k][n] maps input k to output n). */
+int64_t gm_surrogate_param_count(void);
+gm_status gm_surrogate_set_params(gm_ctx* ctx, const float* params, int64_t n);
+gm_status gm_surrogate_get_params(gm_ctx* ctx, float* params_out, int64_t n);
+/* Trains the surrogate of this context's hyperparameters on the GPU: n_pairs
+ * pair geometries like those of the covariance (distances spanning the
+ * context's stars, separations up to the cutoff) with targets from the
+ * sightline quadrature; `steps` Adam steps on mini-batches of `batch` pairs
+ * with learning rate lr decaying by cosine to lr/100; FP32 forward and
+ * backward kernels.  Starts from the current parameters if set, else from a
+ * seeded He initialisation.  Afterwards evaluates the tensor-core network on
+ * fresh pairs; results go to gm_stats (surrogate_*). */
+gm_status gm_surrogate_train(gm_ctx* ctx, int64_t n_pairs, int32_t steps, int32_t batch,
+                             double lr, uint64_t seed);
+/* Loss and gradient of the training objective on n given samples (features
+ * X[n][5] and targets Y[n] = ln K, FP32, host or device), with error-head
+ * weight lam: grad_out has gm_surrogate_param_count() entries (host or
+ * device), *loss_out the loss.  For checking the backward pass. */
+gm_status gm_surrogate_grad(gm_ctx* ctx, int64_t n, const float* X, const float* Y, double lam,
+                            float* grad_out, double* loss_out);
+/* Evaluates the surrogate for n pairs given by distances si, sj (pc) and
+ * chord |u_i - u_j| (host or device arrays), at sigma2 and L0 (pc).
+ * Outputs y and e (FP32, length n).  GM_E_STATE without parameters. */
+gm_status gm_surrogate_eval(gm_ctx* ctx, int64_t n, const double* si, const double* sj,
+                            const double* chord, double sigma2, double L0, float* y_out,
+                            float* e_out);
 
 /* Allocation-free EP site update.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory while they run --

@@ -78,13 +78,14 @@ void prof_begin(gm_ctx* c, const char* name) {
   if (c->prof_pending) prof_end(c);  // two launches before one check
   cudaEvent_t a = prof_event(c), b = prof_event(c);
   if (!a || !b) return;
-  cudaEventRecord(a, c->stream);
+  cudaEventRecord(a, c->prof_stream ? c->prof_stream : c->stream);
   c->prof_recs.push_back({name, a, b});
   c->prof_pending = name;
 }
 
 void prof_end(gm_ctx* c) {
-  if (!c->prof_recs.empty()) cudaEventRecord(c->prof_recs.back().b, c->stream);
+  if (!c->prof_recs.empty())
+    cudaEventRecord(c->prof_recs.back().b, c->prof_stream ? c->prof_stream : c->stream);
   c->prof_pending = nullptr;
 }
 
@@ -218,6 +219,8 @@ static gm_status validate(const gm_config* f) {
   if (!(f->damping > 0 && f->damping <= 1)) return GM_E_INVAL;
   if (!(f->vc_floor >= 0) || !(f->cg_tol > 0) || f->cg_max_iter <= 0) return GM_E_INVAL;
   if (f->rhs_panel < 0 || (f->warm_start != 0 && f->warm_start != 1)) return GM_E_INVAL;
+  if (f->cov_source != GM_COV_QUADRATURE && f->cov_source != GM_COV_SURROGATE) return GM_E_INVAL;
+  if (!(f->surrogate_gate > 0)) return GM_E_INVAL;
   return GM_OK;
 }
 
@@ -245,6 +248,8 @@ void gm_config_default(gm_config* f) {
   f->cg_tol = 1e-10;
   f->rhs_panel = 0;
   f->warm_start = 1;
+  f->cov_source = GM_COV_QUADRATURE;
+  f->surrogate_gate = 1e-3;
 }
 
 const char* gm_status_str(gm_status s) {
@@ -266,18 +271,29 @@ const char* gm_last_error(gm_ctx* c) { return c ? c->last_error.c_str() : "null 
 
 void* gm_stream(gm_ctx* c) { return c ? (void*)c->stream : nullptr; }
 
-gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n, const double* l,
-                     const double* b, const double* s, const double* obs,
-                     const double* obs_sigma, void* stream, const gm_allocator* alloc) {
+gm_status gm_ep_init_fields(gm_ctx** out, const gm_config* cfg, int64_t n, const double* l,
+                            const double* b, const double* s, const double* obs,
+                            const double* obs_sigma, int32_t n_fields, const int32_t* field_id,
+                            const double* field_L0, const double* field_cutoff, void* stream,
+                            const gm_allocator* alloc) {
   if (!out || !cfg) return GM_E_INVAL;
   *out = nullptr;
   if (n < 1 || n >= (1ll << 31) || !l || !b || !s || !obs || !obs_sigma) return GM_E_INVAL;
   if (validate(cfg) != GM_OK) return GM_E_INVAL;
+  if (n_fields < 1 || n_fields > (1 << 20) || (n_fields > 1 && !field_id)) return GM_E_INVAL;
+  // several fields: FP32 panels and the quadrature source only
+  if (n_fields > 1 && (cfg->precision != GM_PREC_FP32 || cfg->cov_source != GM_COV_QUADRATURE))
+    return GM_E_INVAL;
+  for (int32_t f = 0; field_L0 && f < n_fields; ++f)
+    if (!(field_L0[f] > 0) || !std::isfinite(field_L0[f])) return GM_E_INVAL;
+  for (int32_t f = 0; field_cutoff && f < n_fields; ++f)
+    if (!(field_cutoff[f] > 0) || !std::isfinite(field_cutoff[f])) return GM_E_INVAL;
   if (alloc && (!alloc->alloc || !alloc->free)) return GM_E_INVAL;
   gm_ctx* c = new (std::nothrow) gm_ctx();
   if (!c) return GM_E_NOMEM;
   c->cfg = *cfg;
   c->n = n;
+  c->n_fields = n_fields;
   c->stream = (cudaStream_t)stream;
   if (alloc) {
     c->alloc = *alloc;
@@ -352,8 +368,17 @@ gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n, const double
       return fail(cuda_fail(c, cudaGetLastError(), "input check"));
     if (*h) return fail(set_error(c, GM_E_INVAL, "non-finite input, s <= 0 or obs_sigma <= 0"));
   }
-  st = geometry_init(c, in[0], in[1], in[2], in[3], in[4]);
+  int32_t* fid = nullptr;
+  if (n_fields > 1) {
+    fid = (int32_t*)dev_alloc(c, (size_t)n * sizeof(int32_t));
+    if (!fid) return fail(set_error(c, GM_E_NOMEM, "field ids"));
+    cudaMemcpyKind k = is_device_ptr(field_id) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(fid, field_id, (size_t)n * sizeof(int32_t), k, c->stream) != cudaSuccess)
+      return fail(cuda_fail(c, cudaGetLastError(), "field ids"));
+  }
+  st = geometry_init(c, in[0], in[1], in[2], in[3], in[4], fid, field_L0, field_cutoff);
   if (st != GM_OK) return fail(st);
+  if (fid) dev_free_now(c, fid, (size_t)n * sizeof(int32_t));
   for (int k = 4; k >= 0; --k) dev_free_now(c, in[k], nb);
   st = phi_points_init(c);
   if (st != GM_OK) return fail(st);
@@ -365,21 +390,34 @@ gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n, const double
   return GM_OK;
 }
 
+gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n, const double* l,
+                     const double* b, const double* s, const double* obs,
+                     const double* obs_sigma, void* stream, const gm_allocator* alloc) {
+  return gm_ep_init_fields(out, cfg, n, l, b, s, obs, obs_sigma, 1, nullptr, nullptr, nullptr,
+                           stream, alloc);
+}
+
 gm_status gm_build_cov(gm_ctx* c, int64_t* nnz_out) {
   if (!c) return GM_E_INVAL;
   c->launches = 0;
-  gm_status st = neighbour_csr(c, c->n, c->s, c->ux, c->uy, c->uz, true, c->row_ptr, c->col_buf,
-                               &c->nnz, c->diag_pos);
+  gm_status st = neighbour_csr(c, c->n, c->s, c->ux, c->uy, c->uz, c->field_of, true, c->row_ptr,
+                               c->col_buf, &c->nnz, c->diag_pos);
   if (st != GM_OK) return st;
   c->col = (int32_t*)c->col_buf.p;
   const size_t vs = c->cfg.precision == GM_PREC_FP32 ? sizeof(float) : sizeof(double);
   if (!ensure(c, c->val_buf, std::max<int64_t>(c->nnz, 1) * vs))
     return set_error(c, GM_E_NOMEM, "CSR values");
   c->val = c->val_buf.p;
-  st = pair_quadrature(c, c->n, c->s, c->ux, c->uy, c->uz, c->row_ptr, c->col, c->nnz, c->val, true);
+  if (c->cfg.cov_source == GM_COV_SURROGATE) {
+    st = surrogate_values(c);
+  } else {
+    st = pair_quadrature(c, c->n, c->s, c->ux, c->uy, c->uz, c->field_of, c->row_ptr, c->col, c->nnz,
+                         c->val, true);
+  }
   if (st != GM_OK) return st;
   c->t_nblk = 0;
   c->warm_R = 0;
+  pack_invalidate(c);
   st = tiles_build(c);
   if (st != GM_OK) return st;
   st = read_flags(c);
@@ -556,6 +594,8 @@ gm_status gm_get_stats(gm_ctx* c, gm_stats* out) {
 gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, const double* s,
                      double* mean_out, double* var_out) {
   if (!c || nq < 0 || (nq > 0 && (!l || !b || !s || !mean_out || !var_out))) return GM_E_INVAL;
+  if (c->n_fields > 1)
+    return set_error(c, GM_E_STATE, "prediction needs a single-field context");
   if (nq == 0) return GM_OK;
   c->launches = 0;
   gm_status st = ensure_posterior(c);
@@ -585,12 +625,13 @@ gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, co
   if (st != GM_OK) return st;
   Buffer qcol;
   int64_t qnnz = 0;
-  st = neighbour_csr(c, nq, qs, ux, uy, uz, false, qptr, qcol, &qnnz, nullptr);
+  st = neighbour_csr(c, nq, qs, ux, uy, uz, nullptr, false, qptr, qcol, &qnnz, nullptr);
   if (st != GM_OK) return st;
   const size_t vs = c->cfg.precision == GM_PREC_FP32 ? sizeof(float) : sizeof(double);
   void* qval = dev_alloc(c, std::max<int64_t>(qnnz, 1) * vs);
   if (!qval) return set_error(c, GM_E_NOMEM, "query values");
-  st = pair_quadrature(c, nq, qs, ux, uy, uz, qptr, (const int32_t*)qcol.p, qnnz, qval, false);
+  st = pair_quadrature(c, nq, qs, ux, uy, uz, nullptr, qptr, (const int32_t*)qcol.p, qnnz, qval,
+                       false);
   if (st == GM_OK) st = self_quadrature(c, nq, qs, kss);
   if (st != GM_OK) return st;
   // prior mean at the queries

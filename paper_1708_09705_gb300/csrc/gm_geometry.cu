@@ -28,41 +28,45 @@ __global__ void k_unit_vectors(int64_t n, const double* __restrict__ l,
   }
 }
 
-// Bounding box of star positions (single block, fixed reduction order).
-__global__ void k_bbox(int64_t n, const double* __restrict__ s, const double* __restrict__ ux,
-                       const double* __restrict__ uy, const double* __restrict__ uz,
-                       double* __restrict__ out /* 6: min xyz, max xyz */) {
-  __shared__ double sh[6][1024];
+// Bounding box of each field's star positions: one block per field, fixed
+// reduction order.  out[f*8 + 0..5] = min xyz, max xyz; out[f*8 + 6] = count.
+__global__ void k_field_bbox(int64_t n, const int32_t* __restrict__ fid,
+                             const double* __restrict__ s, const double* __restrict__ ux,
+                             const double* __restrict__ uy, const double* __restrict__ uz,
+                             double* __restrict__ out) {
+  __shared__ double sh[7][256];
+  const int f = blockIdx.x;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  double cnt = 0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    if (fid && fid[i] != f) continue;
     double p[3] = {s[i] * ux[i], s[i] * uy[i], s[i] * uz[i]};
     for (int d = 0; d < 3; ++d) {
       lo[d] = fmin(lo[d], p[d]);
       hi[d] = fmax(hi[d], p[d]);
     }
+    cnt += 1;
   }
   for (int d = 0; d < 3; ++d) {
     sh[d][threadIdx.x] = lo[d];
     sh[d + 3][threadIdx.x] = hi[d];
   }
+  sh[6][threadIdx.x] = cnt;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
+    if ((int)threadIdx.x < w) {
       for (int d = 0; d < 3; ++d) {
         sh[d][threadIdx.x] = fmin(sh[d][threadIdx.x], sh[d][threadIdx.x + w]);
         sh[d + 3][threadIdx.x] = fmax(sh[d + 3][threadIdx.x], sh[d + 3][threadIdx.x + w]);
       }
+      sh[6][threadIdx.x] += sh[6][threadIdx.x + w];
+    }
     __syncthreads();
   }
-  if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < 7) out[(int64_t)f * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-struct Grid {
-  int gx, gy, gz;
-  double ox, oy, oz, inv_cell;
-};
-
-__device__ __forceinline__ void cell_coords(const Grid& g, double x, double y, double z,
+__device__ __forceinline__ void cell_coords(const FieldGrid& g, double x, double y, double z,
                                             int* cx, int* cy, int* cz) {
   int a = (int)floor((x - g.ox) * g.inv_cell);
   int b = (int)floor((y - g.oy) * g.inv_cell);
@@ -72,15 +76,18 @@ __device__ __forceinline__ void cell_coords(const Grid& g, double x, double y, d
   *cz = min(max(c, 0), g.gz - 1);
 }
 
-__global__ void k_cell_keys(int64_t n, int64_t n_pad, Grid g, const double* __restrict__ s,
+__global__ void k_cell_keys(int64_t n, int64_t n_pad, const FieldGrid* __restrict__ fg,
+                            const int32_t* __restrict__ fid, const double* __restrict__ s,
                             const double* __restrict__ ux, const double* __restrict__ uy,
                             const double* __restrict__ uz, unsigned long long* __restrict__ keys) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (i < n) {
+      const FieldGrid g = fg[fid ? fid[i] : 0];
       int cx, cy, cz;
       cell_coords(g, s[i] * ux[i], s[i] * uy[i], s[i] * uz[i], &cx, &cy, &cz);
-      unsigned long long id = ((unsigned long long)cx * g.gy + cy) * g.gz + cz;
+      unsigned long long id =
+          (unsigned long long)g.cell_off + ((unsigned long long)cx * g.gy + cy) * g.gz + cz;
       keys[i] = (id << 32) | (unsigned long long)i;
     } else {
       keys[i] = ~0ull;
@@ -135,7 +142,8 @@ __global__ void k_apply_perm(int64_t n, const unsigned long long* __restrict__ k
                              int64_t* __restrict__ perm, double* __restrict__ s,
                              double* __restrict__ ux, double* __restrict__ uy,
                              double* __restrict__ uz, double* __restrict__ obs,
-                             double* __restrict__ sig, int32_t* __restrict__ cell_of) {
+                             double* __restrict__ sig, int32_t* __restrict__ cell_of,
+                             const int32_t* __restrict__ fid, int32_t* __restrict__ field_of) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long key = keys[k];
@@ -148,6 +156,7 @@ __global__ void k_apply_perm(int64_t n, const unsigned long long* __restrict__ k
     obs[k] = obs_in[i];
     sig[k] = sig_in[i];
     cell_of[k] = (int32_t)(key >> 32);
+    field_of[k] = fid ? fid[i] : 0;
   }
 }
 
@@ -173,7 +182,8 @@ __device__ __forceinline__ double dist2(double sr, double xr, double yr, double 
 }
 
 template <bool kFill>
-__global__ void k_neighbours(int64_t n_rows, Grid g, double cut2, const double* __restrict__ rs,
+__global__ void k_neighbours(int64_t n_rows, const FieldGrid* __restrict__ fg,
+                             const int32_t* __restrict__ row_field, const double* __restrict__ rs,
                              const double* __restrict__ rux, const double* __restrict__ ruy,
                              const double* __restrict__ ruz, const double* __restrict__ s,
                              const double* __restrict__ ux, const double* __restrict__ uy,
@@ -185,6 +195,8 @@ __global__ void k_neighbours(int64_t n_rows, Grid g, double cut2, const double* 
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < n_rows; r += nwarps) {
     const double sr = rs[r], xr = rux[r], yr = ruy[r], zr = ruz[r];
+    const FieldGrid g = fg[row_field ? row_field[r] : 0];
+    const double cut2 = g.cut2;
     int cx, cy, cz;
     cell_coords(g, sr * xr, sr * yr, sr * zr, &cx, &cy, &cz);
     int64_t pos = kFill ? count_or_ptr[r] : 0;
@@ -197,8 +209,8 @@ __global__ void k_neighbours(int64_t n_rows, Grid g, double cut2, const double* 
         if (ay < 0 || ay >= g.gy) continue;
         // the three z-neighbours are consecutive cells: one contiguous range
         int z0 = max(cz - 1, 0), z1 = min(cz + 1, g.gz - 1);
-        int64_t c0 = ((int64_t)ax * g.gy + ay) * g.gz + z0;
-        int64_t c1 = ((int64_t)ax * g.gy + ay) * g.gz + z1 + 1;
+        int64_t c0 = g.cell_off + ((int64_t)ax * g.gy + ay) * g.gz + z0;
+        int64_t c1 = g.cell_off + ((int64_t)ax * g.gy + ay) * g.gz + z1 + 1;
         int32_t j0 = cell_start[c0], j1 = cell_start[c1];
         for (int32_t jb = j0; jb < j1; jb += 32) {
           int32_t j = jb + lane;
@@ -278,18 +290,6 @@ __global__ void k_scan_add(int64_t n, int64_t* __restrict__ out, const int64_t* 
 }
 
 // ------------------------------------------------------------ host side
-static Grid grid_of(const gm_ctx* c) {
-  Grid g;
-  g.gx = c->gx;
-  g.gy = c->gy;
-  g.gz = c->gz;
-  g.ox = c->org[0];
-  g.oy = c->org[1];
-  g.oz = c->org[2];
-  g.inv_cell = 1.0 / c->cell;
-  return g;
-}
-
 gm_status sort_u64(gm_ctx* c, unsigned long long* keys, int64_t n_pad) {
   cudaStream_t st = c->stream;
   const int kb = (int)std::min<int64_t>(ceil_div(n_pad, 256), 16 * sm_count(c));
@@ -327,8 +327,10 @@ gm_status scan_i64(gm_ctx* c, const int64_t* in, int64_t* out, int64_t n) {
 }
 
 gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const double* s,
-                        const double* obs, const double* sig) {
+                        const double* obs, const double* sig, const int32_t* fid,
+                        const double* field_L0, const double* field_cut) {
   const int64_t n = c->n;
+  const int nf = c->n_fields;
   cudaStream_t st = c->stream;
   const int sms = sm_count(c);
   const int blocks = (int)std::min<int64_t>(ceil_div(n, 256), 8 * sms);
@@ -336,40 +338,68 @@ gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const doubl
   double* ux_in = (double*)dev_alloc(c, n * sizeof(double));
   double* uy_in = (double*)dev_alloc(c, n * sizeof(double));
   double* uz_in = (double*)dev_alloc(c, n * sizeof(double));
-  double* bbox = (double*)dev_alloc(c, 8 * sizeof(double));
+  double* bbox = (double*)dev_alloc(c, (size_t)nf * 8 * sizeof(double));
   if (!ux_in || !uy_in || !uz_in || !bbox) return set_error(c, GM_E_NOMEM, "geometry scratch");
   GM_PROF(c, "k_unit_vectors");
   k_unit_vectors<<<blocks, 256, 0, st>>>(n, l, b, ux_in, uy_in, uz_in);
   GM_LAUNCH_CHECK(c);
-  GM_PROF(c, "k_bbox");
-  k_bbox<<<1, 1024, 0, st>>>(n, s, ux_in, uy_in, uz_in, bbox);
+  GM_PROF(c, "k_field_bbox");
+  k_field_bbox<<<nf, 256, 0, st>>>(n, fid, s, ux_in, uy_in, uz_in, bbox);
   GM_LAUNCH_CHECK(c);
-  double hb[6];
-  GM_CUDA_CHECK(c, cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st));
+  std::vector<double> hb((size_t)nf * 8);
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(hb.data(), bbox, hb.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st));
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
-  // grid with cell edge >= cutoff and at most 2^26 cells
-  double cell = c->cfg.cutoff_pc;
-  for (int it = 0; it < 64; ++it) {
-    double ext[3];
-    int64_t tot = 1;
-    int dims[3];
-    for (int d = 0; d < 3; ++d) {
-      ext[d] = hb[d + 3] - hb[d];
-      dims[d] = (int)std::min<double>(std::floor(ext[d] / cell) + 1.0, 1 << 26);
-      tot *= dims[d];
+  // per-field grid: cell edge >= cutoff, at most 2^24 cells per field
+  c->h_fgrid.assign(nf, FieldGrid{});
+  c->h_fptr.assign(nf + 1, 0);
+  int64_t off = 0;
+  for (int f = 0; f < nf; ++f) {
+    const double* B = hb.data() + (size_t)f * 8;
+    const double L0 = field_L0 ? field_L0[f] : c->cfg.outer_scale_pc;
+    const double cut = field_cut ? field_cut[f] : c->cfg.cutoff_pc;
+    FieldGrid& g = c->h_fgrid[f];
+    const int64_t cnt = (int64_t)B[6];
+    double lo[3] = {B[0], B[1], B[2]}, hi[3] = {B[3], B[4], B[5]};
+    if (cnt == 0)
+      for (int d = 0; d < 3; ++d) lo[d] = hi[d] = 0.0;
+    double cell = cut;
+    int dims[3] = {1, 1, 1};
+    for (int it = 0; it < 64; ++it) {
+      int64_t tot = 1;
+      for (int d = 0; d < 3; ++d) {
+        dims[d] = (int)std::min<double>(std::floor((hi[d] - lo[d]) / cell) + 1.0, 1 << 24);
+        tot *= dims[d];
+      }
+      if (tot <= (1ll << 24)) break;
+      cell *= 1.26;
     }
-    if (tot <= (1ll << 26)) {
-      c->gx = dims[0];
-      c->gy = dims[1];
-      c->gz = dims[2];
-      break;
-    }
-    cell *= 1.26;
+    g.ox = lo[0];
+    g.oy = lo[1];
+    g.oz = lo[2];
+    g.inv_cell = 1.0 / cell;
+    g.cut2 = cut * cut;
+    g.inv_cut = 1.0 / cut;
+    g.inv_L0 = 1.0 / L0;
+    g.gx = dims[0];
+    g.gy = dims[1];
+    g.gz = dims[2];
+    g.cell_off = off;
+    off += (int64_t)dims[0] * dims[1] * dims[2];
+    c->h_fptr[f + 1] = c->h_fptr[f] + cnt;
   }
-  c->cell = cell;
-  for (int d = 0; d < 3; ++d) c->org[d] = hb[d];
-  const int64_t n_cells = (int64_t)c->gx * c->gy * c->gz;
-  Grid g = grid_of(c);
+  if (off >= (1ll << 31) || c->h_fptr[nf] != n)
+    return set_error(c, GM_E_INVAL, "field ids out of range or too many grid cells");
+  c->n_cells = off;
+  c->fgrid = (FieldGrid*)dev_alloc(c, (size_t)nf * sizeof(FieldGrid));
+  c->fptr = (int64_t*)dev_alloc(c, (size_t)(nf + 1) * sizeof(int64_t));
+  c->field_of = (int32_t*)dev_alloc(c, n * sizeof(int32_t));
+  if (!c->fgrid || !c->fptr || !c->field_of) return set_error(c, GM_E_NOMEM, "field tables");
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(c->fgrid, c->h_fgrid.data(), nf * sizeof(FieldGrid),
+                                   cudaMemcpyHostToDevice, st));
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(c->fptr, c->h_fptr.data(), (nf + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, st));
+  const int64_t n_cells = c->n_cells;
 
   int64_t n_pad = 1024;
   while (n_pad < n) n_pad <<= 1;
@@ -379,7 +409,7 @@ gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const doubl
   if (!keys || !cell_of || !c->cell_start) return set_error(c, GM_E_NOMEM, "cell grid");
   const int kb = (int)std::min<int64_t>(ceil_div(n_pad, 256), 16 * sms);
   GM_PROF(c, "k_cell_keys");
-  k_cell_keys<<<kb, 256, 0, st>>>(n, n_pad, g, s, ux_in, uy_in, uz_in, keys);
+  k_cell_keys<<<kb, 256, 0, st>>>(n, n_pad, c->fgrid, fid, s, ux_in, uy_in, uz_in, keys);
   GM_LAUNCH_CHECK(c);
   {
     gm_status sst = sort_u64(c, keys, n_pad);
@@ -387,7 +417,8 @@ gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const doubl
   }
   GM_PROF(c, "k_apply_perm");
   k_apply_perm<<<blocks, 256, 0, st>>>(n, keys, s, ux_in, uy_in, uz_in, obs, sig, c->perm, c->s,
-                                       c->ux, c->uy, c->uz, c->obs, c->obs_sigma, cell_of);
+                                       c->ux, c->uy, c->uz, c->obs, c->obs_sigma, cell_of, fid,
+                                       c->field_of);
   GM_LAUNCH_CHECK(c);
   GM_PROF(c, "k_cell_start");
   k_cell_start<<<blocks, 256, 0, st>>>(n, n_cells, cell_of, c->cell_start);
@@ -395,7 +426,7 @@ gm_status geometry_init(gm_ctx* c, const double* l, const double* b, const doubl
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
   dev_free_now(c, keys, n_pad * sizeof(unsigned long long));
   dev_free_now(c, cell_of, n * sizeof(int32_t));
-  dev_free_now(c, bbox, 8 * sizeof(double));
+  dev_free_now(c, bbox, (size_t)nf * 8 * sizeof(double));
   dev_free_now(c, uz_in, n * sizeof(double));
   dev_free_now(c, uy_in, n * sizeof(double));
   dev_free_now(c, ux_in, n * sizeof(double));
@@ -412,17 +443,15 @@ gm_status unit_vectors(gm_ctx* c, int64_t n, const double* l, const double* b, d
 }
 
 gm_status neighbour_csr(gm_ctx* c, int64_t n_rows, const double* rs, const double* rux,
-                        const double* ruy, const double* ruz, bool self, int64_t* row_ptr,
-                        Buffer& col_buf, int64_t* nnz_out, int64_t* diag_pos) {
+                        const double* ruy, const double* ruz, const int32_t* row_field, bool self,
+                        int64_t* row_ptr, Buffer& col_buf, int64_t* nnz_out, int64_t* diag_pos) {
   cudaStream_t st = c->stream;
   const int sms = sm_count(c);
-  Grid g = grid_of(c);
-  const double cut2 = c->cfg.cutoff_pc * c->cfg.cutoff_pc;
   int64_t* counts = (int64_t*)dev_alloc(c, (n_rows + 1) * sizeof(int64_t));
   if (!counts) return set_error(c, GM_E_NOMEM, "neighbour counts");
   const int wb = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 32 * sms);
   GM_PROF(c, "k_neighbours");
-  k_neighbours<false><<<wb, 256, 0, st>>>(n_rows, g, cut2, rs, rux, ruy, ruz, c->s, c->ux, c->uy,
+  k_neighbours<false><<<wb, 256, 0, st>>>(n_rows, c->fgrid, row_field, rs, rux, ruy, ruz, c->s, c->ux, c->uy,
                                           c->uz, c->cell_start, counts, nullptr, nullptr, self);
   GM_LAUNCH_CHECK(c);
   {
@@ -437,7 +466,7 @@ gm_status neighbour_csr(gm_ctx* c, int64_t n_rows, const double* rs, const doubl
   if (!ensure(c, col_buf, std::max<int64_t>(nnz, 1) * sizeof(int32_t)))
     return set_error(c, GM_E_NOMEM, "CSR column indices");
   GM_PROF(c, "k_neighbours");
-  k_neighbours<true><<<wb, 256, 0, st>>>(n_rows, g, cut2, rs, rux, ruy, ruz, c->s, c->ux, c->uy,
+  k_neighbours<true><<<wb, 256, 0, st>>>(n_rows, c->fgrid, row_field, rs, rux, ruy, ruz, c->s, c->ux, c->uy,
                                          c->uz, c->cell_start, row_ptr, (int32_t*)col_buf.p,
                                          diag_pos, self);
   GM_LAUNCH_CHECK(c);

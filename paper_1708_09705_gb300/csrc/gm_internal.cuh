@@ -46,6 +46,17 @@ struct Buffer {
 };
 
 struct Workspace;  // solver scratch, see gm_solve.cu
+struct PackState;  // packed multi-field panels, see gm_fields.cu
+
+// Per-field cell grid and hyperparameters.  A context holds one field per
+// independent problem (sky field / sub-catalogue); stars of different fields
+// are never neighbours, so K is block diagonal by field.
+struct FieldGrid {
+  double ox, oy, oz, inv_cell;  // grid origin, 1 / cell edge (edge >= cutoff)
+  double cut2, inv_cut, inv_L0;  // cutoff^2, 1 / cutoff, 1 / outer scale
+  int gx, gy, gz, pad;           // cells per axis
+  int64_t cell_off;              // id of the field's first cell
+};
 
 // Four doubles, 32-byte aligned (one FP64 table segment).
 struct alignas(32) D4 {
@@ -77,11 +88,15 @@ struct gm_ctx {
   double* obs = nullptr;
   double* obs_sigma = nullptr;
 
-  // ---- cell grid (cell edge >= cutoff)
-  int gx = 0, gy = 0, gz = 0;
-  double org[3] = {0, 0, 0};
-  double cell = 0;
-  int32_t* cell_start = nullptr;  // gx*gy*gz + 1
+  // ---- fields and their cell grids (cell edge >= the field's cutoff)
+  int32_t n_fields = 1;
+  std::vector<int64_t> h_fptr;    // internal row offset of each field (n_fields + 1)
+  std::vector<gm::FieldGrid> h_fgrid;
+  int64_t* fptr = nullptr;        // device copy of h_fptr
+  gm::FieldGrid* fgrid = nullptr; // device copy of h_fgrid
+  int32_t* field_of = nullptr;    // field of each internal star
+  int64_t n_cells = 0;
+  int32_t* cell_start = nullptr;  // n_cells + 1
 
   // ---- covariance, CSR over internal order
   bool built = false;
@@ -91,9 +106,13 @@ struct gm_ctx {
   void* val = nullptr;         // double (FP64) or float (FP32)
   gm::Buffer col_buf, val_buf;
   int64_t* diag_pos = nullptr;
-  // row-block tiles of K (FP32 mode): 32-row blocks, union columns, values
+  // row-block tiles of K (FP32 mode): 32-row blocks that never straddle a
+  // field (block b = rows blk_row0[b] .. blk_row0[b+1]-1), union columns, values
   gm::Buffer t_bptr, t_ucol, t_val;
   int64_t t_nblk = 0;
+  std::vector<int64_t> h_boff;     // first block of each field (n_fields + 1)
+  int64_t* boff = nullptr;         // device copy
+  int64_t* blk_row0 = nullptr;     // device, t_nblk + 1
   int64_t t_union = 0;
   double* kdiag = nullptr;
   double* prior_m = nullptr;
@@ -107,6 +126,11 @@ struct gm_ctx {
   void* gtab = nullptr;        // cubic coefficients of g (float4 / double4)
   double gtab_sigma2 = -1;
   int gtab_form = -1;
+
+  // ---- covariance surrogate (FP32 parameters, BF16 operand images)
+  float* mlp_params = nullptr;
+  unsigned char* mlp_img = nullptr;
+  bool mlp_trained = false;   // parameters set (by training or by the caller)
 
   // ---- EP state
   double* tau = nullptr;
@@ -122,9 +146,12 @@ struct gm_ctx {
   void* h_pinned = nullptr;    // 64 KB pinned host scratch
 
   gm::Workspace* ws = nullptr;
+  gm::PackState* pack = nullptr;
 
-  // ---- optional per-kernel timing (CUDA events on the context stream)
+  // ---- optional per-kernel timing (CUDA events on the context stream, or
+  // on prof_stream while a private stream is in use)
   bool prof_on = false;
+  cudaStream_t prof_stream = nullptr;
   const char* prof_pending = nullptr;
   struct ProfRec {
     const char* name;
@@ -190,8 +217,11 @@ void gauss_legendre(int n, double* x, double* w);
 void gauss_hermite(int n, double* x, double* w_times_expx2);
 
 // ---------------------------------------------------------------- stages
+// field_id: field of each caller star (device, int32) or null (one field).
 gm_status geometry_init(gm_ctx* c, const double* l, const double* b,
-                        const double* s, const double* obs, const double* sig);
+                        const double* s, const double* obs, const double* sig,
+                        const int32_t* field_id, const double* field_L0,
+                        const double* field_cut);
 // Ascending bitonic sort of n_pad (a power of two >= 1024) 64-bit keys.
 gm_status sort_u64(gm_ctx* c, unsigned long long* keys, int64_t n_pad);
 // Exclusive scan of n counts: out[0..n], out[n] = total.
@@ -202,10 +232,11 @@ gm_status unit_vectors(gm_ctx* c, int64_t n, const double* l, const double* b, d
 // Counts neighbours within the cutoff of each row, scans to row_ptr (n_rows+1)
 // and fills sorted column indices.  `self` marks rows that are the stars
 // themselves (diag_pos is then filled).
+// row_field: field of each row (null: field 0).
 gm_status neighbour_csr(gm_ctx* c, int64_t n_rows, const double* rs,
                         const double* rux, const double* ruy, const double* ruz,
-                        bool self, int64_t* row_ptr, Buffer& col_buf,
-                        int64_t* nnz_out, int64_t* diag_pos);
+                        const int32_t* row_field, bool self, int64_t* row_ptr,
+                        Buffer& col_buf, int64_t* nnz_out, int64_t* diag_pos);
 gm_status phi_points_init(gm_ctx* c);
 gm_status gtab_update(gm_ctx* c);
 // Pair quadrature for CSR entries; symmetric mode computes j >= i and
@@ -213,8 +244,16 @@ gm_status gtab_update(gm_ctx* c);
 // mode, K_ii and the prior mean.
 gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs,
                           const double* rux, const double* ruy, const double* ruz,
-                          const int64_t* row_ptr, const int32_t* col, int64_t nnz,
-                          void* val, bool symmetric);
+                          const int32_t* row_field, const int64_t* row_ptr,
+                          const int32_t* col, int64_t nnz, void* val, bool symmetric);
+// Quadrature for an explicit pair list (distances, chord): K untapered, FP64 out.
+gm_status pairlist_quadrature(gm_ctx* c, int64_t n, const double* si, const double* sj,
+                              const double* chord, double* out);
+// Copies each lower-triangle entry from its transpose (rows sorted).
+gm_status mirror_csr(gm_ctx* c, int64_t n, const int64_t* row_ptr, const int32_t* col, int64_t nnz,
+                     void* val);
+// Covariance values from the surrogate with quadrature fallback (gm_mlp.cu).
+gm_status surrogate_values(gm_ctx* c);
 // Diagonal-only quadrature (query self-covariance) into kss (FP64).
 gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* kss);
 
@@ -238,5 +277,11 @@ gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
 gm_status site_update(gm_ctx* c, double* max_delta, int64_t* skipped);
 
 void workspace_free(gm_ctx* c);
+
+// Packed per-field variance panels for multi-field contexts (gm_fields.cu).
+gm_status panels_fields(gm_ctx* c, const float* dv, const float* minv, const double* d64,
+                        double* var_out, int64_t* iters_out, double* resid_out);
+void pack_free(gm_ctx* c);
+void pack_invalidate(gm_ctx* c);
 
 }  // namespace gm

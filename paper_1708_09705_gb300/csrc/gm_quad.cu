@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(256) k_pair_quad(
     const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
     T* __restrict__ val, const double* __restrict__ gl_zeta, const double* __restrict__ gl_w,
     const void* __restrict__ gtab, TabF32 tf, TabF64 td, double* __restrict__ kdiag,
-    double* __restrict__ prior_m, unsigned* __restrict__ flags) {
+    double* __restrict__ prior_m, unsigned* __restrict__ flags, const FieldGrid* __restrict__ fg,
+    const int32_t* __restrict__ row_field) {
   extern __shared__ unsigned char smem[];
   typedef typename std::conditional<sizeof(T) == 4, float4, D4>::type T4;
   T* zq = reinterpret_cast<T*>(smem);
@@ -197,10 +198,12 @@ __global__ void __launch_bounds__(256) k_pair_quad(
     const int64_t i = lo;
     const int32_t j = col[e];
     if (P.symmetric && j < i) continue;
+    const FieldGrid& fgi = fg[row_field ? row_field[i] : 0];
+    const double inv_L0 = fgi.inv_L0, inv_cut = fgi.inv_cut;
     const double si = rs[i], sj = s[j];
     const double dx = rux[i] - ux[j], dy = ruy[i] - uy[j], dz = ruz[i] - uz[j];
     const double chord2 = fma(dx, dx, fma(dy, dy, dz * dz));
-    const T a = (T)(si * P.inv_L0), b = (T)(sj * P.inv_L0), c2 = (T)chord2;
+    const T a = (T)(si * inv_L0), b = (T)(sj * inv_L0), c2 = (T)chord2;
     // this lane's nodes on sightline j
     T tp[KPL], ctp[KPL], wp[KPL];
 #pragma unroll
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(256) k_pair_quad(
       if (P.taper == GM_TAPER_WENDLAND) {
         double ds = si - sj;
         double d = sqrt(fma(ds, ds, si * sj * chord2));
-        K *= wendland(d * P.inv_cut);
+        K *= wendland(d * inv_cut);
       }
       if (!isfinite(K)) atomicOr(flags, kFlagNonFinite);
       val[e] = (T)K;
@@ -391,7 +394,8 @@ static QuadParams quad_params(const gm_ctx* c, bool symmetric) {
 template <typename T, int KPL>
 static void launch_pair(gm_ctx* c, const QuadParams& P, int64_t n_rows, const double* rs,
                         const double* rux, const double* ruy, const double* ruz,
-                        const int64_t* row_ptr, const int32_t* col, int64_t nnz, void* val) {
+                        const int32_t* row_field, const int64_t* row_ptr, const int32_t* col,
+                        int64_t nnz, void* val) {
   size_t smem = 2 * kMaxNodes * sizeof(T);
   if (sizeof(T) == 4) smem += (size_t)(kTabF32.n_real() + 1) * sizeof(float4);
   auto kern = k_pair_quad<T, KPL>;
@@ -403,12 +407,14 @@ static void launch_pair(gm_ctx* c, const QuadParams& P, int64_t n_rows, const do
   GM_PROF(c, "k_pair_quad");
   kern<<<blocks, 256, smem, c->stream>>>(P, n_rows, rs, rux, ruy, ruz, c->s, c->ux, c->uy, c->uz,
                                          row_ptr, col, nnz, (T*)val, c->gl_zeta, c->gl_w, c->gtab,
-                                         tab_f32(), tab_f64(), c->kdiag, c->prior_m, c->d_flags);
+                                         tab_f32(), tab_f64(), c->kdiag, c->prior_m, c->d_flags,
+                                         c->fgrid, row_field);
 }
 
 gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, const double* rux,
-                          const double* ruy, const double* ruz, const int64_t* row_ptr,
-                          const int32_t* col, int64_t nnz, void* val, bool symmetric) {
+                          const double* ruy, const double* ruz, const int32_t* row_field,
+                          const int64_t* row_ptr, const int32_t* col, int64_t nnz, void* val,
+                          bool symmetric) {
   if (nnz == 0) return GM_OK;
   gm_status st = gtab_update(c);
   if (st != GM_OK) return st;
@@ -416,14 +422,14 @@ gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, const dou
   const int Q = c->cfg.n_nodes;
   const bool f32 = c->cfg.precision == GM_PREC_FP32;
   if (Q <= 32) {
-    if (f32) launch_pair<float, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
-    else launch_pair<double, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+    if (f32) launch_pair<float, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
+    else launch_pair<double, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
   } else if (Q <= 64) {
-    if (f32) launch_pair<float, 2>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
-    else launch_pair<double, 2>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+    if (f32) launch_pair<float, 2>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
+    else launch_pair<double, 2>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
   } else {
-    if (f32) launch_pair<float, 4>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
-    else launch_pair<double, 4>(c, P, n_rows, rs, rux, ruy, ruz, row_ptr, col, nnz, val);
+    if (f32) launch_pair<float, 4>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
+    else launch_pair<double, 4>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
   }
   GM_LAUNCH_CHECK(c);
   if (symmetric) {
@@ -433,6 +439,19 @@ gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, const dou
     else k_mirror<double><<<blocks, 256, 0, c->stream>>>(n_rows, row_ptr, col, nnz, (double*)val);
     GM_LAUNCH_CHECK(c);
   }
+  return GM_OK;
+}
+
+gm_status mirror_csr(gm_ctx* c, int64_t n, const int64_t* row_ptr, const int32_t* col, int64_t nnz,
+                     void* val) {
+  if (nnz == 0) return GM_OK;
+  int blocks = (int)std::min<int64_t>(ceil_div(nnz, 256), 16 * sm_count(c));
+  GM_PROF(c, "k_mirror");
+  if (c->cfg.precision == GM_PREC_FP32)
+    k_mirror<float><<<blocks, 256, 0, c->stream>>>(n, row_ptr, col, nnz, (float*)val);
+  else
+    k_mirror<double><<<blocks, 256, 0, c->stream>>>(n, row_ptr, col, nnz, (double*)val);
+  GM_LAUNCH_CHECK(c);
   return GM_OK;
 }
 
@@ -456,6 +475,116 @@ gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* k
     if (f32) GM_SELF(float, 4); else GM_SELF(double, 4);
   }
 #undef GM_SELF
+  GM_LAUNCH_CHECK(c);
+  return GM_OK;
+}
+
+}  // namespace gm
+
+namespace gm {
+
+// Sightline quadrature for an explicit list of pair geometries (distances
+// si, sj in pc, chord |u_i - u_j|): K = log1p(R) (or R) without the taper.
+// Same rule and kernel table as the covariance assembly; one warp per pair.
+template <typename T, int KPL>
+__global__ void __launch_bounds__(256) k_pairlist_quad(
+    QuadParams P, int64_t n, const double* __restrict__ si, const double* __restrict__ sj,
+    const double* __restrict__ chord, double* __restrict__ out,
+    const double* __restrict__ gl_zeta, const double* __restrict__ gl_w,
+    const void* __restrict__ gtab, TabF32 tf, TabF64 td) {
+  extern __shared__ unsigned char smem[];
+  typedef typename std::conditional<sizeof(T) == 4, float4, D4>::type T4;
+  T* zq = reinterpret_cast<T*>(smem);
+  T* wq = zq + kMaxNodes;
+  const T4* tab;
+  if (sizeof(T) == 4) {
+    float4* st = reinterpret_cast<float4*>(smem + 2 * kMaxNodes * sizeof(T));
+    const float4* gt = reinterpret_cast<const float4*>(gtab);
+    for (int k = threadIdx.x; k <= tf.last; k += blockDim.x) st[k] = gt[k];
+    tab = reinterpret_cast<const T4*>(st);
+  } else {
+    tab = reinterpret_cast<const T4*>(gtab);
+  }
+  for (int q = threadIdx.x; q < P.Q; q += blockDim.x) {
+    zq[q] = (T)gl_zeta[q];
+    wq[q] = (T)gl_w[q];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < n; p += nwarps) {
+    const T a = (T)(si[p] * P.inv_L0), b = (T)(sj[p] * P.inv_L0);
+    const T c2 = (T)(chord[p] * chord[p]);
+    T tp[KPL], ctp[KPL], wp[KPL];
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) {
+      int q = lane + 32 * k;
+      bool ok = q < P.Q;
+      tp[k] = ok ? b * zq[q] : (T)0;
+      ctp[k] = c2 * tp[k];
+      wp[k] = ok ? wq[q] : (T)0;
+    }
+    T acc = 0;
+    for (int q = 0; q < P.Q; ++q) {
+      const T t = a * zq[q];
+      T inner = 0;
+#pragma unroll
+      for (int k = 0; k < KPL; ++k) {
+        T d = t - tp[k];
+        T x = d * d + t * ctp[k];
+        T gv;
+        if (sizeof(T) == 4)
+          gv = (T)g_lookup(reinterpret_cast<const float4*>(tab), tf, (float)x);
+        else
+          gv = (T)g_lookup(reinterpret_cast<const D4*>(tab), td, (double)x);
+        inner += wp[k] * gv;
+      }
+      acc += wq[q] * inner;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      const double R = (double)acc;
+      out[p] = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
+    }
+  }
+}
+
+template <typename T, int KPL>
+static void launch_pairlist(gm_ctx* c, const QuadParams& P, int64_t n, const double* si,
+                            const double* sj, const double* chord, double* out) {
+  size_t smem = 2 * kMaxNodes * sizeof(T);
+  if (sizeof(T) == 4) smem += (size_t)(kTabF32.n_real() + 1) * sizeof(float4);
+  auto kern = k_pairlist_quad<T, KPL>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  int blocks = std::max(1, per_sm) * sm_count(c);
+  blocks = (int)std::min<int64_t>(blocks, std::max<int64_t>(1, ceil_div(n * 32, 256)));
+  kern<<<blocks, 256, smem, c->stream>>>(P, n, si, sj, chord, out, c->gl_zeta, c->gl_w, c->gtab,
+                                         tab_f32(), tab_f64());
+}
+
+gm_status pairlist_quadrature(gm_ctx* c, int64_t n, const double* si, const double* sj,
+                              const double* chord, double* out) {
+  if (n == 0) return GM_OK;
+  gm_status st = gtab_update(c);
+  if (st != GM_OK) return st;
+  QuadParams P = quad_params(c, false);
+  const int Q = c->cfg.n_nodes;
+  const bool f32 = c->cfg.precision == GM_PREC_FP32;
+  GM_PROF(c, "k_pairlist_quad");
+  if (Q <= 32) {
+    if (f32) launch_pairlist<float, 1>(c, P, n, si, sj, chord, out);
+    else launch_pairlist<double, 1>(c, P, n, si, sj, chord, out);
+  } else if (Q <= 64) {
+    if (f32) launch_pairlist<float, 2>(c, P, n, si, sj, chord, out);
+    else launch_pairlist<double, 2>(c, P, n, si, sj, chord, out);
+  } else {
+    if (f32) launch_pairlist<float, 4>(c, P, n, si, sj, chord, out);
+    else launch_pairlist<double, 4>(c, P, n, si, sj, chord, out);
+  }
   GM_LAUNCH_CHECK(c);
   return GM_OK;
 }

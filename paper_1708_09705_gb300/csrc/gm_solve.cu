@@ -943,7 +943,10 @@ gm_status refresh_posterior(gm_ctx* c) {
   double res_m = 0, res_v = 0;
   if (c->cfg.precision == GM_PREC_FP32) {
     s = posterior_mean<float, float>(c, &it_m, &res_m);
-    if (s == GM_OK)
+    if (s == GM_OK && c->n_fields > 1)
+      s = panels_fields(c, (const float*)W(c).dv.p, (const float*)W(c).minv.p,
+                        (const double*)W(c).d64.p, c->var, &it_v, &res_v);
+    else if (s == GM_OK)
       s = panels<float, float>(c, c->n, c->row_ptr, c->col, c->val, c->kdiag, c->var, &it_v, &res_v,
                                true);
   } else {

@@ -16,14 +16,25 @@ namespace gm {
 
 constexpr int kTile = 32;
 
+// Block of internal row i: blocks of kTile rows counted from each field's
+// first row, so that no block straddles two fields.
+__device__ __forceinline__ int64_t block_of(int64_t i, const int32_t* __restrict__ field_of,
+                                            const int64_t* __restrict__ fptr,
+                                            const int64_t* __restrict__ boff) {
+  const int f = field_of[i];
+  return boff[f] + (i - fptr[f]) / kTile;
+}
+
 __global__ void k_tile_keys(int64_t n, const int64_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col, int64_t nnz, int64_t n_pad,
+                            const int32_t* __restrict__ field_of, const int64_t* __restrict__ fptr,
+                            const int64_t* __restrict__ boff,
                             unsigned long long* __restrict__ keys) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < n; i += nw) {
-    const unsigned long long hi = (unsigned long long)(i / kTile) << 32;
+    const unsigned long long hi = (unsigned long long)block_of(i, field_of, fptr, boff) << 32;
     for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32)
       keys[e] = hi | (unsigned long long)(unsigned)col[e];
   }
@@ -67,13 +78,15 @@ template <typename TA, typename TT>
 __global__ void k_tile_fill(int64_t n, const int64_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col, const TA* __restrict__ val,
                             const int64_t* __restrict__ bptr, const int32_t* __restrict__ ucol,
-                            TT* __restrict__ tval) {
+                            const int32_t* __restrict__ field_of, const int64_t* __restrict__ fptr,
+                            const int64_t* __restrict__ boff,
+                            const int64_t* __restrict__ blk_row0, TT* __restrict__ tval) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < n; i += nw) {
-    const int64_t b = i / kTile;
-    const int t = (int)(i - b * kTile);
+    const int64_t b = block_of(i, field_of, fptr, boff);
+    const int t = (int)(i - blk_row0[b]);
     const int64_t u0 = bptr[b], u1 = bptr[b + 1];
     for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
       const int32_t j = col[e];
@@ -88,53 +101,107 @@ __global__ void k_tile_fill(int64_t n, const int64_t* __restrict__ row_ptr,
 }
 
 // Q = P + d o (K PD) over a panel of R columns, with K in tile form.
-// Warp = (32-column chunk, lane = column); a block's 8 warps take 8 chunks of
-// the same row block, so the value tile (128 B per union column) is shared
-// through L1.  Each warp keeps the 32 row accumulators of its block in
-// registers and prefetches the next gathered value.  pq partials per
-// (blockIdx.x, column).
+// A block = 8 warps = 8 chunks of 32 panel columns of the same row block.
+// Union columns are processed 32 at a time (a batch):
+//   * the block stages the batch's 32 x 32 value tile (4 KB) in shared memory;
+//   * each warp gathers the 32 panel rows PD[j, chunk] of the batch (32
+//     independent coalesced loads) into its own 32 x 32 shared tile;
+//   * each lane then accumulates a 4-row x 8-column piece of the warp's
+//     32 x 32 output with register outer products: per union column one
+//     float4 of values and two float4 of gathered panel values feed 32 FMAs.
+// pq partials per (blockIdx.x, column).
 __global__ void __launch_bounds__(256) k_panel_spmm_tiled(
-    int64_t n, int R, int64_t nblk, const int64_t* __restrict__ bptr,
+    int64_t n, int R, int64_t nblk, const int64_t* __restrict__ blk_row0,
+    const int64_t* __restrict__ bptr,
     const int32_t* __restrict__ ucol, const float* __restrict__ tval, const float* __restrict__ dv,
     const float* __restrict__ P, const float* __restrict__ PD, float* __restrict__ Q,
     double* __restrict__ part_pq) {
+  __shared__ float4 sA[kTile * kTile / 4];        // [union col k][32 rows]
+  __shared__ float4 sB[8][kTile * kTile / 4];     // per warp: [k][32 panel columns]
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int chunk = blockIdx.y * 8 + wib;
-  if (chunk * 32 >= R) return;
-  const int c = chunk * 32 + lane;
-  double pq = 0;
+  const bool live = chunk * 32 < R;  // idle warps still take part in the barriers
+  const int c0 = live ? chunk * 32 : 0;
+  const int rg = lane >> 2;          // rows 4*rg .. 4*rg+3
+  const int cg = lane & 3;           // columns 8*cg .. 8*cg+7
+  float* sBw = reinterpret_cast<float*>(sB[wib]);
+  double pq[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) pq[q] = 0.0;
   for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
-    float acc[kTile];
+    float acc[4][8];
 #pragma unroll
-    for (int t = 0; t < kTile; ++t) acc[t] = 0.f;
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
     const int64_t u0 = bptr[b], u1 = bptr[b + 1];
-    float pd_next = u0 < u1 ? PD[(int64_t)ucol[u0] * R + c] : 0.f;
-    for (int64_t u = u0; u < u1; ++u) {
-      const float pd = pd_next;
-      if (u + 1 < u1) pd_next = PD[(int64_t)ucol[u + 1] * R + c];
-      const float4* vv = reinterpret_cast<const float4*>(tval + u * kTile);
+    for (int64_t ub = u0; ub < u1; ub += 32) {
+      const int cnt = (u1 - ub) < 32 ? (int)(u1 - ub) : 32;
+      __syncthreads();  // previous batch fully read
+      {
+        const int k = threadIdx.x >> 3, q = threadIdx.x & 7;  // union column k, quarter q
+        sA[threadIdx.x] = k < cnt ? __ldg(reinterpret_cast<const float4*>(tval + (ub + k) * kTile) + q)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const int jl = lane < cnt ? ucol[ub + lane] : 0;
 #pragma unroll
-      for (int q = 0; q < kTile / 4; ++q) {
-        const float4 v = __ldg(vv + q);
-        acc[4 * q + 0] = fmaf(v.x, pd, acc[4 * q + 0]);
-        acc[4 * q + 1] = fmaf(v.y, pd, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(v.z, pd, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(v.w, pd, acc[4 * q + 3]);
+      for (int k = 0; k < 32; ++k) {
+        const int j = __shfl_sync(0xffffffffu, jl, k);
+        sBw[k * 32 + lane] = (live && k < cnt) ? PD[(int64_t)j * R + c0 + lane] : 0.f;
+      }
+      __syncthreads();  // value tile and gathered rows staged
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        const float4 a = sA[k * 8 + rg];
+        const float4 b0 = sB[wib][k * 8 + 2 * cg];
+        const float4 b1 = sB[wib][k * 8 + 2 * cg + 1];
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
       }
     }
+    if (live) {
+      double cs[8];
 #pragma unroll
-    for (int t = 0; t < kTile; ++t) {
-      const int64_t i = b * kTile + t;
-      if (i < n) {
-        const int64_t k = i * R + c;
-        const float pi = P[k];
-        const float qi = pi + dv[i] * acc[t];
-        Q[k] = qi;
-        pq += (double)pi * (double)qi;
+      for (int q = 0; q < 8; ++q) cs[q] = 0.0;
+      const int64_t r0b = blk_row0[b], r1b = blk_row0[b + 1];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int64_t i = r0b + 4 * rg + r;
+        if (i < r1b) {
+          const float di = dv[i];
+          const int64_t k0 = i * R + c0 + 8 * cg;
+          const float4 p0 = *reinterpret_cast<const float4*>(P + k0);
+          const float4 p1 = *reinterpret_cast<const float4*>(P + k0 + 4);
+          const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+          float qv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            qv[q] = pv[q] + di * acc[r][q];
+            cs[q] += (double)pv[q] * (double)qv[q];
+          }
+          *reinterpret_cast<float4*>(Q + k0) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+          *reinterpret_cast<float4*>(Q + k0 + 4) = make_float4(qv[4], qv[5], qv[6], qv[7]);
+        }
+      }
+      // column sums over the 8 row groups (lanes with equal cg)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        double v = cs[q];
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        pq[q] += v;
       }
     }
   }
-  part_pq[(int64_t)blockIdx.x * R + c] = pq;
+  if (live && rg == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) part_pq[(int64_t)blockIdx.x * R + c0 + 8 * cg + q] = pq[q];
+  }
 }
 
 gm_status tiles_build(gm_ctx* c) {
@@ -142,7 +209,27 @@ gm_status tiles_build(gm_ctx* c) {
   cudaStream_t st = c->stream;
   const int sms = sm_count(c);
   const int64_t n = c->n, nnz = c->nnz;
-  const int64_t nblk = ceil_div(n, kTile);
+  // field-aligned blocks
+  const int nf = c->n_fields;
+  c->h_boff.assign(nf + 1, 0);
+  for (int f = 0; f < nf; ++f)
+    c->h_boff[f + 1] = c->h_boff[f] + ceil_div(c->h_fptr[f + 1] - c->h_fptr[f], kTile);
+  const int64_t nblk = c->h_boff[nf];
+  {
+    std::vector<int64_t> r0(nblk + 1);
+    for (int f = 0; f < nf; ++f)
+      for (int64_t b = c->h_boff[f]; b < c->h_boff[f + 1]; ++b)
+        r0[b] = c->h_fptr[f] + (b - c->h_boff[f]) * kTile;
+    r0[nblk] = n;
+    if (!c->boff) c->boff = (int64_t*)dev_alloc(c, (nf + 1) * sizeof(int64_t));
+    if (!c->blk_row0) c->blk_row0 = (int64_t*)dev_alloc(c, (nblk + 1) * sizeof(int64_t));
+    if (!c->boff || !c->blk_row0) return set_error(c, GM_E_NOMEM, "tile blocks");
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(c->boff, c->h_boff.data(), (nf + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, st));
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(c->blk_row0, r0.data(), (nblk + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, st));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  }
   int64_t n_pad = 1024;
   while (n_pad < nnz) n_pad <<= 1;
   unsigned long long* keys = (unsigned long long*)dev_alloc(c, n_pad * sizeof(unsigned long long));
@@ -152,7 +239,8 @@ gm_status tiles_build(gm_ctx* c) {
   const int wb = (int)std::min<int64_t>(ceil_div(n * 32, 256), 16 * sms);
   const int eb = (int)std::min<int64_t>(ceil_div(nnz, 256), 16 * sms);
   GM_PROF(c, "k_tile_keys");
-  k_tile_keys<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, nnz, n_pad, keys);
+  k_tile_keys<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, nnz, n_pad, c->field_of, c->fptr, c->boff,
+                                  keys);
   GM_LAUNCH_CHECK(c);
   gm_status s = sort_u64(c, keys, n_pad);
   if (s != GM_OK) return s;
@@ -182,7 +270,7 @@ gm_status tiles_build(gm_ctx* c) {
   GM_CUDA_CHECK(c, cudaMemsetAsync(tv, 0, (size_t)U * kTile * sizeof(float), st));
   GM_PROF(c, "k_tile_fill");
   k_tile_fill<float, float><<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, (const float*)c->val, bptr,
-                                               ucol, tv);
+                                               ucol, c->field_of, c->fptr, c->boff, c->blk_row0, tv);
   GM_LAUNCH_CHECK(c);
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
   dev_free_now(c, ublk, std::max<int64_t>(U, 1) * sizeof(int32_t));
@@ -198,7 +286,8 @@ gm_status panel_spmm_tiled(gm_ctx* c, int64_t n, int R, int nbx, const float* dv
                            const float* PD, float* Q, double* part_pq) {
   dim3 grid(nbx, (unsigned)ceil_div(R / 32, 8));
   GM_PROF(c, "k_panel_spmm_tiled");
-  k_panel_spmm_tiled<<<grid, 256, 0, c->stream>>>(n, R, c->t_nblk, (const int64_t*)c->t_bptr.p,
+  k_panel_spmm_tiled<<<grid, 256, 0, c->stream>>>(n, R, c->t_nblk, c->blk_row0,
+                                                  (const int64_t*)c->t_bptr.p,
                                                   (const int32_t*)c->t_ucol.p,
                                                   (const float*)c->t_val.p, dv, P, PD, Q, part_pq);
   GM_LAUNCH_CHECK(c);

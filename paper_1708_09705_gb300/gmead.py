@@ -23,16 +23,19 @@ PREC_FP64, PREC_FP32 = 0, 1
 FORM_LOGNORMAL, FORM_LINEAR = 0, 1
 TAPER_WENDLAND, TAPER_HARD = 0, 1
 LIK_GAUSS_IN_A, LIK_GAUSS_IN_LNA = 0, 1
+COV_QUADRATURE, COV_SURROGATE = 0, 1
 
 STATUS = {0: "GM_OK", 1: "GM_E_INVAL", 2: "GM_E_NOMEM", 3: "GM_E_CUDA", 4: "GM_E_NOT_SPD",
           5: "GM_E_NOCONV", 6: "GM_E_NONFINITE", 7: "GM_E_TIMEOUT", 8: "GM_E_STATE"}
 
 # every symbol include/gmead.h declares
-EXPORTS = ["gm_config_default", "gm_ep_init", "gm_build_cov", "gm_ep_sweep", "gm_predict",
+EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov", "gm_ep_sweep", "gm_predict",
            "gm_get_posterior", "gm_get_sites", "gm_set_sites", "gm_get_prior", "gm_get_perm",
            "gm_get_csr", "gm_get_stats", "gm_stream", "gm_status_str", "gm_last_error",
            "gm_destroy", "gm_profile", "gm_kernel_time_count", "gm_kernel_time",
-           "gm_site_update_noalloc"]
+           "gm_site_update_noalloc", "gm_surrogate_param_count", "gm_surrogate_set_params",
+           "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
+           "gm_surrogate_grad"]
 
 
 class GmError(RuntimeError):
@@ -46,7 +49,9 @@ class Config(C.Structure):
                 ("cutoff_pc", C.c_double), ("n_nodes", C.c_int32), ("form", C.c_int32),
                 ("taper", C.c_int32), ("precision", C.c_int32), ("likelihood", C.c_int32),
                 ("cg_max_iter", C.c_int32), ("damping", C.c_double), ("vc_floor", C.c_double),
-                ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("warm_start", C.c_int32)]
+                ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("warm_start", C.c_int32),
+                ("cov_source", C.c_int32), ("reserved", C.c_int32),
+                ("surrogate_gate", C.c_double)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -62,7 +67,9 @@ class Stats(C.Structure):
                 ("cg_iters_mean", C.c_int64), ("cg_iters_var", C.c_int64),
                 ("sites_skipped", C.c_int64), ("kernel_launches", C.c_int64),
                 ("last_max_delta", C.c_double), ("cg_resid_mean", C.c_double),
-                ("cg_resid_var", C.c_double)]
+                ("cg_resid_var", C.c_double), ("surrogate_fallback", C.c_int64),
+                ("surrogate_loss", C.c_double), ("surrogate_val_rmse", C.c_double),
+                ("surrogate_gate_frac", C.c_double)]
 
 
 _lib = None
@@ -81,6 +88,8 @@ def lib():
         L.gm_config_default.restype = None
         L.gm_ep_init.argtypes = [C.POINTER(vp), C.POINTER(Config), i64, vp, vp, vp, vp, vp, vp,
                                  C.POINTER(Allocator)]
+        L.gm_ep_init_fields.argtypes = [C.POINTER(vp), C.POINTER(Config), i64, vp, vp, vp, vp, vp,
+                                        i32, vp, vp, vp, vp, C.POINTER(Allocator)]
         L.gm_build_cov.argtypes = [vp, C.POINTER(i64)]
         L.gm_ep_sweep.argtypes = [vp, i32, dbl, C.POINTER(i32), C.POINTER(dbl)]
         L.gm_predict.argtypes = [vp, i64, vp, vp, vp, vp, vp]
@@ -98,6 +107,13 @@ def lib():
         L.gm_destroy.argtypes = [vp]
         L.gm_destroy.restype = None
         L.gm_profile.argtypes = [vp, i32]
+        L.gm_surrogate_param_count.argtypes = []
+        L.gm_surrogate_param_count.restype = i64
+        L.gm_surrogate_set_params.argtypes = [vp, vp, i64]
+        L.gm_surrogate_get_params.argtypes = [vp, vp, i64]
+        L.gm_surrogate_eval.argtypes = [vp, i64, vp, vp, vp, dbl, dbl, vp, vp]
+        L.gm_surrogate_train.argtypes = [vp, i64, i32, i32, dbl, C.c_uint64]
+        L.gm_surrogate_grad.argtypes = [vp, i64, vp, vp, dbl, vp, C.POINTER(dbl)]
         L.gm_site_update_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, vp, i32, dbl, dbl, vp,
                                              C.POINTER(dbl), C.POINTER(i64)]
         L.gm_site_update_noalloc.restype = C.c_int
@@ -105,9 +121,11 @@ def lib():
         L.gm_kernel_time_count.restype = i32
         L.gm_kernel_time.argtypes = [vp, i32, C.POINTER(C.c_char_p), C.POINTER(i64),
                                      C.POINTER(dbl)]
-        for f in ("gm_ep_init", "gm_build_cov", "gm_ep_sweep", "gm_predict", "gm_get_posterior",
+        for f in ("gm_ep_init", "gm_ep_init_fields", "gm_build_cov", "gm_ep_sweep", "gm_predict", "gm_get_posterior",
                   "gm_get_sites", "gm_set_sites", "gm_get_prior", "gm_get_perm", "gm_get_csr",
-                  "gm_get_stats", "gm_profile", "gm_kernel_time"):
+                  "gm_get_stats", "gm_profile", "gm_kernel_time", "gm_surrogate_set_params",
+                  "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
+                  "gm_surrogate_grad"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -245,6 +263,41 @@ class Context:
             out[name.value.decode()] = (cnt.value, ms.value)
         return out
 
+    # ---- covariance surrogate
+    def surrogate_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(lib().gm_surrogate_set_params(self._h, p.ctypes.data, p.size))
+
+    def surrogate_get_params(self):
+        out = np.empty(lib().gm_surrogate_param_count(), dtype=np.float32)
+        self._check(lib().gm_surrogate_get_params(self._h, out.ctypes.data, out.size))
+        return out
+
+    def surrogate_eval(self, si, sj, chord, sigma2, L0):
+        a, ka = _ptr(si)
+        b, kb = _ptr(sj)
+        c, kc = _ptr(chord)
+        n = len(ka)
+        y = np.empty(n, dtype=np.float32)
+        e = np.empty(n, dtype=np.float32)
+        self._check(lib().gm_surrogate_eval(self._h, n, a, b, c, float(sigma2), float(L0),
+                                            y.ctypes.data, e.ctypes.data))
+        return y, e
+
+    def surrogate_train(self, n_pairs=1_000_000, steps=4000, batch=8192, lr=2e-3, seed=1):
+        self._check(lib().gm_surrogate_train(self._h, int(n_pairs), int(steps), int(batch),
+                                             float(lr), int(seed)))
+        return self.stats()
+
+    def surrogate_grad(self, X, Y, lam):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        g = np.empty(lib().gm_surrogate_param_count(), dtype=np.float32)
+        loss = C.c_double()
+        self._check(lib().gm_surrogate_grad(self._h, len(Y), X.ctypes.data, Y.ctypes.data,
+                                            float(lam), g.ctypes.data, C.byref(loss)))
+        return loss.value, g
+
     @property
     def stream(self) -> int:
         return lib().gm_stream(self._h) or 0
@@ -267,11 +320,12 @@ class Context:
         self.close()
 
 
-def ep_init(cfg: Config, l, b, s, obs, obs_sigma, stream=None, torch_alloc=True) -> Context:
-    """Create a context (gm_ep_init).  `stream` is a cudaStream_t as int, a
-    torch.cuda.Stream, or None for torch's current stream when torch is
-    loaded.  With torch_alloc, device memory comes from torch's caching
-    allocator."""
+def ep_init(cfg: Config, l, b, s, obs, obs_sigma, stream=None, torch_alloc=True,
+            field_id=None, field_L0=None, field_cutoff=None) -> Context:
+    """Create a context (gm_ep_init, or gm_ep_init_fields when field_id is
+    given).  `stream` is a cudaStream_t as int, a torch.cuda.Stream, or None
+    for torch's current stream when torch is loaded.  With torch_alloc,
+    device memory comes from torch's caching allocator."""
     L = lib()
     keep = []
     ptrs = []
@@ -304,7 +358,18 @@ def ep_init(cfg: Config, l, b, s, obs, obs_sigma, stream=None, torch_alloc=True)
     except ImportError:
         sptr = int(stream or 0)
     h = C.c_void_p()
-    st = L.gm_ep_init(C.byref(h), C.byref(cfg), int(n), *ptrs, C.c_void_p(sptr), alloc_ptr)
+    if field_id is None:
+        st = L.gm_ep_init(C.byref(h), C.byref(cfg), int(n), *ptrs, C.c_void_p(sptr), alloc_ptr)
+    else:
+        fid = np.ascontiguousarray(field_id, dtype=np.int32)
+        nf = int(fid.max()) + 1 if field_L0 is None else len(field_L0)
+        fL0 = None if field_L0 is None else np.ascontiguousarray(field_L0, dtype=np.float64)
+        fct = None if field_cutoff is None else np.ascontiguousarray(field_cutoff, dtype=np.float64)
+        keep += [fid, fL0, fct]
+        st = L.gm_ep_init_fields(C.byref(h), C.byref(cfg), int(n), *ptrs, nf, fid.ctypes.data,
+                                 None if fL0 is None else fL0.ctypes.data,
+                                 None if fct is None else fct.ctypes.data, C.c_void_p(sptr),
+                                 alloc_ptr)
     ctx = Context(h, n, keep)
     if st != 0:
         msg = L.gm_last_error(h).decode() if h else STATUS.get(st, str(st))

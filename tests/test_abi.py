@@ -40,7 +40,8 @@ def test_status_strings_and_defaults(L):
     assert cfg.sigma2 == 1.0 and cfg.outer_scale_pc == 20.0 and cfg.cutoff_pc == 60.0
     assert cfg.precision == gm.PREC_FP64 and cfg.taper == gm.TAPER_WENDLAND
     assert cfg.warm_start == 1 and cfg.rhs_panel == 0
-    assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2
+    assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2 + 4 * 2 + 8
+    assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-3
 
 
 def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
@@ -56,6 +57,17 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
                        ("precision", 7), ("outer_scale_pc", float("nan")), ("warm_start", 2)):
         c2 = gm.default_config(**{field: bad})
         assert L.gm_ep_init(C.byref(h), C.byref(c2), 4, x, x, x, x, x, None, None) == 1, field
+    assert not h.value
+    # several fields: field ids required, FP32 form only, positive field scales
+    fid = (C.c_int32 * 4)(0, 1, 0, 1)
+    L0 = (C.c_double * 2)(20.0, -1.0)
+    c32 = gm.default_config(precision=gm.PREC_FP32)
+    assert L.gm_ep_init_fields(C.byref(h), C.byref(c32), 4, x, x, x, x, x, 2, None, None, None,
+                               None, None) == 1
+    assert L.gm_ep_init_fields(C.byref(h), C.byref(cfg), 4, x, x, x, x, x, 2, fid, None, None,
+                               None, None) == 1
+    assert L.gm_ep_init_fields(C.byref(h), C.byref(c32), 4, x, x, x, x, x, 2, fid, L0, None,
+                               None, None) == 1
     assert not h.value
     # calls on a null context
     assert L.gm_build_cov(None, None) == 1
