@@ -95,8 +95,9 @@ typedef struct {
                              within cg_tol, not bit for bit); 0: cold start   */
   int32_t cov_source;     /* GM_COV_QUADRATURE or GM_COV_SURROGATE            */
   int32_t reserved;
-  double surrogate_gate;  /* surrogate entries whose estimated relative error
-                             exceeds this are recomputed by quadrature         */
+  double surrogate_gate;  /* surrogate entries whose estimated absolute error
+                             after the taper, W K |y - y_true|, exceeds this
+                             are recomputed by quadrature (default 1e-4)      */
 } gm_config;
 
 /* Device memory hooks.  When given, every device allocation of the context
@@ -123,7 +124,8 @@ typedef struct {
   int64_t surrogate_fallback; /* entries recomputed by quadrature (last build) */
   double surrogate_loss;   /* final training loss (last gm_surrogate_train)    */
   double surrogate_val_rmse; /* RMSE of ln K on fresh pairs, tensor-core path  */
-  double surrogate_gate_frac; /* fraction of those pairs above the gate        */
+  double surrogate_gate_frac; /* fraction of those pairs above the gate
+                                (estimated error with the taper applied)    */
 } gm_stats;
 
 /* Fills *cfg with defaults: sigma2 1, L0 20 pc, rho_bar 1e-3 mag/pc, cutoff
@@ -228,8 +230,8 @@ gm_status gm_kernel_time(gm_ctx* ctx, int32_t k, const char** name, int64_t* lau
 
 /* Covariance surrogate (no counterpart in the paper, which evaluates every
  * entry by the sightline integral of Sect. 3): an MLP with 5 inputs (the
- * pair's scale-free geometry ln(min(s)/L0)/4, ln(max(s)/L0)/4,
- * ln(1e-3 + |u_i - u_j| sqrt(s_i s_j)/L0)/4, sigma2 and ln(L0/20 pc)), three
+ * pair's scale-free geometry ln(sqrt(s_i s_j)/L0)/4, |s_i - s_j|/(3 L0),
+ * |u_i - u_j| sqrt(s_i s_j)/(3 L0), sigma2 and ln(L0/20 pc)), three
  * hidden layers of 64 SiLU units and 2 outputs: y = ln K (K = log1p(R)
  * before the taper) and e, an estimate of ln |y - y_true|.  It runs on the
  * tensor cores with BF16 operands and FP32 accumulation.

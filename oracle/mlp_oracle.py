@@ -7,12 +7,16 @@ The paper computes every covariance entry from the sightline integral
 (Sect. 3); the surrogate is this project's approximation of that integral,
 trained on the quadrature and judged by it.  Network: 5 inputs -> 3 hidden
 layers of 64 units with SiLU -> 2 outputs (the prediction y and a log error
-estimate e).  Inputs are the scale-free features of a pair:
-    f1 = ln(min(s_i, s_j)/L0) / 4,   f2 = ln(max(s_i, s_j)/L0) / 4,
-    f3 = ln(1e-3 + |u_i - u_j| sqrt(s_i s_j)/L0) / 4,   f4 = sigma2,   f5 = ln(L0 / 20 pc)
+estimate e).  Inputs are the scale-free geometry of the pair in units of L0:
+    f1 = ln(sqrt(s_i s_j)/L0) / 4          (mean distance),
+    f2 = |s_i - s_j| / (3 L0)              (offset along the sightlines),
+    f3 = |u_i - u_j| sqrt(s_i s_j) / (3 L0) (transverse offset),
+    f4 = sigma2,   f5 = ln(L0 / 20 pc)
 and the target is y = ln K (K = log1p(R), before the taper).  The loss is
-    mean (y_pred - y)^2 + lambda * mean (e_pred - ln(|y_pred - y| + 1e-5))^2
-with no gradient flowing from the second term into y_pred.
+    mean (y_pred - y)^2 + lambda * mean rho_q(ln(|y_pred - y| + 1e-5) - e_pred)
+with rho_q(u) = u (q - [u < 0]) the pinball (quantile) loss at q = 0.95, so
+that e_pred estimates an upper quantile of the log error (Koenker & Bassett
+1978), and no gradient flowing from the second term into y_pred.
 """
 from __future__ import annotations
 
@@ -21,17 +25,18 @@ import numpy as np
 N_IN, N_HID, N_OUT = 5, 64, 2
 LAYERS = [(N_IN, N_HID), (N_HID, N_HID), (N_HID, N_HID), (N_HID, N_OUT)]
 ERR_FLOOR = 1e-5
+ERR_QUANTILE = 0.95
 
 
 def features(si, sj, chord, sigma2, L0):
     """Scale-free pair features (see module docstring), shape (P, 5)."""
     si, sj = np.asarray(si, float), np.asarray(sj, float)
-    a, b = np.minimum(si, sj) / L0, np.maximum(si, sj) / L0
-    tr = np.asarray(chord, float) * np.sqrt(si * sj) / L0
-    L0 = np.broadcast_to(np.asarray(L0, float), a.shape)
-    return np.stack([np.log(a) / 4, np.log(b) / 4, np.log(1e-3 + tr) / 4,
-                     np.broadcast_to(np.asarray(sigma2, float), a.shape),
-                     np.log(L0 / 20.0)], axis=1)
+    L0a = np.broadcast_to(np.asarray(L0, float), si.shape)
+    gm = np.sqrt(si * sj) / L0a
+    return np.stack([np.log(gm) / 4, np.abs(si - sj) / (3 * L0a),
+                     np.asarray(chord, float) * gm / 3,
+                     np.broadcast_to(np.asarray(sigma2, float), si.shape),
+                     np.log(L0a / 20.0)], axis=1)
 
 
 def init_params(seed=0):
@@ -70,8 +75,10 @@ def loss_and_grads(params, X, y, lam=0.1, err_target=None):
     yp, ep = out[:, 0], out[:, 1]
     r = yp - y
     et = np.log(np.abs(r) + ERR_FLOOR) if err_target is None else err_target
-    loss = np.mean(r * r) + lam * np.mean((ep - et) ** 2)
-    g_out = np.stack([2.0 * r / P, lam * 2.0 * (ep - et) / P], axis=1)
+    u = et - ep                                   # > 0: error under-estimated
+    wq = np.where(u > 0, ERR_QUANTILE, ERR_QUANTILE - 1.0)
+    loss = np.mean(r * r) + lam * np.mean(u * wq)
+    g_out = np.stack([2.0 * r / P, -lam * wq / P], axis=1)
     grads = [None] * len(params)
     g = g_out
     for k in range(len(params) - 1, -1, -1):

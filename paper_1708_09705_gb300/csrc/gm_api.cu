@@ -249,7 +249,7 @@ void gm_config_default(gm_config* f) {
   f->rhs_panel = 0;
   f->warm_start = 1;
   f->cov_source = GM_COV_QUADRATURE;
-  f->surrogate_gate = 1e-3;
+  f->surrogate_gate = 1e-4;
 }
 
 const char* gm_status_str(gm_status s) {

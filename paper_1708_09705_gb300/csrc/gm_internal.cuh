@@ -12,7 +12,6 @@
 namespace gm {
 
 // ---------------------------------------------------------------- constants
-constexpr int kWarp = 32;
 constexpr int kGH = 64;          // Gauss-Hermite nodes of the tilted rule
 constexpr int kMaxNodes = 128;   // Gauss-Legendre nodes per sightline (max)
 

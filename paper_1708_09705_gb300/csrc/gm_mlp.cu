@@ -118,15 +118,15 @@ struct MlpIn {
   double L0;
 };
 
-// Scale-free features of a pair (same definition as the surrogate's CPU
-// statement): ln(min/L0)/4, ln(max/L0)/4, ln(1e-3 + chord sqrt(si sj)/L0)/4,
-// sigma2, ln(L0 / 20 pc).
+// Scale-free geometry of a pair in units of L0: ln(mean distance)/4, offset
+// along the sightlines /3, transverse offset at the mean distance /3, then
+// sigma2 and ln(L0 / 20 pc).
 __device__ __forceinline__ void pair_features(double si, double sj, double chord, double sigma2,
                                               double L0, float* f) {
-  const double a = fmin(si, sj) / L0, b = fmax(si, sj) / L0;
-  f[0] = (float)(0.25 * log(a));
-  f[1] = (float)(0.25 * log(b));
-  f[2] = (float)(0.25 * log(1e-3 + chord * sqrt(si * sj) / L0));
+  const double g = sqrt(si * sj) / L0;
+  f[0] = (float)(0.25 * log(g));
+  f[1] = (float)(fabs(si - sj) / (3.0 * L0));
+  f[2] = (float)(chord * g / 3.0);
   f[3] = (float)sigma2;
   f[4] = (float)log(L0 / 20.0);
 }
@@ -402,10 +402,14 @@ extern "C" gm_status gm_surrogate_eval(gm_ctx* c, int64_t n, const double* si, c
 
 // ---------------------------------------------------------------------------
 // Training (FP32 on the CUDA cores): targets from the sightline quadrature,
-// loss  mean (y - ln K)^2 + lambda mean (e - ln(|y - ln K| + 1e-5))^2  with the
-// error target held fixed, mini-batches drawn with replacement, Adam.
+// loss  mean (y - ln K)^2 + lambda mean rho_q(ln(|y - ln K| + 1e-5) - e), with
+// rho_q(u) = u (q - [u < 0]) the pinball loss at q = 0.95 (so that e tracks an
+// upper quantile of the log error, not its mean) and the error target held
+// fixed; mini-batches drawn with replacement, Adam.
 // ---------------------------------------------------------------------------
 namespace gm {
+
+constexpr float kErrQuantile = 0.95f;
 
 // SplitMix64 (Steele, Lea & Flood 2014): a counter-based stream of 64-bit words.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -523,10 +527,13 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_bwd(int64_t n_data, int B, int 
     }
     const float r = out[0] - Y[p];
     const float et = logf(fabsf(r) + 1e-5f);
-    const float q = out[1] - et;
+    // pinball loss of the error head at quantile kErrQuantile: u > 0 when the
+    // head under-estimates the error
+    const float u = et - out[1];
+    const float wq = u > 0.f ? kErrQuantile : kErrQuantile - 1.f;
     l1 = (double)r * r;
-    l2 = (double)q * q;
-    const float g0 = 2.0f * r / (float)B, g1 = lam * 2.0f * q / (float)B;
+    l2 = (double)(u * wq);
+    const float g0 = 2.0f * r / (float)B, g1 = -lam * wq / (float)B;
     dout[0] = g0;
     dout[1] = g1;
     for (int k = 0; k < 64; ++k) dz3[k] = (W4[k * 2] * g0 + W4[k * 2 + 1] * g1) * dsilu_f(z3[k]);
@@ -796,6 +803,10 @@ extern "C" gm_status gm_surrogate_train(gm_ctx* c, int64_t n_pairs, int32_t step
   st = mlp_forward(c, in, yv, ev);
   if (st != GM_OK) return st;
   std::vector<float> hy(nv), he(nv), ht(nv);
+  std::vector<double> hsi(nv), hsj(nv), hch(nv);
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(hsi.data(), si + n, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(hsj.data(), sj + n, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(hch.data(), ch + n, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
   GM_CUDA_CHECK(c, cudaMemcpyAsync(hy.data(), yv, nv * sizeof(float), cudaMemcpyDeviceToHost, s));
   GM_CUDA_CHECK(c, cudaMemcpyAsync(he.data(), ev, nv * sizeof(float), cudaMemcpyDeviceToHost, s));
   GM_CUDA_CHECK(c, cudaMemcpyAsync(ht.data(), Y + n, nv * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -805,7 +816,14 @@ extern "C" gm_status gm_surrogate_train(gm_ctx* c, int64_t n_pairs, int32_t step
   for (int64_t k = 0; k < nv; ++k) {
     const double d = (double)hy[k] - (double)ht[k];
     se += d * d;
-    if (std::exp((double)he[k]) > c->cfg.surrogate_gate) ++above;
+    // estimated error of the stored entry, with the taper at the pair's separation
+    double w = 1.0;
+    if (c->cfg.taper == GM_TAPER_WENDLAND) {
+      const double dl = hsi[k] - hsj[k];
+      const double h = std::sqrt(dl * dl + hsi[k] * hsj[k] * hch[k] * hch[k]) / c->cfg.cutoff_pc;
+      w = h >= 1.0 ? 0.0 : std::pow(1.0 - h, 4) * (4.0 * h + 1.0);
+    }
+    if (w * std::exp((double)hy[k] + (double)he[k]) > c->cfg.surrogate_gate) ++above;
   }
   c->stats.surrogate_loss = last_loss;
   c->stats.surrogate_val_rmse = std::sqrt(se / nv);
@@ -878,13 +896,13 @@ __global__ void k_surrogate_apply(int64_t np, const int64_t* __restrict__ pe,
     const int64_t ee = pe[p];
     const bool diag = col[ee] == prow[p];
     const float yp = y[p], ep = e[p];
-    const bool fb = diag || !isfinite(yp) || !isfinite(ep) || (double)ep > loggate;
+    // estimated absolute error of the stored (tapered) entry:
+    // W K |y - y_true| = W exp(y + e)
+    const double w = taper == GM_TAPER_WENDLAND ? taper_w(pdist[p] * inv_cut) : 1.0;
+    const bool fb = diag || !isfinite(yp) || !isfinite(ep) ||
+                    !((double)yp + (double)ep + log(w) <= loggate);
     flag[p] = fb ? 1 : 0;
-    if (!fb) {
-      double K = exp((double)yp);
-      if (taper == GM_TAPER_WENDLAND) K *= taper_w(pdist[p] * inv_cut);
-      val[ee] = (T)K;
-    }
+    if (!fb) val[ee] = (T)(w * exp((double)yp));
   }
 }
 

@@ -41,7 +41,7 @@ def test_status_strings_and_defaults(L):
     assert cfg.precision == gm.PREC_FP64 and cfg.taper == gm.TAPER_WENDLAND
     assert cfg.warm_start == 1 and cfg.rhs_panel == 0
     assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2 + 4 * 2 + 8
-    assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-3
+    assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-4
 
 
 def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
