@@ -64,6 +64,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-forms", action="store_true")
+    p.add_argument("--probe", type=float, default=2.0,
+                   help="probed variances: colour classes at least this many cutoffs apart "
+                        "share one solve (0 = exact, one solve per star)")
+    p.add_argument("--no-exact", action="store_true",
+                   help="skip the one-step exact-variance comparison")
     p.add_argument("--workload", default="c2", choices=["c2", "c4_fields"],
                    help="c2: the 20,000-star field (bench line); c4_fields: 256 independent "
                         "fields solved together (batched path)")
@@ -223,6 +228,7 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
     ref = None
     forms = [("plain_fp64", dict(precision=gm.PREC_FP64, cg_tol=1e-10)),
              ("plain_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6)),
+             ("probed_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6, probe_factor=2.0)),
              ("learned_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
                                    cov_source=gm.COV_SURROGATE))]
     for name, kw in forms:
@@ -252,6 +258,8 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
         rec = {"site_updates_per_s": n_sub * sweeps / t_all,
                "pairs_per_s": st["n_pairs"] / t_cov,
                "max_abs_err_mean_lnA_vs_fp64": float(np.max(np.abs(mu - ref)))}
+        if kw.get("probe_factor"):
+            rec["probe_colours"] = st["probe_colours"]
         if train_s is not None:
             rec.update(train_s=train_s, surrogate_val_rmse=st["surrogate_val_rmse"],
                        surrogate_gate_frac=st["surrogate_gate_frac"],
@@ -259,7 +267,10 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
                        unique_pairs=st["n_pairs"])
         out[name] = rec
     return {"stars": n_sub, "sweeps": sweeps, "forms": out,
-            "equal_error_bar": "1e-3 in mean ln A vs the FP64 plain form"}
+            "equal_error_bar": "1e-3 in mean ln A vs the FP64 plain form",
+            "notes": "plain = exact variances (one solve per star); probed = colour classes "
+                     "2 cutoffs apart share a solve; learned = surrogate K with quadrature "
+                     "fallback at the gate"}
 
 
 def run_fields(a):
@@ -279,7 +290,7 @@ def run_fields(a):
     L0 = np.array([f["outer_scale_pc"] for f in fields])
     n = len(fid)
     cfg = gm.default_config(sigma2=1.0, rho_bar=1e-3, n_nodes=64, precision=gm.PREC_FP32,
-                            cg_tol=1e-6)
+                            cg_tol=1e-6, probe_factor=a.probe)
     ctx = gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"],
                      field_id=fid, field_L0=L0, field_cutoff=3 * L0)
     for _ in range(a.warmup):
@@ -309,7 +320,10 @@ def run_fields(a):
            "config": {"workload": "c4_fields: 256 independent fields, star counts log-uniform "
                                   "500-8000, sides 1-3 deg, outer scales 10-40 pc, cutoff 3 L0, "
                                   "64 nodes", "n_stars": n, "n_fields": 256,
-                      "sweeps_per_step": a.sweeps, "nnz": st["nnz"]},
+                      "sweeps_per_step": a.sweeps, "nnz": st["nnz"],
+                      "variances": (f"probed: classes {a.probe:g} cutoffs apart share a solve, "
+                                    f"{st['probe_colours']} classes" if a.probe > 0
+                                    else "exact: one solve per star")},
            "cg_iters_var_last": st["cg_iters_var"],
            "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in
                           sorted(kt.items(), key=lambda kv: -kv[1][1])[:8]}}
@@ -331,7 +345,7 @@ def run_gpu(a):
     cat = make_catalogue(WORKLOAD, n=a.n, seed=rank)
     n = len(cat["s"])
     prec = gm.PREC_FP32 if a.precision == "fp32" else gm.PREC_FP64
-    cfg = gm.config_from_catalogue(cat, precision=prec,
+    cfg = gm.config_from_catalogue(cat, precision=prec, probe_factor=a.probe,
                                    cg_tol=1e-6 if a.precision == "fp32" else 1e-10)
     D = {k: torch.tensor(cat[k], dtype=torch.float64, device=dev)
          for k in ("l", "b", "s", "A_obs", "A_sigma")}
@@ -387,10 +401,37 @@ def run_gpu(a):
 
     # dominant kernel and its roofline
     dom = max(kt.items(), key=lambda kv: kv[1][1])
-    panel = cfg.rhs_panel or (math.ceil(n / 32) * 32)
+    cols = st["probe_colours"] if a.probe > 0 else n
+    panel = cfg.rhs_panel or (math.ceil(cols / 32) * 32)
     roof = roofline_for(dom[0], dom[1][0], dom[1][1], st, a.precision, panel)
     launches = int(sum(v[0] for v in kt.values()))
     total_ms = sum(v[1] for v in kt.values())
+
+    # the same step with exact variances (one solve per star), once: its
+    # time and the probing error on the step's result
+    exact = None
+    if a.probe > 0 and not a.no_exact:
+        cfg_x = gm.config_from_catalogue(cat, precision=prec, probe_factor=0.0,
+                                         cg_tol=cfg.cg_tol)
+        mu_x = torch.empty_like(mu)
+        var_x = torch.empty_like(var)
+        with gm.ep_init(cfg_x, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"]) as cx:
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record()
+            cx.set_sites(zeros, zeros)
+            cx.build_cov()
+            cx.ep_sweep(a.sweeps, 0.0)
+            cx.get_posterior(out=(mu_x, var_x))
+            e1.record()
+            e1.synchronize()
+            tx = e0.elapsed_time(e1) / 1e3
+            sx = cx.stats()
+        exact = {"site_updates_per_s": n * a.sweeps / tx, "ms_per_step": 1e3 * tx,
+                 "steps": 1, "cg_iters_var_last": sx["cg_iters_var"],
+                 "max_abs_err_mean_lnA_probed_vs_exact": float((mu - mu_x).abs().max()),
+                 "max_rel_err_var_probed_vs_exact": float(((var - var_x).abs() / var_x).max())}
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -449,12 +490,17 @@ def run_gpu(a):
                                         "moments and refined mean solve") if a.precision == "fp32"
                           else "FP64 throughout",
                           "cg_tol": cfg.cg_tol, "variance_panel": panel,
+                          "variances": (f"probed (Tang & Saad 2012): colour classes at least "
+                                        f"{a.probe:g} x cutoff apart share one solve, "
+                                        f"{st['probe_colours']} classes for {n} stars; error vs "
+                                        f"exact in exact_variances" if a.probe > 0
+                                        else "exact: one solve per star"),
                           "l2": "inputs (CSR + panels) larger than L2; 256 MiB write between steps",
                           "parallelism": f"replicas x{ws}"},
                "pairs_per_s": pairs_per_s, "cov_ms": 1e3 * t_cov,
                "cg_iters": {"mean": st["cg_iters_mean"], "var_last_panels": st["cg_iters_var"]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": ck, "forms": forms,
+               "clocks": ck, "forms": forms, "exact_variances": exact,
                "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in
                               sorted(kt.items(), key=lambda kv: -kv[1][1])[:8]},
                "kernel_ms_total": total_ms}

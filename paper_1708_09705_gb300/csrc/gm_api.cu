@@ -158,6 +158,12 @@ __global__ void k_scatter_ext(int64_t n, const int64_t* __restrict__ perm,
        k += (int64_t)gridDim.x * blockDim.x)
     dst[perm[k]] = src[k];
 }
+__global__ void k_scatter_i32(int64_t n, const int64_t* __restrict__ perm,
+                              const int32_t* __restrict__ src, int32_t* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[perm[k]] = src[k];
+}
 
 __global__ void k_gather_ext(int64_t n, const int64_t* __restrict__ perm,
                              const double* __restrict__ src, double* __restrict__ dst) {
@@ -221,6 +227,7 @@ static gm_status validate(const gm_config* f) {
   if (f->rhs_panel < 0 || (f->warm_start != 0 && f->warm_start != 1)) return GM_E_INVAL;
   if (f->cov_source != GM_COV_QUADRATURE && f->cov_source != GM_COV_SURROGATE) return GM_E_INVAL;
   if (!(f->surrogate_gate > 0)) return GM_E_INVAL;
+  if (!(f->probe_factor >= 0) || !std::isfinite(f->probe_factor)) return GM_E_INVAL;
   return GM_OK;
 }
 
@@ -420,6 +427,8 @@ gm_status gm_build_cov(gm_ctx* c, int64_t* nnz_out) {
   pack_invalidate(c);
   st = tiles_build(c);
   if (st != GM_OK) return st;
+  st = probe_colouring(c);
+  if (st != GM_OK) return st;
   st = read_flags(c);
   if (st != GM_OK) return st;
   prof_collect(c);
@@ -582,6 +591,22 @@ gm_status gm_get_csr(gm_ctx* c, int64_t* row_ptr_out, int32_t* col_out, double* 
     dev_free_now(c, tmp, std::max<int64_t>(c->nnz, 1) * sizeof(double));
     if (st != GM_OK) return st;
   }
+  return GM_OK;
+}
+
+gm_status gm_get_probe_colours(gm_ctx* c, int32_t* colour_out) {
+  if (!c || !colour_out) return GM_E_INVAL;
+  if (!c->built || !c->probe_colour || c->probe_factor_done <= 0)
+    return set_error(c, GM_E_STATE, "no probing colouring (probe_factor 0 or no gm_build_cov)");
+  c->launches = 0;
+  int32_t* tmp = (int32_t*)dev_alloc(c, c->n * sizeof(int32_t));
+  if (!tmp) return set_error(c, GM_E_NOMEM, "colour staging");
+  GM_PROF(c, "k_scatter_i32");
+  k_scatter_i32<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->probe_colour, tmp);
+  GM_LAUNCH_CHECK(c);
+  gm_status st = copy_out(c, colour_out, tmp, c->n * sizeof(int32_t));
+  if (st != GM_OK) return st;
+  dev_free_now(c, tmp, c->n * sizeof(int32_t));
   return GM_OK;
 }
 

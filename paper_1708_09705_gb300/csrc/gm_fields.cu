@@ -4,8 +4,10 @@
 // whose stars are never neighbours) has a block-diagonal K.  Each field f
 // solves its own N_f right-hand sides against its own N_f rows, so its
 // panels are N_f x W_f (W_f = N_f rounded up to 32) and all fields' panels
-// are packed into one array.  Every CG step runs as one launch over all
-// fields: the tiled panel product over (row block, column-chunk group)
+// are packed into one array (with probed variances a field's columns are
+// its colour classes instead of its stars, W_f = classes rounded up to 32).
+// Every CG step runs as one launch over all fields: the tiled panel product
+// over (row block, column-chunk group)
 // items, element-wise updates over (field, column chunk, row segment)
 // items with per-column partial sums, and a per-column reduction that keeps
 // each column's CG scalars.  The sequence of one iteration is captured as a
@@ -86,6 +88,29 @@ __global__ void k_pk_rhs(int64_t n, const int32_t* __restrict__ field_of,
       const int32_t j = col[e];
       Rr[F.P + (j - F.row0) * F.W + cc] = dv[j] * val[e];
     }
+  }
+}
+
+// Probed right-hand sides: column k of field f sums the right-hand sides of
+// the field's stars of colour class k; thread per row j (fixed summation
+// order), as in the single-panel solver.
+__global__ void k_pk_rhs_probe(int64_t n, const int32_t* __restrict__ field_of,
+                               const PackField* __restrict__ pf, const int64_t* __restrict__ row_ptr,
+                               const int32_t* __restrict__ col, const float* __restrict__ val,
+                               const float* __restrict__ dv, const double* __restrict__ tau,
+                               const double* __restrict__ kd, const int32_t* __restrict__ pcol,
+                               float* __restrict__ Rr) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const PackField F = pf[field_of[j]];
+    float* row = Rr + F.P + (j - F.row0) * F.W;
+    const float dj = dv[j];
+    for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+      const int32_t r = col[e];
+      if (tau[r] * kd[r] >= 1.0) continue;
+      row[pcol[r]] += dj * val[e];
+    }
+    if (tau[j] * kd[j] >= 1.0) row[pcol[j]] += 1.f;
   }
 }
 
@@ -292,16 +317,18 @@ __global__ void k_pk_final(int64_t n, const int32_t* __restrict__ field_of,
                            const int32_t* __restrict__ col, const float* __restrict__ val,
                            const double* __restrict__ d64, const float* __restrict__ X,
                            const double* __restrict__ kd, const double* __restrict__ tau,
-                           double* __restrict__ var_out, unsigned* __restrict__ flags) {
+                           const int32_t* __restrict__ pcol, double* __restrict__ var_out,
+                           unsigned* __restrict__ flags) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < n; r += nw) {
     const PackField F = pf[field_of[r]];
-    const int64_t cc = r - F.row0;
+    // the star's column: its own, or its colour class's when probing
+    const int64_t cc = pcol ? (int64_t)pcol[r] : r - F.row0;
     double v;
     if (tau[r] * kd[r] >= 1.0) {
-      v = (1.0 - (double)X[F.P + cc * F.W + cc]) / tau[r];
+      v = (1.0 - (double)X[F.P + (r - F.row0) * F.W + cc]) / tau[r];
     } else {
       double acc = 0;
       for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
@@ -328,11 +355,13 @@ static gm_status pack_setup(gm_ctx* c) {
   std::vector<int64_t> wptr(nf + 1, 0);
   std::vector<int4> eit;
   int64_t P = 0, Wp = 0, PO = 0;
+  const bool probe = c->probe_colour && c->probe_factor_done > 0;
   for (int f = 0; f < nf; ++f) {
     PackField& F = S.h_pf[f];
     F.row0 = c->h_fptr[f];
     F.nrows = c->h_fptr[f + 1] - F.row0;
-    F.W = ceil_div(std::max<int64_t>(F.nrows, 1), 32) * 32;
+    const int64_t cols = probe ? (int64_t)c->h_probe_ncol[f] : F.nrows;
+    F.W = ceil_div(std::max<int64_t>(cols, 1), 32) * 32;
     F.P = P;
     F.Wptr = Wp;
     F.S = std::max<int64_t>(1, ceil_div(F.nrows, kSeg));
@@ -463,10 +492,18 @@ gm_status panels_fields(gm_ctx* c, const float* dv, const float* minv, const dou
   const int ib = (int)std::min<int64_t>(ceil_div(S.n_eitems * 32, 256), 16 * sms);
   const int rb = (int)std::min<int64_t>(ceil_div(tc, 256), 8 * sms);
   const int nf = c->n_fields;
+  const bool probe = c->probe_colour && c->probe_factor_done > 0;
   GM_CUDA_CHECK(c, cudaMemsetAsync(Rr, 0, (size_t)S.total_elems * sizeof(float), st));
-  GM_PROF(c, "k_pk_rhs");
-  k_pk_rhs<<<wb, 256, 0, st>>>(n, c->field_of, S.pf, c->row_ptr, c->col, (const float*)c->val, dv,
-                               c->tau, c->kdiag, Rr);
+  if (probe) {
+    GM_PROF(c, "k_pk_rhs_probe");
+    k_pk_rhs_probe<<<(int)std::min<int64_t>(ceil_div(n, 256), 16 * sms), 256, 0, st>>>(
+        n, c->field_of, S.pf, c->row_ptr, c->col, (const float*)c->val, dv, c->tau, c->kdiag,
+        c->probe_colour, Rr);
+  } else {
+    GM_PROF(c, "k_pk_rhs");
+    k_pk_rhs<<<wb, 256, 0, st>>>(n, c->field_of, S.pf, c->row_ptr, c->col, (const float*)c->val,
+                                 dv, c->tau, c->kdiag, Rr);
+  }
   GM_LAUNCH_CHECK(c);
   GM_PROF(c, "k_pk_elem_init");
   k_pk_elem<kPkInit><<<ib, 256, 0, st>>>(S.n_eitems, S.eitems, S.pf, minv, dv, scal, tc, active,
@@ -528,7 +565,8 @@ gm_status panels_fields(gm_ctx* c, const float* dv, const float* minv, const dou
   }
   GM_PROF(c, "k_pk_final");
   k_pk_final<<<wb, 256, 0, st>>>(n, c->field_of, S.pf, c->row_ptr, c->col, (const float*)c->val,
-                                 d64, X, c->kdiag, c->tau, var_out, c->d_flags);
+                                 d64, X, c->kdiag, c->tau, probe ? c->probe_colour : nullptr,
+                                 var_out, c->d_flags);
   GM_LAUNCH_CHECK(c);
   std::vector<double> h(2 * tc);
   GM_CUDA_CHECK(c, cudaMemcpyAsync(h.data(), scal + 4 * tc, 2 * tc * sizeof(double),

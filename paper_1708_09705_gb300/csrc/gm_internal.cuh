@@ -20,6 +20,7 @@ enum : unsigned {
   kFlagNonFinite = 1u,
   kFlagNotSPD = 2u,
   kFlagTimeout = 4u,
+  kFlagProbeOverflow = 8u,
 };
 
 // Log-spaced cubic table of g(x), x = r^2 / L0^2.  Segment k >= 0 covers
@@ -139,6 +140,12 @@ struct gm_ctx {
   double* alpha = nullptr;     // mu = m + K alpha
   bool post_valid = false;
   int64_t warm_R = 0;          // panel width of saved variance solutions (0 = none)
+  int warm_probe = 0;          // those solutions are per colour class (1) or per star (0)
+
+  // ---- probed variances: colour class of each internal star, classes per field
+  int32_t* probe_colour = nullptr;
+  std::vector<int32_t> h_probe_ncol;
+  double probe_factor_done = 0;  // probe_factor the colouring was made for
 
   // ---- status flags and pinned readback
   unsigned* d_flags = nullptr;
@@ -255,6 +262,9 @@ gm_status mirror_csr(gm_ctx* c, int64_t n, const int64_t* row_ptr, const int32_t
 gm_status surrogate_values(gm_ctx* c);
 // Diagonal-only quadrature (query self-covariance) into kss (FP64).
 gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* kss);
+
+// Colour classes for probed variances when cfg.probe_factor > 0 (gm_probe.cu).
+gm_status probe_colouring(gm_ctx* c);
 
 // Row-block tiles of K for the FP32 variance panels (gm_tiles.cu).
 gm_status tiles_build(gm_ctx* c);

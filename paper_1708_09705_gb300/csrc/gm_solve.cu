@@ -330,6 +330,33 @@ __global__ void k_panel_rhs(int64_t r0, int64_t n_cols, int R, const int64_t* __
   }
 }
 
+// Probed right-hand sides: column k sums the right-hand sides of the stars of
+// colour class c0 + k (v_r or e_r as above).  One thread per row j, so that
+// every panel entry is summed in a fixed order: (j, colour(r)) receives
+// d_j K_jr for each non-unit neighbour r of j, and (j, colour(j)) receives 1
+// when j itself is a unit star.
+template <typename TA, typename TV>
+__global__ void k_panel_rhs_probe(int64_t n, int64_t c0, int64_t n_cols, int R,
+                                  const int64_t* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ col, const TA* __restrict__ val,
+                                  const TV* __restrict__ dv, const double* __restrict__ tau,
+                                  const double* __restrict__ kd, const int32_t* __restrict__ pcol,
+                                  TV* __restrict__ Rr) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    TV* row = Rr + j * R;
+    const TV dj = dv[j];
+    for (int64_t e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+      const int32_t r = col[e];
+      const int64_t k = (int64_t)pcol[r] - c0;
+      if (k < 0 || k >= n_cols || unit_rhs(tau, kd, r)) continue;
+      row[k] += dj * (TV)val[e];
+    }
+    const int64_t kj = (int64_t)pcol[j] - c0;
+    if (kj >= 0 && kj < n_cols && unit_rhs(tau, kd, j)) row[kj] += (TV)1;
+  }
+}
+
 template <typename TV>
 __global__ void __launch_bounds__(kBT) k_panel_init(int64_t n, int R, const TV* __restrict__ minv,
                                                     const TV* __restrict__ dv,
@@ -620,6 +647,41 @@ __global__ void k_panel_final(int64_t r0, int64_t n_cols, int R, const int64_t* 
   }
 }
 
+// Probed variances: star r reads its estimate from the column of its colour
+// class (when that class is in this panel).
+template <typename TA, typename TV>
+__global__ void k_panel_final_probe(int64_t n, int64_t c0, int64_t n_cols, int R,
+                                    const int64_t* __restrict__ row_ptr,
+                                    const int32_t* __restrict__ col, const TA* __restrict__ val,
+                                    const double* __restrict__ d64, const TV* __restrict__ X,
+                                    const double* __restrict__ kdiag, const double* __restrict__ tau,
+                                    const int32_t* __restrict__ pcol, double* __restrict__ var_out,
+                                    unsigned* __restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nw) {
+    const int64_t k = (int64_t)pcol[r] - c0;
+    if (k < 0 || k >= n_cols) continue;
+    double v;
+    if (unit_rhs(tau, kdiag, r)) {
+      v = (1.0 - (double)X[r * R + k]) / tau[r];
+    } else {
+      double acc = 0;
+      for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
+        const int32_t j = col[e];
+        acc += d64[j] * (double)val[e] * (double)X[(int64_t)j * R + k];
+      }
+      acc = warp_sum(acc);
+      v = kdiag[r] - acc;
+    }
+    if (lane == 0) {
+      if (!isfinite(v)) atomicOr(flags, kFlagNonFinite);
+      var_out[r] = v;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host
 static int vec_grid(gm_ctx* c) { return 2 * sm_count(c); }
 
@@ -800,6 +862,9 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
                         const void* val, const double* kdiag_rows, double* var_out,
                         int64_t* iters_out, double* resid_out, bool stars) {
   const bool warm = stars;
+  // probed variances: one column per colour class instead of one per star
+  const bool probe = stars && c->probe_colour && c->probe_factor_done > 0 && c->n_fields == 1;
+  const int64_t n_cols_all = probe ? (int64_t)c->h_probe_ncol[0] : n_rows;
   Workspace& ws = W(c);
   const int64_t n = c->n;
   cudaStream_t st = c->stream;
@@ -812,7 +877,7 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     double budget = std::min<double>(0.4 * (double)free_b, 48e9);
     R = (int64_t)(budget / (5.0 * (double)n * sizeof(TV)));
   }
-  R = std::max<int64_t>(32, std::min<int64_t>(R, ceil_div(n_rows, 32) * 32));
+  R = std::max<int64_t>(32, std::min<int64_t>(R, ceil_div(n_cols_all, 32) * 32));
   R = (R / 32) * 32;
   const int nbx = std::max(1, (int)std::min<int64_t>(ceil_div(n, 8), (int64_t)(4 * sms * 32 / (R / 32 + 1)) + 1));
   const size_t pbytes = (size_t)n * R * sizeof(TV);
@@ -839,14 +904,23 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   const int rb = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 16 * sms);
   const int redb = (int)ceil_div(R, 256);
   int64_t total_it = 0;
-  for (int64_t r0 = 0; r0 < n_rows; r0 += R) {
-    const int64_t ncols = std::min<int64_t>(R, n_rows - r0);
+  const int tb = (int)std::min<int64_t>(ceil_div(n, 256), 16 * sms);
+  for (int64_t r0 = 0; r0 < n_cols_all; r0 += R) {
+    const int64_t ncols = std::min<int64_t>(R, n_cols_all - r0);
     GM_CUDA_CHECK(c, cudaMemsetAsync(Rr, 0, pbytes, st));
-    GM_PROF(c, "k_panel_rhs");
-    k_panel_rhs<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col, (const TA*)val, dv,
-                                            warm ? c->tau : nullptr, kdiag_rows, Rr);
+    if (probe) {
+      GM_PROF(c, "k_panel_rhs_probe");
+      k_panel_rhs_probe<TA, TV><<<tb, 256, 0, st>>>(n, r0, ncols, (int)R, row_ptr, col,
+                                                    (const TA*)val, dv, c->tau, kdiag_rows,
+                                                    c->probe_colour, Rr);
+    } else {
+      GM_PROF(c, "k_panel_rhs");
+      k_panel_rhs<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col, (const TA*)val, dv,
+                                              warm ? c->tau : nullptr, kdiag_rows, Rr);
+    }
     GM_LAUNCH_CHECK(c);
-    const bool use_warm = warm && c->cfg.warm_start && c->warm_R == R && n_rows <= R;
+    const bool use_warm = warm && c->cfg.warm_start && c->warm_R == R && n_cols_all <= R &&
+                          c->warm_probe == (probe ? 1 : 0);
     if (use_warm) {
       GM_PROF(c, "k_panel_scale");
       k_panel_scale<TV><<<grid, kBT, 0, st>>>(n, (int)R, dv, X, PD);
@@ -897,10 +971,18 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
       }
     }
     total_it += std::min(it, max_it);
-    GM_PROF(c, "k_panel_final");
-    k_panel_final<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col, (const TA*)val,
-                                              (const double*)ws.d64.p, X, kdiag_rows,
-                                              warm ? c->tau : nullptr, var_out, c->d_flags);
+    if (probe) {
+      GM_PROF(c, "k_panel_final_probe");
+      k_panel_final_probe<TA, TV><<<(int)std::min<int64_t>(ceil_div(n * 32, 256), 16 * sms), 256,
+                                    0, st>>>(n, r0, ncols, (int)R, row_ptr, col, (const TA*)val,
+                                             (const double*)ws.d64.p, X, kdiag_rows, c->tau,
+                                             c->probe_colour, var_out, c->d_flags);
+    } else {
+      GM_PROF(c, "k_panel_final");
+      k_panel_final<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col, (const TA*)val,
+                                                (const double*)ws.d64.p, X, kdiag_rows,
+                                                warm ? c->tau : nullptr, var_out, c->d_flags);
+    }
     GM_LAUNCH_CHECK(c);
   }
   // worst relative residual over the last panel's columns
@@ -913,7 +995,8 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     if (h[k] > 0) worst = std::max(worst, std::sqrt(h[R + k] / h[k]));
   *iters_out = total_it;
   *resid_out = worst;
-  c->warm_R = (warm && n_rows <= R) ? R : 0;
+  c->warm_R = (warm && n_cols_all <= R) ? R : 0;
+  c->warm_probe = probe ? 1 : 0;
   return GM_OK;
 }
 

@@ -35,7 +35,7 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_destroy", "gm_profile", "gm_kernel_time_count", "gm_kernel_time",
            "gm_site_update_noalloc", "gm_surrogate_param_count", "gm_surrogate_set_params",
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
-           "gm_surrogate_grad"]
+           "gm_surrogate_grad", "gm_get_probe_colours"]
 
 
 class GmError(RuntimeError):
@@ -51,7 +51,7 @@ class Config(C.Structure):
                 ("cg_max_iter", C.c_int32), ("damping", C.c_double), ("vc_floor", C.c_double),
                 ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("warm_start", C.c_int32),
                 ("cov_source", C.c_int32), ("reserved", C.c_int32),
-                ("surrogate_gate", C.c_double)]
+                ("surrogate_gate", C.c_double), ("probe_factor", C.c_double)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -69,7 +69,7 @@ class Stats(C.Structure):
                 ("last_max_delta", C.c_double), ("cg_resid_mean", C.c_double),
                 ("cg_resid_var", C.c_double), ("surrogate_fallback", C.c_int64),
                 ("surrogate_loss", C.c_double), ("surrogate_val_rmse", C.c_double),
-                ("surrogate_gate_frac", C.c_double)]
+                ("surrogate_gate_frac", C.c_double), ("probe_colours", C.c_int64)]
 
 
 _lib = None
@@ -96,6 +96,7 @@ def lib():
         for f in ("gm_get_posterior", "gm_get_sites", "gm_set_sites", "gm_get_prior"):
             getattr(L, f).argtypes = [vp, vp, vp]
         L.gm_get_perm.argtypes = [vp, vp]
+        L.gm_get_probe_colours.argtypes = [vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.gm_stream.argtypes = [vp]
@@ -125,7 +126,7 @@ def lib():
                   "gm_get_sites", "gm_set_sites", "gm_get_prior", "gm_get_perm", "gm_get_csr",
                   "gm_get_stats", "gm_profile", "gm_kernel_time", "gm_surrogate_set_params",
                   "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
-                  "gm_surrogate_grad"):
+                  "gm_surrogate_grad", "gm_get_probe_colours"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -234,6 +235,12 @@ class Context:
     def get_perm(self):
         out = np.empty(self.n, dtype=np.int64)
         self._check(lib().gm_get_perm(self._h, out.ctypes.data))
+        return out
+
+    def get_probe_colours(self):
+        """Colour class of each star (caller order) when probing is on."""
+        out = np.empty(self.n, dtype=np.int32)
+        self._check(lib().gm_get_probe_colours(self._h, out.ctypes.data))
         return out
 
     def get_csr(self):

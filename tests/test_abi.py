@@ -40,8 +40,9 @@ def test_status_strings_and_defaults(L):
     assert cfg.sigma2 == 1.0 and cfg.outer_scale_pc == 20.0 and cfg.cutoff_pc == 60.0
     assert cfg.precision == gm.PREC_FP64 and cfg.taper == gm.TAPER_WENDLAND
     assert cfg.warm_start == 1 and cfg.rhs_panel == 0
-    assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2 + 4 * 2 + 8
+    assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2 + 4 * 2 + 8 + 8
     assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-4
+    assert cfg.probe_factor == 0.0        # exact variances unless asked
 
 
 def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
@@ -54,7 +55,8 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
     # null array
     assert L.gm_ep_init(C.byref(h), C.byref(cfg), 4, x, None, x, x, x, None, None) == 1
     for field, bad in (("sigma2", -1.0), ("n_nodes", 1), ("damping", 0.0), ("cg_tol", 0.0),
-                       ("precision", 7), ("outer_scale_pc", float("nan")), ("warm_start", 2)):
+                       ("precision", 7), ("outer_scale_pc", float("nan")), ("warm_start", 2),
+                       ("probe_factor", -1.0), ("probe_factor", float("inf"))):
         c2 = gm.default_config(**{field: bad})
         assert L.gm_ep_init(C.byref(h), C.byref(c2), 4, x, x, x, x, x, None, None) == 1, field
     assert not h.value

@@ -1,0 +1,142 @@
+"""Probed posterior variances (colour classes sharing one solve) on the GPU:
+the colouring checked for validity and the greedy property, the probed EP
+against the oracle's exact EP, and probed against exact variances at the
+full size of the 20,000-star workload and on batched fields."""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import oracle as O
+from synth import catalogue_subset, make_catalogue, make_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_09705_gb300 import _build
+    _build.build()
+    import paper_1708_09705_gb300 as pkg
+    return pkg
+
+
+def positions(cat):
+    u = O.unit_vectors(cat["l"], cat["b"])
+    return u * np.asarray(cat["s"])[:, None]
+
+
+def check_colouring(col, x, D):
+    """Valid (no two stars closer than D share a class), classes numbered
+    0..k-1, and greedy: a star of class k has, for every smaller class,
+    a neighbour closer than D holding it."""
+    k = col.max() + 1
+    assert col.min() == 0 and np.array_equal(np.unique(col), np.arange(k))
+    nb = cKDTree(x).query_ball_point(x, np.nextafter(D, 0.0))
+    for i, lst in enumerate(nb):
+        others = [j for j in lst if j != i]
+        assert col[i] not in set(col[others]), i
+        if col[i] > 0:
+            assert set(range(col[i])) <= set(col[others]), i
+    return k
+
+
+def test_colouring_valid_and_greedy(gm):
+    cat = catalogue_subset(make_catalogue("c2_plain_20k", truth="mean"), np.arange(3000))
+    cfg = gm.config_from_catalogue(cat, precision=gm.PREC_FP32, probe_factor=2.0)
+    with gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"]) as ctx:
+        ctx.build_cov()
+        col = ctx.get_probe_colours()
+        st = ctx.stats()
+        # a second build keeps the colouring (deterministic)
+        ctx.build_cov()
+        assert np.array_equal(ctx.get_probe_colours(), col)
+    k = check_colouring(col, positions(cat), 2.0 * cat["cutoff_pc"])
+    assert st["probe_colours"] == k and k < len(col)
+
+
+def test_no_colouring_without_probing(gm):
+    cat = make_catalogue("c1_plain_400")
+    with gm.ep_init(gm.config_from_catalogue(cat), cat["l"], cat["b"], cat["s"], cat["A_obs"],
+                    cat["A_sigma"]) as ctx:
+        ctx.build_cov()
+        with pytest.raises(gm.GmError):
+            ctx.get_probe_colours()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_probed_ep_matches_oracle_exact_ep(gm, prec):
+    """On the narrow 400-star field the probing error at 3 x cutoff is
+    ~5e-6 (oracle pin); the EP result stays within 1e-4 of the exact EP."""
+    cat = make_catalogue("c1_plain_400")
+    cv = O.build_cov(cat)
+    ref = O.ep_run(cv["K"], cv["m"], cat["A_obs"], cat["A_sigma"], max_sweeps=4, tol=0.0)
+    p = gm.PREC_FP64 if prec == "fp64" else gm.PREC_FP32
+    cfg = gm.config_from_catalogue(cat, precision=p, probe_factor=3.0, cg_tol=1e-10)
+    with gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"]) as ctx:
+        ctx.build_cov()
+        ctx.ep_sweep(4)
+        mu, var = ctx.get_posterior()
+        st = ctx.stats()
+    assert 0 < st["probe_colours"] < 400
+    e_mu = np.abs(mu - ref["mu"]).max()
+    e_var = np.max(np.abs(var - ref["var"]) / ref["var"])
+    print("probed EP (%s, %d classes) vs exact oracle: mean %.2e, var rel %.2e"
+          % (prec, st["probe_colours"], e_mu, e_var))
+    assert e_mu < 1e-4 and e_var < 1e-4
+
+
+def test_probed_variances_full_size_fp32(gm):
+    """20,000-star workload at the bench's settings: probed (2 x cutoff)
+    against exact variances for the same sites."""
+    cat = make_catalogue("c2_plain_20k")
+    base = dict(precision=gm.PREC_FP32, cg_tol=1e-6)
+    with gm.ep_init(gm.config_from_catalogue(cat, **base), cat["l"], cat["b"], cat["s"],
+                    cat["A_obs"], cat["A_sigma"]) as ctx:
+        ctx.build_cov()
+        ctx.ep_sweep(1)
+        tau, nu = ctx.get_sites()
+        mu_x, var_x = ctx.get_posterior()
+    with gm.ep_init(gm.config_from_catalogue(cat, probe_factor=2.0, **base), cat["l"], cat["b"],
+                    cat["s"], cat["A_obs"], cat["A_sigma"]) as ctx:
+        ctx.build_cov()
+        ctx.set_sites(tau, nu)
+        mu_p, var_p = ctx.get_posterior()
+        st = ctx.stats()
+    rel = np.abs(var_p - var_x) / var_x
+    print("probed vs exact at 20k: %d classes, var rel max %.2e median %.2e, mean %.2e"
+          % (st["probe_colours"], rel.max(), np.median(rel), np.abs(mu_p - mu_x).max()))
+    assert st["probe_colours"] < 20000 / 3
+    assert rel.max() < 2e-4
+    assert np.abs(mu_p - mu_x).max() < 1e-5
+
+
+def test_probed_fields_match_exact_fields(gm):
+    fields = make_fields(n_fields=6, scale=0.08, seed=3)
+    keys = ("l", "b", "s", "A_obs", "A_sigma")
+    cat = {k: np.concatenate([f[k] for f in fields]) for k in keys}
+    fid = np.concatenate([np.full(len(f["s"]), i, dtype=np.int32) for i, f in enumerate(fields)])
+    L0 = np.array([f["outer_scale_pc"] for f in fields])
+    out = {}
+    for pf in (0.0, 3.0):
+        cfg = gm.default_config(sigma2=1.0, outer_scale_pc=20.0, rho_bar=1e-3, cutoff_pc=60.0,
+                                n_nodes=32, precision=gm.PREC_FP32, cg_tol=1e-7, probe_factor=pf)
+        with gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"],
+                        field_id=fid, field_L0=L0, field_cutoff=3 * L0) as ctx:
+            ctx.build_cov()
+            ctx.ep_sweep(3)
+            out[pf] = ctx.get_posterior() + (ctx.stats(),)
+            if pf > 0:
+                col = ctx.get_probe_colours()
+    (mu0, var0, _), (mu1, var1, st1) = out[0.0], out[3.0]
+    # classes are numbered per field and valid within each field
+    x = positions(cat)
+    tot = 0
+    for f in range(len(fields)):
+        sel = fid == f
+        tot += check_colouring(col[sel], x[sel], 3.0 * 3 * L0[f])
+    assert st1["probe_colours"] == tot < len(fid)
+    assert np.abs(mu1 - mu0).max() < 1e-4
+    assert np.max(np.abs(var1 - var0) / var0) < 1e-4
