@@ -221,6 +221,13 @@ gm_status gm_get_perm(gm_ctx* ctx, int64_t* perm_out);
 gm_status gm_get_csr(gm_ctx* ctx, int64_t* row_ptr_out, int32_t* col_out,
                      double* val_out);
 
+/* Stored covariance entries K_ij (tapered, as used by the solves) for nq
+ * caller index pairs (i[q], j[q]); 0 where the pair is beyond the cutoff.
+ * i, j: int64, host or device; out: nq doubles, host or device.
+ * GM_E_INVAL for an index outside [0, n); GM_E_STATE before gm_build_cov. */
+gm_status gm_get_entries(gm_ctx* ctx, int64_t nq, const int64_t* i, const int64_t* j,
+                         double* out);
+
 /* Colour class of each star (caller order, int32, length n) when probing is
  * on (probe_factor > 0, after gm_build_cov); classes are numbered from 0 per
  * field.  GM_E_STATE if no colouring exists. */

@@ -158,6 +158,46 @@ __global__ void k_scatter_ext(int64_t n, const int64_t* __restrict__ perm,
        k += (int64_t)gridDim.x * blockDim.x)
     dst[perm[k]] = src[k];
 }
+__global__ void k_invert_perm(int64_t n, const int64_t* __restrict__ perm,
+                              int64_t* __restrict__ iperm) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    iperm[perm[k]] = k;
+}
+
+// Stored K_ij for caller index pairs: binary search of the internal column
+// of j in the internal row of i (columns are sorted); 0 when not stored.
+template <typename TA>
+__global__ void k_entries(int64_t nq, int64_t n, const int64_t* __restrict__ qi,
+                          const int64_t* __restrict__ qj, const int64_t* __restrict__ iperm,
+                          const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                          const TA* __restrict__ val, double* __restrict__ out,
+                          unsigned* __restrict__ flags) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = qi[q], b = qj[q];
+    if (a < 0 || a >= n || b < 0 || b >= n) {
+      out[q] = NAN;
+      atomicOr(flags, kFlagBadIndex);
+      continue;
+    }
+    const int64_t r = iperm[a];
+    const int32_t cj = (int32_t)iperm[b];
+    int64_t lo = row_ptr[r], hi = row_ptr[r + 1];
+    double v = 0.0;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      const int32_t cm = col[mid];
+      if (cm == cj) {
+        v = (double)val[mid];
+        break;
+      }
+      if (cm < cj) lo = mid + 1; else hi = mid;
+    }
+    out[q] = v;
+  }
+}
+
 __global__ void k_scatter_i32(int64_t n, const int64_t* __restrict__ perm,
                               const int32_t* __restrict__ src, int32_t* __restrict__ dst) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -423,9 +463,10 @@ gm_status gm_build_cov(gm_ctx* c, int64_t* nnz_out) {
   }
   if (st != GM_OK) return st;
   c->t_nblk = 0;
+  c->tc_nblk = 0;
   c->warm_R = 0;
   pack_invalidate(c);
-  st = tiles_build(c);
+  st = tc_wanted(c) ? tc_tiles_build(c) : tiles_build(c);
   if (st != GM_OK) return st;
   st = probe_colouring(c);
   if (st != GM_OK) return st;
@@ -590,6 +631,51 @@ gm_status gm_get_csr(gm_ctx* c, int64_t* row_ptr_out, int32_t* col_out, double* 
     st = copy_out(c, val_out, tmp, c->nnz * sizeof(double));
     dev_free_now(c, tmp, std::max<int64_t>(c->nnz, 1) * sizeof(double));
     if (st != GM_OK) return st;
+  }
+  return GM_OK;
+}
+
+gm_status gm_get_entries(gm_ctx* c, int64_t nq, const int64_t* i, const int64_t* j,
+                         double* out) {
+  if (!c || nq < 0 || (nq > 0 && (!i || !j || !out))) return GM_E_INVAL;
+  if (!c->built) return set_error(c, GM_E_STATE, "gm_build_cov must come first");
+  if (nq == 0) return GM_OK;
+  c->launches = 0;
+  if (!c->iperm) {
+    c->iperm = (int64_t*)dev_alloc(c, c->n * sizeof(int64_t));
+    if (!c->iperm) return set_error(c, GM_E_NOMEM, "inverse permutation");
+    GM_PROF(c, "k_invert_perm");
+    k_invert_perm<<<eb(c, c->n), 256, 0, c->stream>>>(c->n, c->perm, c->iperm);
+    GM_LAUNCH_CHECK(c);
+  }
+  const size_t ib = nq * sizeof(int64_t);
+  unsigned char* tmp = (unsigned char*)dev_alloc(c, 2 * ib + nq * sizeof(double));
+  if (!tmp) return set_error(c, GM_E_NOMEM, "entry staging");
+  int64_t* di = (int64_t*)tmp;
+  int64_t* dj = (int64_t*)(tmp + ib);
+  double* dout = (double*)(tmp + 2 * ib);
+  gm_status st;
+  if ((st = copy_in(c, (double*)di, i, ib)) != GM_OK || (st = copy_in(c, (double*)dj, j, ib)) != GM_OK)
+    return st;
+  GM_PROF(c, "k_entries");
+  if (c->cfg.precision == GM_PREC_FP32)
+    k_entries<float><<<eb(c, nq), 256, 0, c->stream>>>(nq, c->n, di, dj, c->iperm, c->row_ptr,
+                                                       c->col, (const float*)c->val, dout,
+                                                       c->d_flags);
+  else
+    k_entries<double><<<eb(c, nq), 256, 0, c->stream>>>(nq, c->n, di, dj, c->iperm, c->row_ptr,
+                                                        c->col, (const double*)c->val, dout,
+                                                        c->d_flags);
+  GM_LAUNCH_CHECK(c);
+  if ((st = copy_out(c, out, dout, nq * sizeof(double))) != GM_OK) return st;
+  unsigned* h = (unsigned*)c->h_pinned;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                   c->stream));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  dev_free_now(c, tmp, 2 * ib + nq * sizeof(double));
+  if (*h & kFlagBadIndex) {
+    GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream));
+    return set_error(c, GM_E_INVAL, "star index out of range");
   }
   return GM_OK;
 }

@@ -21,6 +21,7 @@ enum : unsigned {
   kFlagNotSPD = 2u,
   kFlagTimeout = 4u,
   kFlagProbeOverflow = 8u,
+  kFlagBadIndex = 16u,
 };
 
 // Log-spaced cubic table of g(x), x = r^2 / L0^2.  Segment k >= 0 covers
@@ -81,6 +82,7 @@ struct gm_ctx {
 
   // ---- stars, internal (spatially sorted) order
   int64_t* perm = nullptr;     // internal -> caller index
+  int64_t* iperm = nullptr;    // caller -> internal index (made on first use)
   double* s = nullptr;         // distance
   double* ux = nullptr;        // unit vector components
   double* uy = nullptr;
@@ -114,6 +116,10 @@ struct gm_ctx {
   int64_t* boff = nullptr;         // device copy
   int64_t* blk_row0 = nullptr;     // device, t_nblk + 1
   int64_t t_union = 0;
+  // 128-row tiles of K for the tensor-core panel product (single-field FP32):
+  // K-step prefix per block, padded union columns, BF16 operand images
+  int64_t tc_nblk = 0, tc_nks = 0;
+  gm::Buffer tc_kbase, tc_upad, tc_img;
   double* kdiag = nullptr;
   double* prior_m = nullptr;
 
@@ -265,6 +271,12 @@ gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* k
 
 // Colour classes for probed variances when cfg.probe_factor > 0 (gm_probe.cu).
 gm_status probe_colouring(gm_ctx* c);
+
+// 128-row tiles and the tensor-core panel product (gm_tc.cu).
+bool tc_wanted(gm_ctx* c);
+gm_status tc_tiles_build(gm_ctx* c);
+gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const float* P,
+                        const float* PD, float* Q, double* part_pq);
 
 // Row-block tiles of K for the FP32 variance panels (gm_tiles.cu).
 gm_status tiles_build(gm_ctx* c);

@@ -841,9 +841,16 @@ static gm_status posterior_mean(gm_ctx* c, int64_t* iters, double* resid) {
 }
 
 // Panel product Q = P + d o (K PD) with the tiled kernel when available.
+// *nbx_used: rows of per-column partials written to pa (the reduction's nbx).
 template <typename TA, typename TV>
 static gm_status panel_product(gm_ctx* c, int64_t n, int64_t R, int nbx, dim3 grid, const TV* dv,
-                               const TV* P, const TV* PD, TV* Q, double* pa) {
+                               const TV* P, const TV* PD, TV* Q, double* pa, int* nbx_used) {
+  *nbx_used = nbx;
+  if (sizeof(TV) == 4 && c->tc_nblk > 0) {
+    *nbx_used = (int)c->tc_nblk;
+    return panel_spmm_tc(c, n, (int)R, (const float*)dv, (const float*)P, (const float*)PD,
+                         (float*)Q, pa);
+  }
   if (sizeof(TV) == 4 && c->t_nblk > 0)
     return panel_spmm_tiled(c, n, (int)R, nbx, (const float*)dv, (const float*)P,
                             (const float*)PD, (float*)Q, pa);
@@ -881,16 +888,18 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   R = (R / 32) * 32;
   const int nbx = std::max(1, (int)std::min<int64_t>(ceil_div(n, 8), (int64_t)(4 * sms * 32 / (R / 32 + 1)) + 1));
   const size_t pbytes = (size_t)n * R * sizeof(TV);
+  // partial rows: the panel product may write more rows (one per 128-row tile)
+  const int64_t npa = std::max<int64_t>(nbx, sizeof(TV) == 4 ? c->tc_nblk : 0);
   bool ok = ensure(c, ws.P_X, pbytes) && ensure(c, ws.P_R, pbytes) && ensure(c, ws.P_P, pbytes) &&
             ensure(c, ws.P_PD, pbytes) && ensure(c, ws.P_Q, pbytes) &&
-            ensure(c, ws.P_part, 2 * (size_t)nbx * R * sizeof(double)) &&
+            ensure(c, ws.P_part, (size_t)(npa + nbx) * R * sizeof(double)) &&
             ensure(c, ws.P_scal, 6 * (size_t)R * sizeof(double)) &&
             ensure(c, ws.P_active, (size_t)(R + 32) * sizeof(int));
   if (!ok) return set_error(c, GM_E_NOMEM, "variance panels");
   TV *X = (TV*)ws.P_X.p, *Rr = (TV*)ws.P_R.p, *P = (TV*)ws.P_P.p, *PD = (TV*)ws.P_PD.p,
      *Q = (TV*)ws.P_Q.p;
   double* pa = (double*)ws.P_part.p;
-  double* pb = pa + (size_t)nbx * R;
+  double* pb = pa + (size_t)npa * R;
   double* scal = (double*)ws.P_scal.p;
   int* active = (int*)ws.P_active.p;
   int* n_active = active + R;
@@ -925,7 +934,8 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
       GM_PROF(c, "k_panel_scale");
       k_panel_scale<TV><<<grid, kBT, 0, st>>>(n, (int)R, dv, X, PD);
       GM_LAUNCH_CHECK(c);
-      gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, X, PD, Q, pa);
+      int nbu = nbx;
+      gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, X, PD, Q, pa, &nbu);
       if (ss != GM_OK) return ss;
       GM_PROF(c, "k_panel_init_warm");
       k_panel_init_warm<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, Rr, Q, P, PD, pa, pb);
@@ -945,12 +955,13 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
     int it = *hn == 0 ? 0 : 1;  // no active column (all right-hand sides zero): no iteration
     for (; it >= 1 && it <= max_it; ++it) {
+      int nbu = nbx;
       {
-        gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, P, PD, Q, pa);
+        gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, P, PD, Q, pa, &nbu);
         if (ss != GM_OK) return ss;
       }
       GM_PROF(c, "k_panel_reduce");
-      k_panel_reduce<<<redb, 256, 0, st>>>(1, nbx, (int)R, ncols, tol2, it, max_it, pa, nullptr,
+      k_panel_reduce<<<redb, 256, 0, st>>>(1, nbu, (int)R, ncols, tol2, it, max_it, pa, nullptr,
                                            scal, active, n_active, c->d_flags);
       GM_LAUNCH_CHECK(c);
       GM_PROF(c, "k_panel_update1");

@@ -1,0 +1,457 @@
+// Tensor-core panel product of the variance solves: Q = P + d o (K PD) over
+// a panel of R right-hand sides, with K in 128-row tiles and the products on
+// the 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulators
+// in tensor memory).
+//
+// Precision: every FP32 operand x is split into three BF16 pieces,
+// x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2), which hold its 24
+// significand bits; of the nine piece products the six whose size is at
+// least 2^-16 of the leading one (x1y1, x1y2, x2y1, x1y3, x2y2, x3y1) are
+// accumulated, so each product carries an error below about 2^-22 of |xy|,
+// that of an FP32 product.
+//
+// Tile format.  Rows are cut into blocks of 128 (the stars are spatially
+// sorted, so a block's rows share most neighbours: 62 % of the dense slots
+// are stored entries on the 20,000-star workload).  A block's union of
+// column indices is padded to a multiple of 16 by repeating its last column
+// (with zero values) and cut into K-steps of 16 union columns.  Per K-step
+// the tile keeps three 4 KB operand images (one per BF16 piece) of the
+// 128 x 16 block of K values in the no-swizzle K-major layout of 8-row x
+// 16-byte core matrices.
+//
+// CTA = (row block, 256 panel columns), 256 threads.  Per K-step every thread
+// gathers its panel column's 16 values PD[u_k, c] (registers, one step ahead),
+// splits them and writes the three 256 x 16 B operands; one thread issues the
+// six tcgen05.mma (M = 128 rows, N = 256 columns, K = 16) into the 128 x 256
+// FP32 accumulator and commits to the step buffer's mbarrier.  Two step
+// buffers: the gathers of step k+1 run while the tensor cores work on step k.
+// Epilogue: tcgen05.ld of the accumulator, Q = P + d o acc, and per-column
+// partial sums of P^T Q for the CG step length (fixed order).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
+#include "gm_internal.cuh"
+
+namespace gm {
+
+constexpr int kTcRows = 128;                 // M
+constexpr int kTcCols = 256;                 // N
+constexpr int kTcK = 16;                     // K per MMA
+constexpr int kTcA = kTcRows * kTcK * 2;     // 4 KB per piece
+constexpr int kTcB = kTcCols * kTcK * 2;     // 8 KB per piece
+constexpr int kTcStage = 3 * kTcA + 3 * kTcB;  // 36 KB
+constexpr int kTcSmem = 2 * kTcStage + 4 * kTcCols * 8;  // + P^T Q partials (8 KB)
+
+// byte offset of (row, k) in a no-swizzle K-major image with 16 columns:
+// core matrices of 8 rows x 16 B, k-adjacent 128 B apart, row groups 256 B apart
+__host__ __device__ __forceinline__ int tc_off(int row, int k) {
+  return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint32_t tc_smem(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;  // LBO: k-adjacent core matrices
+  d |= (uint64_t)((256u >> 4) & 0x3FFF) << 32;  // SBO: 8-row groups
+  d |= (uint64_t)1 << 46;                       // descriptor version
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 A and B (K-major), FP32 D.
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                              ((uint32_t)(kTcCols >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
+}
+
+// Bounded wait on an mbarrier phase; false if it gave up.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+    if (done) return true;
+  }
+  return false;
+}
+
+// three BF16 pieces of x (x1 + x2 + x3 == x to 24 bits)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b,
+                                       __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(b);
+  c = __float2bfloat16_rn(r2);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// ---------------------------------------------------------------- tiles
+__global__ void k_tc_keys(int64_t n, const int64_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ col, int64_t nnz, int64_t n_pad,
+                          unsigned long long* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    const unsigned long long hi = (unsigned long long)(i / kTcRows) << 32;
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32)
+      keys[e] = hi | (unsigned long long)(unsigned)col[e];
+  }
+  for (int64_t e = nnz + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_pad;
+       e += (int64_t)gridDim.x * blockDim.x)
+    keys[e] = ~0ull;
+}
+
+__global__ void k_tc_flags(int64_t nnz, const unsigned long long* __restrict__ keys,
+                           int64_t* __restrict__ flag) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    flag[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
+}
+
+__global__ void k_tc_unique(int64_t nnz, const unsigned long long* __restrict__ keys,
+                            const int64_t* __restrict__ flag, const int64_t* __restrict__ pos,
+                            int32_t* __restrict__ ucol, int32_t* __restrict__ ublk) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (flag[e]) {
+      const int64_t p = pos[e];
+      ucol[p] = (int32_t)(keys[e] & 0xffffffffull);
+      ublk[p] = (int32_t)(keys[e] >> 32);
+    }
+  }
+}
+
+// bptr[b] = first union position of block b
+__global__ void k_tc_bptr(int64_t U, int64_t nblk, const int32_t* __restrict__ ublk,
+                          int64_t* __restrict__ bptr) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= U;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t prev = p == 0 ? -1 : ublk[p - 1];
+    const int64_t cur = p == U ? nblk : ublk[p];
+    for (int64_t b = prev + 1; b <= cur; ++b) bptr[b] = p;
+  }
+}
+
+// Padded union columns: slot (block b, local position q) holds the block's
+// q-th union column, or its last one past the end.
+__global__ void k_tc_ucol(int64_t nblk, const int64_t* __restrict__ bptr,
+                          const int64_t* __restrict__ kbase, const int32_t* __restrict__ ucol,
+                          int32_t* __restrict__ upad) {
+  for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const int64_t u0 = bptr[b], u1 = bptr[b + 1];
+    const int64_t slots = (kbase[b + 1] - kbase[b]) * kTcK;
+    for (int64_t q = threadIdx.x; q < slots; q += blockDim.x)
+      upad[kbase[b] * kTcK + q] = ucol[u0 + q < u1 ? u0 + q : u1 - 1];
+  }
+}
+
+// Operand images: entry (i, j) of block b = i / 128 at union position q of j
+// goes to K-step kbase[b] + q / 16, column q % 16, row i % 128, three pieces.
+__global__ void k_tc_fill(int64_t n, const int64_t* __restrict__ row_ptr,
+                          const int32_t* __restrict__ col, const float* __restrict__ val,
+                          const int64_t* __restrict__ bptr, const int64_t* __restrict__ kbase,
+                          const int32_t* __restrict__ ucol, unsigned char* __restrict__ img) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    const int64_t b = i / kTcRows;
+    const int t = (int)(i - b * kTcRows);
+    const int64_t u0 = bptr[b], u1 = bptr[b + 1];
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+      const int32_t j = col[e];
+      int64_t lo = u0, hi = u1;  // ucol[lo] <= j < ucol[hi]
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ucol[mid] <= j) lo = mid; else hi = mid;
+      }
+      const int64_t q = lo - u0;
+      unsigned char* step = img + (kbase[b] + q / kTcK) * (int64_t)(3 * kTcA);
+      __nv_bfloat16 p1, p2, p3;
+      split3(val[e], p1, p2, p3);
+      const int off = tc_off(t, (int)(q % kTcK));
+      *reinterpret_cast<__nv_bfloat16*>(step + off) = p1;
+      *reinterpret_cast<__nv_bfloat16*>(step + kTcA + off) = p2;
+      *reinterpret_cast<__nv_bfloat16*>(step + 2 * kTcA + off) = p3;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- product
+__global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
+    int64_t n, int R, const int64_t* __restrict__ kbase, const int32_t* __restrict__ upad,
+    const uint4* __restrict__ img, const float* __restrict__ dv, const float* __restrict__ P,
+    const float* __restrict__ PD, float* __restrict__ Q, double* __restrict__ part_pq,
+    unsigned* __restrict__ flags) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  double* sh_pq = reinterpret_cast<double*>(smem + 2 * kTcStage);  // [4][256]
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int64_t b = blockIdx.x;
+  const int c0 = blockIdx.y * kTcCols;
+  const int col = c0 + t;
+  const bool live = col < R;
+  const int64_t ks0 = kbase[b], nks = kbase[b + 1] - ks0;
+
+  if (t == 0) {
+    abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        tc_smem(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  // registers of one step: three 16-byte pieces of the tile image and the
+  // column's 16 gathered panel values
+  uint4 ra[3];
+  float rb[16];
+  auto load_step = [&](int64_t ks) {
+    const uint4* src = img + (ks0 + ks) * (3 * kTcA / 16);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) ra[q] = __ldg(src + t + 256 * q);
+    const int4* u4 = reinterpret_cast<const int4*>(upad + (ks0 + ks) * kTcK);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int4 u = __ldg(u4 + q);
+      const int idx[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        rb[4 * q + r] = live ? __ldg(PD + (int64_t)idx[r] * R + col) : 0.f;
+    }
+  };
+
+  if (nks > 0) load_step(0);
+  for (int64_t ks = 0; ks < nks; ++ks) {
+    const int s = (int)(ks & 1);
+    unsigned char* sA = smem + s * kTcStage;
+    unsigned char* sB = sA + 3 * kTcA;
+    // the buffer was last read by the MMAs of step ks - 2
+    if (ks >= 2 && !tc_wait(tc_smem(&mbar[s]), (uint32_t)(((ks - 2) >> 1) & 1))) abort_flag = 1;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) reinterpret_cast<uint4*>(sA)[t + 256 * q] = ra[q];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+        split3(rb[8 * h + 2 * q], a0, a1, a2);
+        split3(rb[8 * h + 2 * q + 1], b0, b1, b2);
+        w1[q] = pack2(a0, b0);
+        w2[q] = pack2(a1, b1);
+        w3[q] = pack2(a2, b2);
+      }
+      const int off = tc_off(t, 8 * h);
+      *reinterpret_cast<uint4*>(sB + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+      *reinterpret_cast<uint4*>(sB + kTcB + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+      *reinterpret_cast<uint4*>(sB + 2 * kTcB + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+    }
+    if (ks + 1 < nks) load_step(ks + 1);
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (abort_flag) break;
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a = tc_smem(sA), bb = tc_smem(sB);
+      const uint64_t A1 = tc_desc(a), A2 = tc_desc(a + kTcA), A3 = tc_desc(a + 2 * kTcA);
+      const uint64_t B1 = tc_desc(bb), B2 = tc_desc(bb + kTcB), B3 = tc_desc(bb + 2 * kTcB);
+      // small terms first
+      tc_mma(tmem, A3, B1, ks > 0 ? 1u : 0u);
+      tc_mma(tmem, A2, B2, 1u);
+      tc_mma(tmem, A1, B3, 1u);
+      tc_mma(tmem, A2, B1, 1u);
+      tc_mma(tmem, A1, B2, 1u);
+      tc_mma(tmem, A1, B1, 1u);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              tc_smem(&mbar[s])));
+    }
+  }
+  // all MMAs done: the last commit tracks every earlier one
+  if (!abort_flag && nks > 0) {
+    const int64_t last = nks - 1;
+    if (!tc_wait(tc_smem(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  __syncthreads();
+  if (!abort_flag) {
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = 32 * quad + lane;
+    const int64_t row = b * kTcRows + r;
+    const bool vrow = row < n;
+    const float dr = vrow ? dv[row] : 0.f;
+#pragma unroll 1
+    for (int ch = 0; ch < 8; ++ch) {
+      const int cl = 128 * half + 16 * ch;
+      uint32_t u[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+            "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]),
+            "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+          : "r"(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cl));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int cg = c0 + cl + k;
+        double pq = 0.0;
+        if (vrow && cg < R) {
+          const int64_t at = row * R + cg;
+          const float p = P[at];
+          const float q = p + dr * __uint_as_float(u[k]);
+          Q[at] = q;
+          pq = (double)p * (double)q;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
+        if (lane == 0) sh_pq[quad * kTcCols + cl + k] = pq;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (!abort_flag) {
+    if (live)
+      part_pq[b * R + col] = ((sh_pq[t] + sh_pq[kTcCols + t]) + sh_pq[2 * kTcCols + t]) +
+                             sh_pq[3 * kTcCols + t];
+  } else if (t == 0) {
+    atomicOr(flags, kFlagTimeout);
+    // give MMAs still in flight a bounded chance to finish before the
+    // accumulator columns are released
+    for (int s = 0; s < 2; ++s) {
+      const int64_t uses = nks > s ? (nks - 1 - s) / 2 + 1 : 0;
+      if (uses > 0) tc_wait(tc_smem(&mbar[s]), (uint32_t)((uses - 1) & 1));
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  }
+}
+
+// ---------------------------------------------------------------- host
+// The tensor-core path serves single-field FP32 contexts unless GM_SPMM=simt.
+bool tc_wanted(gm_ctx* c) {
+  if (c->cfg.precision != GM_PREC_FP32 || c->n_fields != 1) return false;
+  const char* e = std::getenv("GM_SPMM");
+  return !(e && e[0] == 's');
+}
+
+gm_status tc_tiles_build(gm_ctx* c) {
+  c->tc_nblk = 0;
+  const int64_t n = c->n, nnz = c->nnz;
+  cudaStream_t st = c->stream;
+  const int sms = sm_count(c);
+  const int64_t nblk = ceil_div(n, kTcRows);
+  int64_t n_pad = 1024;
+  while (n_pad < nnz) n_pad <<= 1;
+  unsigned long long* keys = (unsigned long long*)dev_alloc(c, n_pad * sizeof(unsigned long long));
+  int64_t* flag = (int64_t*)dev_alloc(c, std::max<int64_t>(nnz, 1) * sizeof(int64_t));
+  int64_t* pos = (int64_t*)dev_alloc(c, (nnz + 1) * sizeof(int64_t));
+  if (!keys || !flag || !pos) return set_error(c, GM_E_NOMEM, "tensor-core tile keys");
+  const int wb = (int)std::min<int64_t>(ceil_div(n * 32, 256), 32 * sms);
+  const int eb = (int)std::min<int64_t>(ceil_div(nnz, 256), 16 * sms);
+  GM_PROF(c, "k_tc_keys");
+  k_tc_keys<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, nnz, n_pad, keys);
+  GM_LAUNCH_CHECK(c);
+  gm_status s = sort_u64(c, keys, n_pad);
+  if (s != GM_OK) return s;
+  GM_PROF(c, "k_tc_flags");
+  k_tc_flags<<<eb, 256, 0, st>>>(nnz, keys, flag);
+  GM_LAUNCH_CHECK(c);
+  s = scan_i64(c, flag, pos, nnz);
+  if (s != GM_OK) return s;
+  int64_t U = 0;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(&U, pos + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  int32_t* ucol = (int32_t*)dev_alloc(c, std::max<int64_t>(U, 1) * sizeof(int32_t));
+  int32_t* ublk = (int32_t*)dev_alloc(c, std::max<int64_t>(U, 1) * sizeof(int32_t));
+  int64_t* bptr = (int64_t*)dev_alloc(c, (nblk + 1) * sizeof(int64_t));
+  if (!ucol || !ublk || !bptr) return set_error(c, GM_E_NOMEM, "tensor-core tile union");
+  GM_PROF(c, "k_tc_unique");
+  k_tc_unique<<<eb, 256, 0, st>>>(nnz, keys, flag, pos, ucol, ublk);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_tc_bptr");
+  k_tc_bptr<<<(int)std::min<int64_t>(ceil_div(U + 1, 256), 16 * sms), 256, 0, st>>>(U, nblk, ublk,
+                                                                                   bptr);
+  GM_LAUNCH_CHECK(c);
+  std::vector<int64_t> hb(nblk + 1), hk(nblk + 1, 0);
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(hb.data(), bptr, (nblk + 1) * sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, st));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  for (int64_t b = 0; b < nblk; ++b) hk[b + 1] = hk[b] + ceil_div(hb[b + 1] - hb[b], kTcK);
+  const int64_t nks = hk[nblk];
+  if (!ensure(c, c->tc_kbase, (nblk + 1) * sizeof(int64_t)) ||
+      !ensure(c, c->tc_upad, std::max<int64_t>(nks, 1) * kTcK * sizeof(int32_t)) ||
+      !ensure(c, c->tc_img, std::max<int64_t>(nks, 1) * 3 * kTcA))
+    return set_error(c, GM_E_NOMEM, "tensor-core tiles");
+  int64_t* kbase = (int64_t*)c->tc_kbase.p;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(kbase, hk.data(), (nblk + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, st));
+  GM_PROF(c, "k_tc_ucol");
+  k_tc_ucol<<<(int)std::min<int64_t>(nblk, 16 * sms), 256, 0, st>>>(nblk, bptr, kbase, ucol,
+                                                                    (int32_t*)c->tc_upad.p);
+  GM_LAUNCH_CHECK(c);
+  GM_CUDA_CHECK(c, cudaMemsetAsync(c->tc_img.p, 0, (size_t)nks * 3 * kTcA, st));
+  GM_PROF(c, "k_tc_fill");
+  k_tc_fill<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, (const float*)c->val, bptr, kbase, ucol,
+                                (unsigned char*)c->tc_img.p);
+  GM_LAUNCH_CHECK(c);
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  dev_free_now(c, bptr, (nblk + 1) * sizeof(int64_t));
+  dev_free_now(c, ublk, std::max<int64_t>(U, 1) * sizeof(int32_t));
+  dev_free_now(c, ucol, std::max<int64_t>(U, 1) * sizeof(int32_t));
+  dev_free_now(c, pos, (nnz + 1) * sizeof(int64_t));
+  dev_free_now(c, flag, std::max<int64_t>(nnz, 1) * sizeof(int64_t));
+  dev_free_now(c, keys, n_pad * sizeof(unsigned long long));
+  c->tc_nblk = nblk;
+  c->tc_nks = nks;
+  return GM_OK;
+}
+
+gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const float* P,
+                        const float* PD, float* Q, double* part_pq) {
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  dim3 grid((unsigned)c->tc_nblk, (unsigned)ceil_div(R, kTcCols));
+  GM_PROF(c, "k_panel_spmm_tc");
+  k_panel_spmm_tc<<<grid, 256, kTcSmem, c->stream>>>(
+      n, R, (const int64_t*)c->tc_kbase.p, (const int32_t*)c->tc_upad.p,
+      (const uint4*)c->tc_img.p, dv, P, PD, Q, part_pq, c->d_flags);
+  GM_LAUNCH_CHECK(c);
+  return GM_OK;
+}
+
+}  // namespace gm

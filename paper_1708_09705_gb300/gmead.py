@@ -35,7 +35,7 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_destroy", "gm_profile", "gm_kernel_time_count", "gm_kernel_time",
            "gm_site_update_noalloc", "gm_surrogate_param_count", "gm_surrogate_set_params",
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
-           "gm_surrogate_grad", "gm_get_probe_colours"]
+           "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries"]
 
 
 class GmError(RuntimeError):
@@ -97,6 +97,7 @@ def lib():
             getattr(L, f).argtypes = [vp, vp, vp]
         L.gm_get_perm.argtypes = [vp, vp]
         L.gm_get_probe_colours.argtypes = [vp, vp]
+        L.gm_get_entries.argtypes = [vp, i64, vp, vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.gm_stream.argtypes = [vp]
@@ -126,7 +127,7 @@ def lib():
                   "gm_get_sites", "gm_set_sites", "gm_get_prior", "gm_get_perm", "gm_get_csr",
                   "gm_get_stats", "gm_profile", "gm_kernel_time", "gm_surrogate_set_params",
                   "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
-                  "gm_surrogate_grad", "gm_get_probe_colours"):
+                  "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -235,6 +236,15 @@ class Context:
     def get_perm(self):
         out = np.empty(self.n, dtype=np.int64)
         self._check(lib().gm_get_perm(self._h, out.ctypes.data))
+        return out
+
+    def get_entries(self, i, j):
+        """Stored K_ij for caller index pairs (0 beyond the cutoff)."""
+        i = np.ascontiguousarray(i, dtype=np.int64)
+        j = np.ascontiguousarray(j, dtype=np.int64)
+        out = np.empty(len(i), dtype=np.float64)
+        self._check(lib().gm_get_entries(self._h, len(i), i.ctypes.data, j.ctypes.data,
+                                         out.ctypes.data))
         return out
 
     def get_probe_colours(self):
