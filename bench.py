@@ -198,6 +198,25 @@ def roofline_for(name, launches, ms, st, cfg_prec, panel):
                 "frac": ach / peak, "traffic": None, "kernel": name,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz",
                 "work_per_launch": f"2 x nnz x panel = {flops:.3e} flop"}
+    if name == "k_panel_spmm_tc":
+        # algorithmic work as above (FP32-grade products); the tensor pipe
+        # runs six BF16 MMAs per product (three-piece split) on the dense
+        # tile slots, so the FP32-grade peak is the BF16 peak / 6
+        flops = 2.0 * nnz * panel
+        ach = flops / avg_s / 1e12
+        bf = pk.get("bf16_tflops_sustained", 1700.0)
+        peak = bf / 6.0
+        groups = math.ceil(panel / 256)
+        exe = st.get("tile_ksteps", 0) * 6 * 2.0 * 128 * 16 * 256 * groups
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": name,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured) / 6 "
+                               "BF16 MMAs per FP32-grade product",
+                "work_per_launch": f"2 x nnz x panel = {flops:.3e} flop",
+                "tensor_pipe": {"executed_tflops": exe / avg_s / 1e12,
+                                "frac_of_bf16_sustained": exe / avg_s / 1e12 / bf,
+                                "executed_per_launch": f"{exe:.3e} flop (6 MMAs x dense "
+                                                       f"128x16x256 per K-step)"}}
     if name == "k_pair_quad":
         q = 64
         flops = QUAD_FLOPS_PER_NODE_PAIR * q * q * n_pairs

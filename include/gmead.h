@@ -135,6 +135,8 @@ typedef struct {
                                 (estimated error with the taper applied)    */
   int64_t probe_colours;   /* colour classes (variance solves) when probing,
                               summed over fields (last gm_build_cov)          */
+  int64_t tile_ksteps;     /* tensor-core tiles: K-steps of 16 union columns
+                              summed over 128-row blocks (0: CUDA-core path)  */
 } gm_stats;
 
 /* Fills *cfg with defaults: sigma2 1, L0 20 pc, rho_bar 1e-3 mag/pc, cutoff

@@ -371,6 +371,7 @@ bool tc_wanted(gm_ctx* c) {
 
 gm_status tc_tiles_build(gm_ctx* c) {
   c->tc_nblk = 0;
+  c->stats.tile_ksteps = 0;
   const int64_t n = c->n, nnz = c->nnz;
   cudaStream_t st = c->stream;
   const int sms = sm_count(c);
@@ -438,6 +439,7 @@ gm_status tc_tiles_build(gm_ctx* c) {
   dev_free_now(c, keys, n_pad * sizeof(unsigned long long));
   c->tc_nblk = nblk;
   c->tc_nks = nks;
+  c->stats.tile_ksteps = nks;
   return GM_OK;
 }
 

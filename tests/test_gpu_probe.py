@@ -109,7 +109,11 @@ def test_probed_variances_full_size_fp32(gm):
     print("probed vs exact at 20k: %d classes, var rel max %.2e median %.2e, mean %.2e"
           % (st["probe_colours"], rel.max(), np.median(rel), np.abs(mu_p - mu_x).max()))
     assert st["probe_colours"] < 20000 / 3
-    assert rel.max() < 2e-4
+    # both sides are FP32 panel solves stopped at a 1e-5 relative residual;
+    # each carries ~1e-4 relative variance error against FP64 (tensor-core
+    # test), so their difference is bounded by a few 1e-4, while the probing
+    # error itself (4e-8 at 2c on this field, oracle study) shows in the median
+    assert rel.max() < 1e-3 and np.median(rel) < 1e-5
     assert np.abs(mu_p - mu_x).max() < 1e-5
 
 
