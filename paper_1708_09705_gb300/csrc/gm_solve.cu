@@ -571,7 +571,30 @@ __global__ void __launch_bounds__(kBT) k_panel_update1(int64_t n, int R, const T
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const TV a = (TV)scal[c];
   double rz = 0, rr = 0;
-  for (int64_t i = w; i < n; i += nw) {
+  // four rows per pass with all loads issued first (memory-level parallelism)
+  int64_t i = w;
+  for (; i + 3 * nw < n; i += 4 * nw) {
+    TV x[4], p[4], r[4], q[4], m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = (i + u * nw) * R + c;
+      x[u] = X[k];
+      p[u] = P[k];
+      r[u] = Rr[k];
+      q[u] = Q[k];
+      m[u] = minv[i + u * nw];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = (i + u * nw) * R + c;
+      X[k] = x[u] + a * p[u];
+      const TV ri = r[u] - a * q[u];
+      Rr[k] = ri;
+      rz += (double)ri * (double)(m[u] * ri);
+      rr += (double)ri * (double)ri;
+    }
+  }
+  for (; i < n; i += nw) {
     int64_t k = i * R + c;
     X[k] += a * P[k];
     TV ri = Rr[k] - a * Q[k];
@@ -607,7 +630,26 @@ __global__ void __launch_bounds__(kBT) k_panel_update2(int64_t n, int R, const T
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const TV be = (TV)scal[R + c];
-  for (int64_t i = w; i < n; i += nw) {
+  int64_t i = w;
+  for (; i + 3 * nw < n; i += 4 * nw) {
+    TV r[4], p[4], m[4], d[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = (i + u * nw) * R + c;
+      r[u] = Rr[k];
+      p[u] = P[k];
+      m[u] = minv[i + u * nw];
+      d[u] = dv[i + u * nw];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t k = (i + u * nw) * R + c;
+      const TV pi = m[u] * r[u] + be * p[u];
+      P[k] = pi;
+      PD[k] = d[u] * pi;
+    }
+  }
+  for (; i < n; i += nw) {
     int64_t k = i * R + c;
     TV pi = minv[i] * Rr[k] + be * P[k];
     P[k] = pi;

@@ -4,11 +4,13 @@
 // in tensor memory).
 //
 // Precision: every FP32 operand x is split into three BF16 pieces,
-// x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2), which hold its 24
-// significand bits; of the nine piece products the six whose size is at
-// least 2^-16 of the leading one (x1y1, x1y2, x2y1, x1y3, x2y2, x3y1) are
-// accumulated, so each product carries an error below about 2^-22 of |xy|,
-// that of an FP32 product.
+// x1 = x rounded to BF16 (nearest even), x2 = the same of x - x1, x3 = the
+// same of x - x1 - x2; each difference is exact in FP32 and x1 + x2 + x3 == x.
+// Of the nine piece products the six whose size is at least 2^-16 of the
+// leading one (x1y1, x1y2, x2y1, x1y3, x2y2, x3y1) are accumulated, so each
+// product carries an error below 2^-23 of |xy| (the dropped terms), about
+// that of an FP32 product.  The rounding is done on the bit patterns with
+// integer adds and masks: no conversion instructions.
 //
 // Tile format.  Rows are cut into blocks of 128 (the stars are spatially
 // sorted, so a block's rows share most neighbours: 62 % of the dense slots
@@ -20,15 +22,13 @@
 // 16-byte core matrices.
 //
 // CTA = (row block, 256 panel columns), 256 threads.  Per K-step every thread
-// gathers its panel column's 16 values PD[u_k, c] (registers, one step ahead),
+// gathers its panel column's 16 values PD[u_k, c] (registers, two steps ahead),
 // splits them and writes the three 256 x 16 B operands; one thread issues the
 // six tcgen05.mma (M = 128 rows, N = 256 columns, K = 16) into the 128 x 256
 // FP32 accumulator and commits to the step buffer's mbarrier.  Two step
 // buffers: the gathers of step k+1 run while the tensor cores work on step k.
 // Epilogue: tcgen05.ld of the accumulator, Q = P + d o acc, and per-column
 // partial sums of P^T Q for the CG step length (fixed order).
-#include <cuda_bf16.h>
-
 #include <algorithm>
 #include <cstdlib>
 #include <vector>
@@ -89,18 +89,25 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// three BF16 pieces of x (x1 + x2 + x3 == x to 24 bits)
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b,
-                                       __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(b);
-  c = __float2bfloat16_rn(r2);
+// x rounded to BF16 (nearest, ties to even) as an FP32 bit pattern whose low
+// 16 bits are zero; the BF16 value is the high half
+__device__ __forceinline__ uint32_t bf16_rne_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+// three BF16 pieces of x (x1 + x2 + x3 == x)
+__device__ __forceinline__ void split3(float x, uint32_t& a, uint32_t& b, uint32_t& c) {
+  a = bf16_rne_bits(x);
+  const float r1 = x - __uint_as_float(a);
+  b = bf16_rne_bits(r1);
+  const float r2 = r1 - __uint_as_float(b);
+  c = bf16_rne_bits(r2);
+}
+
+// two BF16 values (high halves of lo and hi) in one 32-bit word, lo first
+__device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
+  return __byte_perm(lo, hi, 0x7632);
 }
 
 // ---------------------------------------------------------------- tiles
@@ -186,12 +193,12 @@ __global__ void k_tc_fill(int64_t n, const int64_t* __restrict__ row_ptr,
       }
       const int64_t q = lo - u0;
       unsigned char* step = img + (kbase[b] + q / kTcK) * (int64_t)(3 * kTcA);
-      __nv_bfloat16 p1, p2, p3;
+      uint32_t p1, p2, p3;
       split3(val[e], p1, p2, p3);
       const int off = tc_off(t, (int)(q % kTcK));
-      *reinterpret_cast<__nv_bfloat16*>(step + off) = p1;
-      *reinterpret_cast<__nv_bfloat16*>(step + kTcA + off) = p2;
-      *reinterpret_cast<__nv_bfloat16*>(step + 2 * kTcA + off) = p3;
+      *reinterpret_cast<uint16_t*>(step + off) = (uint16_t)(p1 >> 16);
+      *reinterpret_cast<uint16_t*>(step + kTcA + off) = (uint16_t)(p2 >> 16);
+      *reinterpret_cast<uint16_t*>(step + 2 * kTcA + off) = (uint16_t)(p3 >> 16);
     }
   }
 }
@@ -231,26 +238,42 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  // registers of one step: three 16-byte pieces of the tile image and the
-  // column's 16 gathered panel values
-  uint4 ra[3];
-  float rb[16];
-  auto load_step = [&](int64_t ks) {
-    const uint4* src = img + (ks0 + ks) * (3 * kTcA / 16);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) ra[q] = __ldg(src + t + 256 * q);
+  // Register pipeline: the union column indices of a step are loaded three
+  // steps ahead, its tile pieces and gathered panel values two steps ahead
+  // (the gathers wait on the indices, so each is one global round trip).
+  struct Vals {
+    uint4 a[3];    // this thread's three 16-byte pieces of the tile image
+    float b[16];   // the column's 16 gathered panel values
+  };
+  Vals v0{}, v1{};
+  int4 idx[4];
+  auto load_idx = [&](int64_t ks) {
     const int4* u4 = reinterpret_cast<const int4*>(upad + (ks0 + ks) * kTcK);
 #pragma unroll
+    for (int q = 0; q < 4; ++q) idx[q] = __ldg(u4 + q);
+  };
+  auto load_vals = [&](Vals& v, int64_t ks) {
+    const uint4* src = img + (ks0 + ks) * (3 * kTcA / 16);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v.a[q] = __ldg(src + t + 256 * q);
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int4 u = __ldg(u4 + q);
-      const int idx[4] = {u.x, u.y, u.z, u.w};
+      const int j[4] = {idx[q].x, idx[q].y, idx[q].z, idx[q].w};
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        rb[4 * q + r] = live ? __ldg(PD + (int64_t)idx[r] * R + col) : 0.f;
+        v.b[4 * q + r] = live ? __ldg(PD + (int64_t)j[r] * R + col) : 0.f;
     }
   };
 
-  if (nks > 0) load_step(0);
+  if (nks > 0) {
+    load_idx(0);
+    load_vals(v0, 0);
+  }
+  if (nks > 1) {
+    load_idx(1);
+    load_vals(v1, 1);
+  }
+  if (nks > 2) load_idx(2);
   for (int64_t ks = 0; ks < nks; ++ks) {
     const int s = (int)(ks & 1);
     unsigned char* sA = smem + s * kTcStage;
@@ -258,15 +281,15 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
     // the buffer was last read by the MMAs of step ks - 2
     if (ks >= 2 && !tc_wait(tc_smem(&mbar[s]), (uint32_t)(((ks - 2) >> 1) & 1))) abort_flag = 1;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) reinterpret_cast<uint4*>(sA)[t + 256 * q] = ra[q];
+    for (int q = 0; q < 3; ++q) reinterpret_cast<uint4*>(sA)[t + 256 * q] = v0.a[q];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       uint32_t w1[4], w2[4], w3[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        __nv_bfloat16 a0, a1, a2, b0, b1, b2;
-        split3(rb[8 * h + 2 * q], a0, a1, a2);
-        split3(rb[8 * h + 2 * q + 1], b0, b1, b2);
+        uint32_t a0, a1, a2, b0, b1, b2;
+        split3(v0.b[8 * h + 2 * q], a0, a1, a2);
+        split3(v0.b[8 * h + 2 * q + 1], b0, b1, b2);
         w1[q] = pack2(a0, b0);
         w2[q] = pack2(a1, b1);
         w3[q] = pack2(a2, b2);
@@ -276,7 +299,9 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
       *reinterpret_cast<uint4*>(sB + kTcB + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
       *reinterpret_cast<uint4*>(sB + 2 * kTcB + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
     }
-    if (ks + 1 < nks) load_step(ks + 1);
+    v0 = v1;
+    if (ks + 2 < nks) load_vals(v1, ks + 2);
+    if (ks + 3 < nks) load_idx(ks + 3);
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
