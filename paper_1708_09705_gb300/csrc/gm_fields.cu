@@ -11,8 +11,10 @@
 // items, element-wise updates over (field, column chunk, row segment)
 // items with per-column partial sums, and a per-column reduction that keeps
 // each column's CG scalars.  The sequence of one iteration is captured as a
-// CUDA graph (eight iterations per graph launch); the block shape of the
-// panel product is autotuned on first use.
+// CUDA graph (eight iterations per graph launch).  The panel product runs on
+// the tensor cores over field-aligned 128-row tiles (prefetch depth tuned on
+// first use) or, with GM_SPMM=simt, on the CUDA cores over 32-row tiles
+// (block shape tuned on first use).
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -44,6 +46,11 @@ struct PackState {
   int32_t* blk_field = nullptr;
   Buffer X, R, Pp, PD, Q, pa, pb, scal, active;
   int wpb = 0;                   // tuned warps per block of the panel product (4 or 8)
+  // tensor-core product: (tile block, column group) items, per-block panel base and width
+  int2* tc_items = nullptr;
+  int64_t n_tc_items = 0;
+  int64_t* tc_base = nullptr;
+  int32_t* tc_width = nullptr;
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -389,6 +396,21 @@ static gm_status pack_setup(gm_ctx* c) {
   }
   S.n_sitems8 = (int64_t)it8.size();
   S.n_sitems4 = (int64_t)it4.size();
+  // tensor-core tiles (field-aligned 128-row blocks): items and panel geometry
+  std::vector<int2> itc;
+  std::vector<int64_t> tbase(std::max<int64_t>(c->tc_nblk, 1), 0);
+  std::vector<int32_t> twidth(std::max<int64_t>(c->tc_nblk, 1), 0);
+  if (c->tc_nblk > 0) {
+    for (int f = 0; f < nf; ++f) {
+      const PackField& F = S.h_pf[f];
+      for (int64_t b = c->h_tc_boff[f]; b < c->h_tc_boff[f + 1]; ++b) {
+        tbase[b] = F.P - F.row0 * F.W;
+        twidth[b] = (int32_t)F.W;
+        for (int64_t g = 0; g < ceil_div(F.W, 256); ++g) itc.push_back(make_int2((int)b, (int)g));
+      }
+    }
+  }
+  S.n_tc_items = (int64_t)itc.size();
   cudaStream_t st = c->stream;
   S.pf = (PackField*)dev_alloc(c, nf * sizeof(PackField));
   S.wptr = (int64_t*)dev_alloc(c, (nf + 1) * sizeof(int64_t));
@@ -396,8 +418,19 @@ static gm_status pack_setup(gm_ctx* c) {
   S.sitems = (int2*)dev_alloc(c, std::max<int64_t>(1, S.n_sitems8) * sizeof(int2));
   S.sitems4 = (int2*)dev_alloc(c, std::max<int64_t>(1, S.n_sitems4) * sizeof(int2));
   S.blk_field = (int32_t*)dev_alloc(c, std::max<int64_t>(1, c->t_nblk) * sizeof(int32_t));
-  if (!S.pf || !S.wptr || !S.eitems || !S.sitems || !S.sitems4 || !S.blk_field)
+  S.tc_items = (int2*)dev_alloc(c, std::max<int64_t>(1, S.n_tc_items) * sizeof(int2));
+  S.tc_base = (int64_t*)dev_alloc(c, tbase.size() * sizeof(int64_t));
+  S.tc_width = (int32_t*)dev_alloc(c, twidth.size() * sizeof(int32_t));
+  if (!S.pf || !S.wptr || !S.eitems || !S.sitems || !S.sitems4 || !S.blk_field || !S.tc_items ||
+      !S.tc_base || !S.tc_width)
     return set_error(c, GM_E_NOMEM, "field pack tables");
+  if (S.n_tc_items > 0)
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(S.tc_items, itc.data(), S.n_tc_items * sizeof(int2),
+                                     cudaMemcpyHostToDevice, st));
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(S.tc_base, tbase.data(), tbase.size() * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, st));
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(S.tc_width, twidth.data(), twidth.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, st));
   GM_CUDA_CHECK(c, cudaMemcpyAsync(S.pf, S.h_pf.data(), nf * sizeof(PackField), cudaMemcpyHostToDevice, st));
   GM_CUDA_CHECK(c, cudaMemcpyAsync(S.wptr, wptr.data(), (nf + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   GM_CUDA_CHECK(c, cudaMemcpyAsync(S.eitems, eit.data(), S.n_eitems * sizeof(int4), cudaMemcpyHostToDevice, st));
@@ -422,6 +455,11 @@ static gm_status pack_setup(gm_ctx* c) {
 }
 
 static void launch_spmm(gm_ctx* c, PackState& S, int wpb, cudaStream_t st, const float* dv) {
+  if (S.n_tc_items > 0) {
+    panel_spmm_tc_packed(c, S.n_tc_items, S.tc_items, S.tc_base, S.tc_width, dv,
+                         (const float*)S.Pp.p, (const float*)S.PD.p, (float*)S.Q.p, st, false);
+    return;
+  }
   const int sms = sm_count(c);
   if (wpb == 4) {
     const int g = (int)std::min<int64_t>(S.n_sitems4, 8 * sms);
@@ -441,6 +479,10 @@ static void launch_spmm(gm_ctx* c, PackState& S, int wpb, cudaStream_t st, const
 // Times both block shapes of the panel product once and keeps the faster;
 // the choice can be pinned with GM_PANEL_WARPS=4|8.
 static gm_status autotune(gm_ctx* c, PackState& S, const float* dv) {
+  if (S.n_tc_items > 0)
+    return panel_spmm_tc_packed(c, S.n_tc_items, S.tc_items, S.tc_base, S.tc_width, dv,
+                                (const float*)S.Pp.p, (const float*)S.PD.p, (float*)S.Q.p,
+                                c->stream, true);
   if (S.wpb) return GM_OK;
   if (const char* env = std::getenv("GM_PANEL_WARPS")) {
     const int w = std::atoi(env);

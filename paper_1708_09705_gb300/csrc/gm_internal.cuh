@@ -120,6 +120,9 @@ struct gm_ctx {
   // K-step prefix per block, padded union columns, BF16 operand images
   int64_t tc_nblk = 0, tc_nks = 0;
   gm::Buffer tc_kbase, tc_upad, tc_img;
+  std::vector<int64_t> h_tc_boff;   // first tile block of each field (n_fields + 1)
+  gm::Buffer tc_brow0, tc_boffd;    // first row of each block (+ end); device h_tc_boff
+  int tc_pf = 0;                    // tuned prefetch depth of the tile product (0: untuned)
   double* kdiag = nullptr;
   double* prior_m = nullptr;
 
@@ -277,6 +280,12 @@ bool tc_wanted(gm_ctx* c);
 gm_status tc_tiles_build(gm_ctx* c);
 gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const float* P,
                         const float* PD, float* Q, double* part_pq);
+// Packed multi-field panels (no partials); tune = choose the prefetch depth
+// (on the context stream, outside any graph capture) instead of launching.
+gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
+                               const int64_t* blk_base, const int32_t* blk_width, const float* dv,
+                               const float* P, const float* PD, float* Q, cudaStream_t st,
+                               bool tune);
 
 // Row-block tiles of K for the FP32 variance panels (gm_tiles.cu).
 gm_status tiles_build(gm_ctx* c);

@@ -111,14 +111,27 @@ __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
 }
 
 // ---------------------------------------------------------------- tiles
+// Tile block of internal row i: blocks of 128 rows counted from each field's
+// first row (no block straddles two fields).
+struct TcBlocks {
+  const int32_t* field_of;  // null: one field
+  const int64_t* fptr;      // first row of each field
+  const int64_t* boff;      // first block of each field
+};
+__device__ __forceinline__ int64_t tc_block(int64_t i, const TcBlocks& tb) {
+  if (!tb.field_of) return i / kTcRows;
+  const int f = tb.field_of[i];
+  return tb.boff[f] + (i - tb.fptr[f]) / kTcRows;
+}
+
 __global__ void k_tc_keys(int64_t n, const int64_t* __restrict__ row_ptr,
                           const int32_t* __restrict__ col, int64_t nnz, int64_t n_pad,
-                          unsigned long long* __restrict__ keys) {
+                          TcBlocks tb, unsigned long long* __restrict__ keys) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < n; i += nw) {
-    const unsigned long long hi = (unsigned long long)(i / kTcRows) << 32;
+    const unsigned long long hi = (unsigned long long)tc_block(i, tb) << 32;
     for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32)
       keys[e] = hi | (unsigned long long)(unsigned)col[e];
   }
@@ -171,18 +184,19 @@ __global__ void k_tc_ucol(int64_t nblk, const int64_t* __restrict__ bptr,
   }
 }
 
-// Operand images: entry (i, j) of block b = i / 128 at union position q of j
-// goes to K-step kbase[b] + q / 16, column q % 16, row i % 128, three pieces.
+// Operand images: entry (i, j) of block b at union position q of j goes to
+// K-step kbase[b] + q / 16, column q % 16, row i - brow0[b], three pieces.
 __global__ void k_tc_fill(int64_t n, const int64_t* __restrict__ row_ptr,
                           const int32_t* __restrict__ col, const float* __restrict__ val,
                           const int64_t* __restrict__ bptr, const int64_t* __restrict__ kbase,
-                          const int32_t* __restrict__ ucol, unsigned char* __restrict__ img) {
+                          const int32_t* __restrict__ ucol, TcBlocks tb,
+                          const int64_t* __restrict__ brow0, unsigned char* __restrict__ img) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < n; i += nw) {
-    const int64_t b = i / kTcRows;
-    const int t = (int)(i - b * kTcRows);
+    const int64_t b = tc_block(i, tb);
+    const int t = (int)(i - brow0[b]);
     const int64_t u0 = bptr[b], u1 = bptr[b + 1];
     for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
       const int32_t j = col[e];
@@ -204,11 +218,26 @@ __global__ void k_tc_fill(int64_t n, const int64_t* __restrict__ row_ptr,
 }
 
 // ---------------------------------------------------------------- product
+// Geometry of the panels.  One panel (single field): element (row, col) at
+// row * R + col, CTA (blockIdx.x = row block, blockIdx.y = column group),
+// partials of P^T Q per (row block, column).  Packed fields: element (row,
+// col) of a field at base_b + row * W_b + col with base_b = P_f - row0_f W_f,
+// CTA = items[blockIdx.x] = (row block, column group of its field), no
+// partials (the packed CG forms P^T Q in its element-wise pass).
+struct TcPanels {
+  const int64_t* base;   // per tile block (packed) or null
+  const int32_t* width;  // per tile block (packed) or null
+  const int64_t* row0;   // first row of each tile block (packed) or null
+  const int2* items;     // (block, column group) per CTA (packed) or null
+};
+
+// PF: gathered panel values are loaded PF steps ahead (indices PF + 1).
+template <int PF>
 __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
     int64_t n, int R, const int64_t* __restrict__ kbase, const int32_t* __restrict__ upad,
     const uint4* __restrict__ img, const float* __restrict__ dv, const float* __restrict__ P,
     const float* __restrict__ PD, float* __restrict__ Q, double* __restrict__ part_pq,
-    unsigned* __restrict__ flags) {
+    TcPanels pk, unsigned* __restrict__ flags) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
@@ -216,10 +245,27 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
   double* sh_pq = reinterpret_cast<double*>(smem + 2 * kTcStage);  // [4][256]
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int64_t b = blockIdx.x;
-  const int c0 = blockIdx.y * kTcCols;
+  const bool packed = pk.items != nullptr;
+  int64_t b, base, brow0, bend;
+  int c0, W;
+  if (packed) {
+    const int2 it = pk.items[blockIdx.x];
+    b = it.x;
+    c0 = it.y * kTcCols;
+    W = pk.width[b];
+    base = pk.base[b];
+    brow0 = pk.row0[b];
+    bend = pk.row0[b + 1];
+  } else {
+    b = blockIdx.x;
+    c0 = blockIdx.y * kTcCols;
+    W = R;
+    base = 0;
+    brow0 = b * kTcRows;
+    bend = min(brow0 + kTcRows, n);
+  }
   const int col = c0 + t;
-  const bool live = col < R;
+  const bool live = col < W;
   const int64_t ks0 = kbase[b], nks = kbase[b + 1] - ks0;
 
   if (t == 0) {
@@ -238,9 +284,9 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  // Register pipeline: the union column indices of a step are loaded three
-  // steps ahead, its tile pieces and gathered panel values two steps ahead
-  // (the gathers wait on the indices, so each is one global round trip).
+  // Register pipeline: the tile pieces and gathered panel values of a step
+  // are loaded PF steps ahead and its union column indices PF + 1 steps
+  // ahead (the gathers wait on the indices, so each is one global round trip).
   struct Vals {
     uint4 a[3];    // this thread's three 16-byte pieces of the tile image
     float b[16];   // the column's 16 gathered panel values
@@ -261,7 +307,7 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
       const int j[4] = {idx[q].x, idx[q].y, idx[q].z, idx[q].w};
 #pragma unroll
       for (int r = 0; r < 4; ++r)
-        v.b[4 * q + r] = live ? __ldg(PD + (int64_t)j[r] * R + col) : 0.f;
+        v.b[4 * q + r] = live ? __ldg(PD + (base + (int64_t)j[r] * W + col)) : 0.f;
     }
   };
 
@@ -269,11 +315,11 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
     load_idx(0);
     load_vals(v0, 0);
   }
-  if (nks > 1) {
+  if (PF == 2 && nks > 1) {
     load_idx(1);
     load_vals(v1, 1);
   }
-  if (nks > 2) load_idx(2);
+  if (nks > PF) load_idx(PF);
   for (int64_t ks = 0; ks < nks; ++ks) {
     const int s = (int)(ks & 1);
     unsigned char* sA = smem + s * kTcStage;
@@ -299,9 +345,14 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
       *reinterpret_cast<uint4*>(sB + kTcB + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
       *reinterpret_cast<uint4*>(sB + 2 * kTcB + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
     }
-    v0 = v1;
-    if (ks + 2 < nks) load_vals(v1, ks + 2);
-    if (ks + 3 < nks) load_idx(ks + 3);
+    if (PF == 2) {
+      v0 = v1;
+      if (ks + 2 < nks) load_vals(v1, ks + 2);
+      if (ks + 3 < nks) load_idx(ks + 3);
+    } else {
+      if (ks + 1 < nks) load_vals(v0, ks + 1);
+      if (ks + 2 < nks) load_idx(ks + 2);
+    }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -333,8 +384,8 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
   if (!abort_flag) {
     const int quad = warp & 3, half = warp >> 2;
     const int r = 32 * quad + lane;
-    const int64_t row = b * kTcRows + r;
-    const bool vrow = row < n;
+    const int64_t row = brow0 + r;
+    const bool vrow = row < bend;
     const float dr = vrow ? dv[row] : 0.f;
 #pragma unroll 1
     for (int ch = 0; ch < 8; ++ch) {
@@ -351,23 +402,25 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
       for (int k = 0; k < 16; ++k) {
         const int cg = c0 + cl + k;
         double pq = 0.0;
-        if (vrow && cg < R) {
-          const int64_t at = row * R + cg;
+        if (vrow && cg < W) {
+          const int64_t at = base + row * W + cg;
           const float p = P[at];
           const float q = p + dr * __uint_as_float(u[k]);
           Q[at] = q;
           pq = (double)p * (double)q;
         }
+        if (!packed) {  // uniform over the CTA
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
-        if (lane == 0) sh_pq[quad * kTcCols + cl + k] = pq;
+          for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
+          if (lane == 0) sh_pq[quad * kTcCols + cl + k] = pq;
+        }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (!abort_flag) {
-    if (live)
+    if (live && !packed)
       part_pq[b * R + col] = ((sh_pq[t] + sh_pq[kTcCols + t]) + sh_pq[2 * kTcCols + t]) +
                              sh_pq[3 * kTcCols + t];
   } else if (t == 0) {
@@ -387,9 +440,9 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
 }
 
 // ---------------------------------------------------------------- host
-// The tensor-core path serves single-field FP32 contexts unless GM_SPMM=simt.
+// The tensor-core path serves FP32 contexts unless GM_SPMM=simt.
 bool tc_wanted(gm_ctx* c) {
-  if (c->cfg.precision != GM_PREC_FP32 || c->n_fields != 1) return false;
+  if (c->cfg.precision != GM_PREC_FP32) return false;
   const char* e = std::getenv("GM_SPMM");
   return !(e && e[0] == 's');
 }
@@ -400,7 +453,25 @@ gm_status tc_tiles_build(gm_ctx* c) {
   const int64_t n = c->n, nnz = c->nnz;
   cudaStream_t st = c->stream;
   const int sms = sm_count(c);
-  const int64_t nblk = ceil_div(n, kTcRows);
+  // field-aligned blocks of 128 rows
+  const int nf = c->n_fields;
+  c->h_tc_boff.assign(nf + 1, 0);
+  for (int f = 0; f < nf; ++f)
+    c->h_tc_boff[f + 1] = c->h_tc_boff[f] + ceil_div(c->h_fptr[f + 1] - c->h_fptr[f], kTcRows);
+  const int64_t nblk = c->h_tc_boff[nf];
+  std::vector<int64_t> hr0(nblk + 1, n);
+  for (int f = 0; f < nf; ++f)
+    for (int64_t b = c->h_tc_boff[f]; b < c->h_tc_boff[f + 1]; ++b)
+      hr0[b] = c->h_fptr[f] + (b - c->h_tc_boff[f]) * kTcRows;
+  if (!ensure(c, c->tc_brow0, (nblk + 1) * sizeof(int64_t)) ||
+      !ensure(c, c->tc_boffd, (nf + 1) * sizeof(int64_t)))
+    return set_error(c, GM_E_NOMEM, "tensor-core block tables");
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(c->tc_brow0.p, hr0.data(), (nblk + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, st));
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(c->tc_boffd.p, c->h_tc_boff.data(), (nf + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, st));
+  TcBlocks tb{nullptr, nullptr, nullptr};
+  if (nf > 1) tb = TcBlocks{c->field_of, c->fptr, (const int64_t*)c->tc_boffd.p};
   int64_t n_pad = 1024;
   while (n_pad < nnz) n_pad <<= 1;
   unsigned long long* keys = (unsigned long long*)dev_alloc(c, n_pad * sizeof(unsigned long long));
@@ -410,7 +481,7 @@ gm_status tc_tiles_build(gm_ctx* c) {
   const int wb = (int)std::min<int64_t>(ceil_div(n * 32, 256), 32 * sms);
   const int eb = (int)std::min<int64_t>(ceil_div(nnz, 256), 16 * sms);
   GM_PROF(c, "k_tc_keys");
-  k_tc_keys<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, nnz, n_pad, keys);
+  k_tc_keys<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, nnz, n_pad, tb, keys);
   GM_LAUNCH_CHECK(c);
   gm_status s = sort_u64(c, keys, n_pad);
   if (s != GM_OK) return s;
@@ -453,7 +524,7 @@ gm_status tc_tiles_build(gm_ctx* c) {
   GM_CUDA_CHECK(c, cudaMemsetAsync(c->tc_img.p, 0, (size_t)nks * 3 * kTcA, st));
   GM_PROF(c, "k_tc_fill");
   k_tc_fill<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, (const float*)c->val, bptr, kbase, ucol,
-                                (unsigned char*)c->tc_img.p);
+                                tb, (const int64_t*)c->tc_brow0.p, (unsigned char*)c->tc_img.p);
   GM_LAUNCH_CHECK(c);
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
   dev_free_now(c, bptr, (nblk + 1) * sizeof(int64_t));
@@ -468,17 +539,81 @@ gm_status tc_tiles_build(gm_ctx* c) {
   return GM_OK;
 }
 
+static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const float* dv,
+                           const float* P, const float* PD, float* Q, double* part_pq,
+                           TcPanels pk, cudaStream_t st) {
+  const int64_t* kb = (const int64_t*)c->tc_kbase.p;
+  const int32_t* up = (const int32_t*)c->tc_upad.p;
+  const uint4* im = (const uint4*)c->tc_img.p;
+  if (pf == 2)
+    k_panel_spmm_tc<2><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
+                                                   c->d_flags);
+  else
+    k_panel_spmm_tc<1><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
+                                                   c->d_flags);
+  return GM_OK;
+}
+
+// Prefetch depth of the tile product: GM_TC_PREFETCH=1|2, else the faster of
+// the two on the context's first panel product (one timed launch each; the
+// product is idempotent: Q is overwritten).
+static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv, const float* P,
+                         const float* PD, float* Q, double* part_pq, TcPanels pk) {
+  if (c->tc_pf) return GM_OK;
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<2>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  if (const char* e = std::getenv("GM_TC_PREFETCH")) {
+    const int v = std::atoi(e);
+    if (v == 1 || v == 2) {
+      c->tc_pf = v;
+      return GM_OK;
+    }
+  }
+  cudaEvent_t a, b;
+  GM_CUDA_CHECK(c, cudaEventCreate(&a));
+  GM_CUDA_CHECK(c, cudaEventCreate(&b));
+  float best = 1e30f;
+  for (int pf : {1, 2}) {
+    float ms = 0;
+    GM_CUDA_CHECK(c, cudaEventRecord(a, c->stream));
+    launch_tc(c, pf, grid, n, R, dv, P, PD, Q, part_pq, pk, c->stream);
+    GM_CUDA_CHECK(c, cudaEventRecord(b, c->stream));
+    GM_CUDA_CHECK(c, cudaEventSynchronize(b));
+    GM_LAUNCH_CHECK(c);
+    GM_CUDA_CHECK(c, cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) {
+      best = ms;
+      c->tc_pf = pf;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return GM_OK;
+}
+
 gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const float* P,
                         const float* PD, float* Q, double* part_pq) {
-  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   dim3 grid((unsigned)c->tc_nblk, (unsigned)ceil_div(R, kTcCols));
+  const TcPanels pk{nullptr, nullptr, nullptr, nullptr};
+  gm_status s = tc_tune(c, grid, n, R, dv, P, PD, Q, part_pq, pk);
+  if (s != GM_OK) return s;
   GM_PROF(c, "k_panel_spmm_tc");
-  k_panel_spmm_tc<<<grid, 256, kTcSmem, c->stream>>>(
-      n, R, (const int64_t*)c->tc_kbase.p, (const int32_t*)c->tc_upad.p,
-      (const uint4*)c->tc_img.p, dv, P, PD, Q, part_pq, c->d_flags);
+  launch_tc(c, c->tc_pf, grid, n, R, dv, P, PD, Q, part_pq, pk, c->stream);
   GM_LAUNCH_CHECK(c);
   return GM_OK;
+}
+
+// Packed multi-field panels: one CTA per (tile block, column group) item.
+gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
+                               const int64_t* blk_base, const int32_t* blk_width, const float* dv,
+                               const float* P, const float* PD, float* Q, cudaStream_t st,
+                               bool tune) {
+  const TcPanels pk{blk_base, blk_width, (const int64_t*)c->tc_brow0.p, items};
+  dim3 grid((unsigned)n_items);
+  if (tune) return tc_tune(c, grid, c->n, 0, dv, P, PD, Q, nullptr, pk);
+  return launch_tc(c, c->tc_pf, grid, c->n, 0, dv, P, PD, Q, nullptr, pk, st);
 }
 
 }  // namespace gm
