@@ -386,7 +386,9 @@ static gm_status pack_setup(gm_ctx* c) {
   S.n_eitems = (int64_t)eit.size();
   std::vector<int2> it8, it4;
   std::vector<int32_t> bf(c->t_nblk);
-  for (int f = 0; f < nf; ++f) {
+  // CUDA-core 32-row tiles exist only when the tensor-core tiles were not
+  // built (their block table h_boff is empty otherwise)
+  for (int f = 0; c->t_nblk > 0 && f < nf; ++f) {
     const int64_t chunks = S.h_pf[f].W / 32;
     for (int64_t b = c->h_boff[f]; b < c->h_boff[f + 1]; ++b) {
       bf[b] = f;
