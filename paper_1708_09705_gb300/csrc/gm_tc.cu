@@ -218,6 +218,52 @@ __global__ void k_tc_fill(int64_t n, const int64_t* __restrict__ row_ptr,
 }
 
 // ---------------------------------------------------------------- product
+// Epilogue of a tile: warps 0-7 read the 128 x 256 accumulator (warp w: TMEM
+// lanes 32 (w mod 4) .., columns 128 (w div 4) ..), write Q = P + d o acc and,
+// for a single panel, the per-column partial sums of P^T Q into sh_pq[4][256].
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, int64_t brow0,
+                                            int64_t bend, int64_t base, int W, int c0,
+                                            bool packed, const float* __restrict__ dv,
+                                            const float* __restrict__ P, float* __restrict__ Q,
+                                            double* sh_pq) {
+  {
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = 32 * quad + lane;
+    const int64_t row = brow0 + r;
+    const bool vrow = row < bend;
+    const float dr = vrow ? dv[row] : 0.f;
+#pragma unroll 1
+    for (int ch = 0; ch < 8; ++ch) {
+      const int cl = 128 * half + 16 * ch;
+      uint32_t u[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+            "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]),
+            "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+          : "r"(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cl));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int cg = c0 + cl + k;
+        double pq = 0.0;
+        if (vrow && cg < W) {
+          const int64_t at = base + row * W + cg;
+          const float p = P[at];
+          const float q = p + dr * __uint_as_float(u[k]);
+          Q[at] = q;
+          pq = (double)p * (double)q;
+        }
+        if (!packed) {  // uniform over the CTA
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
+          if (lane == 0) sh_pq[quad * kTcCols + cl + k] = pq;
+        }
+      }
+    }
+  }
+}
+
 // Geometry of the panels.  One panel (single field): element (row, col) at
 // row * R + col, CTA (blockIdx.x = row block, blockIdx.y = column group),
 // partials of P^T Q per (row block, column).  Packed fields: element (row,
@@ -381,42 +427,8 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   __syncthreads();
-  if (!abort_flag) {
-    const int quad = warp & 3, half = warp >> 2;
-    const int r = 32 * quad + lane;
-    const int64_t row = brow0 + r;
-    const bool vrow = row < bend;
-    const float dr = vrow ? dv[row] : 0.f;
-#pragma unroll 1
-    for (int ch = 0; ch < 8; ++ch) {
-      const int cl = 128 * half + 16 * ch;
-      uint32_t u[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
-            "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]),
-            "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
-          : "r"(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cl));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int cg = c0 + cl + k;
-        double pq = 0.0;
-        if (vrow && cg < W) {
-          const int64_t at = base + row * W + cg;
-          const float p = P[at];
-          const float q = p + dr * __uint_as_float(u[k]);
-          Q[at] = q;
-          pq = (double)p * (double)q;
-        }
-        if (!packed) {  // uniform over the CTA
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
-          if (lane == 0) sh_pq[quad * kTcCols + cl + k] = pq;
-        }
-      }
-    }
-  }
+  if (!abort_flag)
+    tc_epilogue(tmem, warp, lane, brow0, bend, base, W, c0, packed, dv, P, Q, sh_pq);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (!abort_flag) {
@@ -434,6 +446,205 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
   }
   __syncthreads();
   if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  }
+}
+
+
+// Warp-specialised variant: warps 0-7 (one panel column per thread) fill a
+// ring of kTcRing stage buffers and arrive on the stage's "full" mbarrier;
+// warp 8 waits on it, issues the six MMAs and commits to the stage's "empty"
+// mbarrier, which the fillers wait on before reusing the buffer.  No CTA-wide
+// barrier per K-step: the fillers run up to kTcRing - 1 steps ahead of the
+// tensor cores.  Every wait is bounded and also gives up when another thread
+// has given up (shared abort flag).
+constexpr int kTcRing = 3;
+constexpr int kTcSmemWs = kTcRing * kTcStage;  // P^T Q partials reuse stage 0
+
+__device__ __forceinline__ bool tc_wait_or_abort(uint32_t mbar, uint32_t parity,
+                                                 volatile int* abort_flag) {
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+    if (done) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(288, 2) k_panel_spmm_tc_ws(
+    int64_t n, int R, const int64_t* __restrict__ kbase, const int32_t* __restrict__ upad,
+    const uint4* __restrict__ img, const float* __restrict__ dv, const float* __restrict__ P,
+    const float* __restrict__ PD, float* __restrict__ Q, double* __restrict__ part_pq,
+    TcPanels pk, unsigned* __restrict__ flags) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t full[kTcRing], empty[kTcRing];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  volatile int* abort_v = &abort_flag;
+  double* sh_pq = reinterpret_cast<double*>(smem);  // [4][256], after the last MMA
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const bool packed = pk.items != nullptr;
+  int64_t b, base, brow0, bend;
+  int c0, W;
+  if (packed) {
+    const int2 it = pk.items[blockIdx.x];
+    b = it.x;
+    c0 = it.y * kTcCols;
+    W = pk.width[b];
+    base = pk.base[b];
+    brow0 = pk.row0[b];
+    bend = pk.row0[b + 1];
+  } else {
+    b = blockIdx.x;
+    c0 = blockIdx.y * kTcCols;
+    W = R;
+    base = 0;
+    brow0 = b * kTcRows;
+    bend = min(brow0 + kTcRows, n);
+  }
+  const int col = c0 + t;
+  const bool live = t < 256 && col < W;
+  const int64_t ks0 = kbase[b], nks = kbase[b + 1] - ks0;
+
+  if (t == 0) {
+    abort_flag = 0;
+    for (int q = 0; q < kTcRing; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" ::"r"(tc_smem(&full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&empty[q])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        tc_smem(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  if (warp < 8) {
+    // ---- fillers: gather, split and stage one K-step per ring slot
+    uint4 ra[3];
+    float rb[16];
+    int4 idx[4];
+    auto load_idx = [&](int64_t ks) {
+      const int4* u4 = reinterpret_cast<const int4*>(upad + (ks0 + ks) * kTcK);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) idx[q] = __ldg(u4 + q);
+    };
+    auto load_vals = [&](int64_t ks) {
+      const uint4* src = img + (ks0 + ks) * (3 * kTcA / 16);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) ra[q] = __ldg(src + t + 256 * q);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j[4] = {idx[q].x, idx[q].y, idx[q].z, idx[q].w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          rb[4 * q + r] = live ? __ldg(PD + (base + (int64_t)j[r] * W + col)) : 0.f;
+      }
+    };
+    if (nks > 0) {
+      load_idx(0);
+      load_vals(0);
+    }
+    if (nks > 1) load_idx(1);
+    for (int64_t ks = 0; ks < nks; ++ks) {
+      const int s = (int)(ks % kTcRing);
+      const int64_t use = ks / kTcRing;
+      unsigned char* sA = smem + s * kTcStage;
+      unsigned char* sB = sA + 3 * kTcA;
+      // the slot was last read by the MMAs of step ks - kTcRing
+      if (use > 0 && !tc_wait_or_abort(tc_smem(&empty[s]), (uint32_t)((use - 1) & 1), abort_v)) {
+        abort_flag = 1;
+        break;
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) reinterpret_cast<uint4*>(sA)[t + 256 * q] = ra[q];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t a0, a1, a2, b0, b1, b2;
+          split3(rb[8 * h + 2 * q], a0, a1, a2);
+          split3(rb[8 * h + 2 * q + 1], b0, b1, b2);
+          w1[q] = pack2(a0, b0);
+          w2[q] = pack2(a1, b1);
+          w3[q] = pack2(a2, b2);
+        }
+        const int off = tc_off(t, 8 * h);
+        *reinterpret_cast<uint4*>(sB + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4*>(sB + kTcB + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        *reinterpret_cast<uint4*>(sB + 2 * kTcB + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem(&full[s])) : "memory");
+      if (ks + 1 < nks) load_vals(ks + 1);
+      if (ks + 2 < nks) load_idx(ks + 2);
+    }
+  } else if (lane == 0) {
+    // ---- MMA issuer
+    for (int64_t ks = 0; ks < nks; ++ks) {
+      const int s = (int)(ks % kTcRing);
+      const int64_t use = ks / kTcRing;
+      if (!tc_wait_or_abort(tc_smem(&full[s]), (uint32_t)(use & 1), abort_v)) {
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a = tc_smem(smem + s * kTcStage), bb = a + 3 * kTcA;
+      const uint64_t A1 = tc_desc(a), A2 = tc_desc(a + kTcA), A3 = tc_desc(a + 2 * kTcA);
+      const uint64_t B1 = tc_desc(bb), B2 = tc_desc(bb + kTcB), B3 = tc_desc(bb + 2 * kTcB);
+      tc_mma(tmem, A3, B1, ks > 0 ? 1u : 0u);
+      tc_mma(tmem, A2, B2, 1u);
+      tc_mma(tmem, A1, B3, 1u);
+      tc_mma(tmem, A2, B1, 1u);
+      tc_mma(tmem, A1, B2, 1u);
+      tc_mma(tmem, A1, B1, 1u);
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              tc_smem(&empty[s])));
+    }
+  }
+  // all MMAs done: the last step's commit tracks every earlier one
+  if (nks > 0 && !*abort_v) {
+    const int64_t last = nks - 1;
+    if (!tc_wait_or_abort(tc_smem(&empty[last % kTcRing]), (uint32_t)((last / kTcRing) & 1),
+                          abort_v))
+      abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool ok = !abort_flag;
+  if (ok && warp < 8)
+    tc_epilogue(tmem, warp, lane, brow0, bend, base, W, c0, packed, dv, P, Q, sh_pq);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (ok) {
+    if (live && !packed)
+      part_pq[b * R + col] = ((sh_pq[t] + sh_pq[kTcCols + t]) + sh_pq[2 * kTcCols + t]) +
+                             sh_pq[3 * kTcCols + t];
+  } else if (t == 0) {
+    atomicOr(flags, kFlagTimeout);
+    // a bounded chance for MMAs in flight to finish before the columns go
+    for (int q = 0; q < kTcRing; ++q) {
+      const int64_t uses = nks > q ? (nks - 1 - q) / kTcRing + 1 : 0;
+      if (uses > 0) tc_wait(tc_smem(&empty[q]), (uint32_t)((uses - 1) & 1));
+    }
+  }
+  __syncthreads();
+  if (warp == 8) {
     asm volatile("tcgen05.fence::after_thread_sync;");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   }
@@ -545,7 +756,10 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
   const int64_t* kb = (const int64_t*)c->tc_kbase.p;
   const int32_t* up = (const int32_t*)c->tc_upad.p;
   const uint4* im = (const uint4*)c->tc_img.p;
-  if (pf == 2)
+  if (pf == 3)
+    k_panel_spmm_tc_ws<<<grid, 288, kTcSmemWs, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
+                                                     c->d_flags);
+  else if (pf == 2)
     k_panel_spmm_tc<2><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
                                                    c->d_flags);
   else
@@ -554,9 +768,10 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
   return GM_OK;
 }
 
-// Prefetch depth of the tile product: GM_TC_PREFETCH=1|2, else the faster of
-// the two on the context's first panel product (one timed launch each; the
-// product is idempotent: Q is overwritten).
+// Variant of the tile product: 1, 2 = CTA-synchronous with gathers one or two
+// steps ahead, 3 = warp-specialised ring.  GM_TC_PREFETCH=1|2|3 pins it, else
+// the fastest on the context's first panel product (one timed launch each;
+// the product is idempotent: Q is overwritten).
 static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv, const float* P,
                          const float* PD, float* Q, double* part_pq, TcPanels pk) {
   if (c->tc_pf) return GM_OK;
@@ -564,9 +779,11 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<2>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc_ws,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemWs));
   if (const char* e = std::getenv("GM_TC_PREFETCH")) {
     const int v = std::atoi(e);
-    if (v == 1 || v == 2) {
+    if (v >= 1 && v <= 3) {
       c->tc_pf = v;
       return GM_OK;
     }
@@ -575,7 +792,7 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
   GM_CUDA_CHECK(c, cudaEventCreate(&a));
   GM_CUDA_CHECK(c, cudaEventCreate(&b));
   float best = 1e30f;
-  for (int pf : {1, 2}) {
+  for (int pf : {1, 2, 3}) {
     float ms = 0;
     GM_CUDA_CHECK(c, cudaEventRecord(a, c->stream));
     launch_tc(c, pf, grid, n, R, dv, P, PD, Q, part_pq, pk, c->stream);

@@ -23,15 +23,21 @@ def gm():
 @pytest.mark.parametrize("probe", [0.0, 2.0])
 def test_tensor_core_panel_product_matches_simt_and_fp64(gm, monkeypatch, probe):
     """The tensor-core FP32 errors against the FP64 path must be those of the
-    CUDA-core FP32 kernel (same tolerance class)."""
+    CUDA-core FP32 kernel (same tolerance class), for every variant of the
+    tile product (gathers one or two steps ahead, warp-specialised ring)."""
     cat = catalogue_subset(make_catalogue("c2_plain_20k", truth="mean"), np.arange(2500))
     res = {}
-    for name, prec, env in (("fp64", gm.PREC_FP64, None), ("tc", gm.PREC_FP32, None),
-                            ("simt", gm.PREC_FP32, "simt")):
+    runs = [("fp64", gm.PREC_FP64, None, None), ("simt", gm.PREC_FP32, "simt", None)]
+    runs += [("tc%d" % v, gm.PREC_FP32, None, str(v)) for v in (1, 2, 3)]
+    for name, prec, env, variant in runs:
         if env:
             monkeypatch.setenv("GM_SPMM", env)
         else:
             monkeypatch.delenv("GM_SPMM", raising=False)
+        if variant:
+            monkeypatch.setenv("GM_TC_PREFETCH", variant)
+        else:
+            monkeypatch.delenv("GM_TC_PREFETCH", raising=False)
         cfg = gm.config_from_catalogue(cat, precision=prec, probe_factor=probe,
                                        cg_tol=1e-10 if prec == gm.PREC_FP64 else 1e-6)
         with gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"]) as ctx:
@@ -41,13 +47,18 @@ def test_tensor_core_panel_product_matches_simt_and_fp64(gm, monkeypatch, probe)
             mu, var = ctx.get_posterior()
             res[name] = (mu, var, ctx.kernel_times())
     monkeypatch.delenv("GM_SPMM", raising=False)
-    assert "k_panel_spmm_tc" in res["tc"][2] and "k_panel_spmm_tiled" not in res["tc"][2]
+    monkeypatch.delenv("GM_TC_PREFETCH", raising=False)
     assert "k_panel_spmm_tiled" in res["simt"][2]
     mu64, v64 = res["fp64"][0], res["fp64"][1]
     err = {k: (np.abs(res[k][0] - mu64).max(), np.max(np.abs(res[k][1] - v64) / v64))
-           for k in ("tc", "simt")}
-    print("FP32 vs FP64 after 3 sweeps (mean, var rel): tensor cores %.2e %.2e, "
-          "CUDA cores %.2e %.2e" % (err["tc"] + err["simt"]))
-    for k in (0, 1):
-        assert err["tc"][k] <= 3 * err["simt"][k] + 1e-6
-    assert err["tc"][0] < 1e-3 and err["tc"][1] < 1e-2
+           for k in ("tc1", "tc2", "tc3", "simt")}
+    for v in ("tc1", "tc2", "tc3"):
+        assert "k_panel_spmm_tc" in res[v][2] and "k_panel_spmm_tiled" not in res[v][2]
+        print("FP32 vs FP64 after 3 sweeps (mean, var rel): tensor cores (%s) %.2e %.2e, "
+              "CUDA cores %.2e %.2e" % ((v,) + err[v] + err["simt"]))
+        for k in (0, 1):
+            assert err[v][k] <= 3 * err["simt"][k] + 1e-6
+        assert err[v][0] < 1e-3 and err[v][1] < 1e-2
+    # the variants compute the same products in the same order: equal results
+    for v in ("tc2", "tc3"):
+        assert np.array_equal(res[v][0], res["tc1"][0]) and np.array_equal(res[v][1], res["tc1"][1])
