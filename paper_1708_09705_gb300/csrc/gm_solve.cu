@@ -657,116 +657,6 @@ __global__ void __launch_bounds__(kBT) k_panel_update2(int64_t n, int R, const T
   }
 }
 
-// FP32 panels, four columns per lane (float4): a warp moves 512 contiguous
-// bytes of a panel row per access.  Same arithmetic and summation order per
-// column as k_panel_update1 / k_panel_update2.  R is a multiple of 32, so a
-// float4 of columns is either wholly inside the panel or wholly outside.
-__global__ void __launch_bounds__(kBT) k_panel_update1_v4(int64_t n, int R,
-                                                          const float* __restrict__ minv,
-                                                          const double* __restrict__ scal,
-                                                          float* __restrict__ X,
-                                                          float* __restrict__ Rr,
-                                                          const float* __restrict__ P,
-                                                          const float* __restrict__ Q,
-                                                          double* __restrict__ part_rz,
-                                                          double* __restrict__ part_rr) {
-  __shared__ double sh_a[8][128], sh_b[8][128];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int c = blockIdx.y * 128 + 4 * lane;
-  const bool in = c < R;
-  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  float a[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) a[q] = in ? (float)scal[c + q] : 0.f;
-  double rz[4] = {0, 0, 0, 0}, rr[4] = {0, 0, 0, 0};
-  if (in) {
-    for (int64_t i = w; i < n; i += nw) {
-      const int64_t k = i * R + c;
-      float4 x = *reinterpret_cast<float4*>(X + k);
-      const float4 p = *reinterpret_cast<const float4*>(P + k);
-      float4 r = *reinterpret_cast<float4*>(Rr + k);
-      const float4 q = *reinterpret_cast<const float4*>(Q + k);
-      const float m = minv[i];
-      x.x += a[0] * p.x;
-      x.y += a[1] * p.y;
-      x.z += a[2] * p.z;
-      x.w += a[3] * p.w;
-      r.x = r.x - a[0] * q.x;
-      r.y = r.y - a[1] * q.y;
-      r.z = r.z - a[2] * q.z;
-      r.w = r.w - a[3] * q.w;
-      *reinterpret_cast<float4*>(X + k) = x;
-      *reinterpret_cast<float4*>(Rr + k) = r;
-      const float rv[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        rz[u] += (double)rv[u] * (double)(m * rv[u]);
-        rr[u] += (double)rv[u] * (double)rv[u];
-      }
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    sh_a[wib][4 * lane + u] = rz[u];
-    sh_b[wib][4 * lane + u] = rr[u];
-  }
-  __syncthreads();
-  if (threadIdx.x < 128) {
-    const int cc = blockIdx.y * 128 + threadIdx.x;
-    if (cc < R) {
-      double s1 = 0, s2 = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        s1 += sh_a[k][threadIdx.x];
-        s2 += sh_b[k][threadIdx.x];
-      }
-      part_rz[(int64_t)blockIdx.x * R + cc] = s1;
-      part_rr[(int64_t)blockIdx.x * R + cc] = s2;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kBT) k_panel_update2_v4(int64_t n, int R,
-                                                          const float* __restrict__ minv,
-                                                          const float* __restrict__ dv,
-                                                          const double* __restrict__ scal,
-                                                          const int* __restrict__ active,
-                                                          const float* __restrict__ Rr,
-                                                          float* __restrict__ P,
-                                                          float* __restrict__ PD) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int c = blockIdx.y * 128 + 4 * lane;
-  if (c >= R) return;
-  // frozen columns keep P (never read with alpha != 0)
-  const bool act[4] = {active[c] != 0, active[c + 1] != 0, active[c + 2] != 0,
-                       active[c + 3] != 0};
-  if (!act[0] && !act[1] && !act[2] && !act[3]) return;
-  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  float be[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) be[q] = (float)scal[R + c + q];
-  for (int64_t i = w; i < n; i += nw) {
-    const int64_t k = i * R + c;
-    const float4 r = *reinterpret_cast<const float4*>(Rr + k);
-    float4 p = *reinterpret_cast<float4*>(P + k);
-    const float m = minv[i], d = dv[i];
-    const float4 pn = make_float4(m * r.x + be[0] * p.x, m * r.y + be[1] * p.y,
-                                  m * r.z + be[2] * p.z, m * r.w + be[3] * p.w);
-    p.x = act[0] ? pn.x : p.x;
-    p.y = act[1] ? pn.y : p.y;
-    p.z = act[2] ? pn.z : p.z;
-    p.w = act[3] ? pn.w : p.w;
-    *reinterpret_cast<float4*>(P + k) = p;
-    float4 pd = *reinterpret_cast<float4*>(PD + k);
-    pd.x = act[0] ? d * p.x : pd.x;
-    pd.y = act[1] ? d * p.y : pd.y;
-    pd.z = act[2] ? d * p.z : pd.z;
-    pd.w = act[3] ? d * p.w : pd.w;
-    *reinterpret_cast<float4*>(PD + k) = pd;
-  }
-}
-
 // Sigma_rr from the solution column: k_rr - v_r^T y (v_r = d o k_r) or
 // (1 - y_r) / tau_r for unit right-hand sides.
 template <typename TA, typename TV>
@@ -1062,7 +952,6 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   const int max_it = c->cfg.cg_max_iter;
   int* hn = (int*)c->h_pinned;
   dim3 grid(nbx, (unsigned)(R / 32));
-  dim3 grid4(nbx, (unsigned)ceil_div(R, 128));  // FP32 element-wise kernels, float4 columns
   const int rb = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 16 * sms);
   const int redb = (int)ceil_div(R, 256);
   int64_t total_it = 0;
@@ -1118,12 +1007,7 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
                                            scal, active, n_active, c->d_flags);
       GM_LAUNCH_CHECK(c);
       GM_PROF(c, "k_panel_update1");
-      if (sizeof(TV) == 4)
-        k_panel_update1_v4<<<grid4, kBT, 0, st>>>(n, (int)R, (const float*)minv, scal, (float*)X,
-                                                  (float*)Rr, (const float*)P, (const float*)Q,
-                                                  pa, pb);
-      else
-        k_panel_update1<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, scal, X, Rr, P, Q, pa, pb);
+      k_panel_update1<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, scal, X, Rr, P, Q, pa, pb);
       GM_LAUNCH_CHECK(c);
       GM_CUDA_CHECK(c, cudaMemsetAsync(n_active, 0, sizeof(int), st));
       GM_PROF(c, "k_panel_reduce");
@@ -1131,12 +1015,7 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
                                            active, n_active, c->d_flags);
       GM_LAUNCH_CHECK(c);
       GM_PROF(c, "k_panel_update2");
-      if (sizeof(TV) == 4)
-        k_panel_update2_v4<<<grid4, kBT, 0, st>>>(n, (int)R, (const float*)minv,
-                                                  (const float*)dv, scal, active,
-                                                  (const float*)Rr, (float*)P, (float*)PD);
-      else
-        k_panel_update2<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, scal, active, Rr, P, PD);
+      k_panel_update2<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, scal, active, Rr, P, PD);
       GM_LAUNCH_CHECK(c);
       if (it % check == 0 || it == max_it) {
         GM_CUDA_CHECK(c, cudaMemcpyAsync(hn, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
