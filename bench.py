@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--probe", type=float, default=2.0,
                    help="probed variances: colour classes at least this many cutoffs apart "
                         "share one solve (0 = exact, one solve per star)")
+    p.add_argument("--deflate", type=int, default=64, choices=[0, 64],
+                   help="deflation vectors of the FP32 variance preconditioner (0 = Jacobi)")
     p.add_argument("--no-exact", action="store_true",
                    help="skip the one-step exact-variance comparison")
     p.add_argument("--workload", default="c2", choices=["c2", "c4_fields"],
@@ -248,6 +250,8 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
     forms = [("plain_fp64", dict(precision=gm.PREC_FP64, cg_tol=1e-10)),
              ("plain_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6)),
              ("probed_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6, probe_factor=2.0)),
+             ("probed_deflated_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
+                                           probe_factor=2.0, deflate=64)),
              ("learned_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
                                    cov_source=gm.COV_SURROGATE))]
     for name, kw in forms:
@@ -364,7 +368,7 @@ def run_gpu(a):
     cat = make_catalogue(WORKLOAD, n=a.n, seed=rank)
     n = len(cat["s"])
     prec = gm.PREC_FP32 if a.precision == "fp32" else gm.PREC_FP64
-    cfg = gm.config_from_catalogue(cat, precision=prec, probe_factor=a.probe,
+    cfg = gm.config_from_catalogue(cat, precision=prec, probe_factor=a.probe, deflate=a.deflate,
                                    cg_tol=1e-6 if a.precision == "fp32" else 1e-10)
     D = {k: torch.tensor(cat[k], dtype=torch.float64, device=dev)
          for k in ("l", "b", "s", "A_obs", "A_sigma")}
@@ -431,7 +435,7 @@ def run_gpu(a):
     exact = None
     if a.probe > 0 and not a.no_exact:
         cfg_x = gm.config_from_catalogue(cat, precision=prec, probe_factor=0.0,
-                                         cg_tol=cfg.cg_tol)
+                                         deflate=a.deflate, cg_tol=cfg.cg_tol)
         mu_x = torch.empty_like(mu)
         var_x = torch.empty_like(var)
         with gm.ep_init(cfg_x, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"]) as cx:
@@ -514,6 +518,9 @@ def run_gpu(a):
                                         f"{st['probe_colours']} classes for {n} stars; error vs "
                                         f"exact in exact_variances" if a.probe > 0
                                         else "exact: one solve per star"),
+                          "preconditioner": ("Jacobi + spectral deflation with 64 Ritz vectors "
+                                             "of the scaled B (per refresh)" if a.deflate
+                                             and a.precision == "fp32" else "Jacobi"),
                           "l2": "inputs (CSR + panels) larger than L2; 256 MiB write between steps",
                           "parallelism": f"replicas x{ws}"},
                "pairs_per_s": pairs_per_s, "cov_ms": 1e3 * t_cov,

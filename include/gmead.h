@@ -94,7 +94,11 @@ typedef struct {
                              cg_tol; resume from saved sites is then equal
                              within cg_tol, not bit for bit); 0: cold start   */
   int32_t cov_source;     /* GM_COV_QUADRATURE or GM_COV_SURROGATE            */
-  int32_t reserved;
+  int32_t deflate;        /* 0 or 64: deflation vectors of the FP32 variance
+                             panels' preconditioner (spectral preconditioner
+                             from 64 Ritz vectors of the Jacobi-scaled B,
+                             refreshed per posterior update; single-field
+                             FP32 contexts, ignored otherwise)              */
   double surrogate_gate;  /* surrogate entries whose estimated absolute error
                              after the taper, W K |y - y_true|, exceeds this
                              are recomputed by quadrature (default 1e-4)      */

@@ -268,6 +268,7 @@ static gm_status validate(const gm_config* f) {
   if (f->cov_source != GM_COV_QUADRATURE && f->cov_source != GM_COV_SURROGATE) return GM_E_INVAL;
   if (!(f->surrogate_gate > 0)) return GM_E_INVAL;
   if (!(f->probe_factor >= 0) || !std::isfinite(f->probe_factor)) return GM_E_INVAL;
+  if (f->deflate != 0 && f->deflate != 64) return GM_E_INVAL;
   return GM_OK;
 }
 
@@ -799,6 +800,7 @@ void gm_destroy(gm_ctx* c) {
   for (auto e : c->prof_pool) cudaEventDestroy(e);
   c->prof_pool.clear();
   workspace_free(c);
+  deflate_free(c);
   for (auto& b : c->owned) {
     if (c->has_alloc)
       c->alloc.free(b.p, b.bytes, (void*)c->stream, c->alloc.user);

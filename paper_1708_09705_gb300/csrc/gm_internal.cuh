@@ -47,6 +47,7 @@ struct Buffer {
 };
 
 struct Workspace;  // solver scratch, see gm_solve.cu
+struct Deflation;  // deflation vectors of the variance panels, see gm_deflate.cu
 struct PackState;  // packed multi-field panels, see gm_fields.cu
 
 // Per-field cell grid and hyperparameters.  A context holds one field per
@@ -161,6 +162,7 @@ struct gm_ctx {
   void* h_pinned = nullptr;    // 64 KB pinned host scratch
 
   gm::Workspace* ws = nullptr;
+  gm::Deflation* defl = nullptr;
   gm::PackState* pack = nullptr;
 
   // ---- optional per-kernel timing (CUDA events on the context stream, or
@@ -286,6 +288,22 @@ gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
                                const int64_t* blk_base, const int32_t* blk_width, const float* dv,
                                const float* P, const float* PD, float* Q, cudaStream_t st,
                                bool tune);
+
+// Q = B P for an n x R FP32 panel with PD = d o P given (the variance panels'
+// product); part: max(tile blocks, ceil(n / 8)) x R doubles of scratch.
+gm_status panel_apply_B_f32(gm_ctx* c, int R, const float* dv, const float* P, const float* PD,
+                            float* Q, double* part);
+
+// Spectral deflation of the FP32 variance-panel preconditioner (gm_deflate.cu).
+gm_status deflate_prepare(gm_ctx* c, const float* dv, const float* minv);
+bool deflate_ready(gm_ctx* c);
+// C = Y^T R for the panel residuals; corr_row[c] = sum_j w_j C_jc^2
+gm_status deflate_rhs(gm_ctx* c, int R, const float* Rr, double* corr_row);
+// P = M^-1 R + Yw C + beta P on active columns (all, beta 0 when null), PD = d o P
+gm_status deflate_update(gm_ctx* c, int R, int nbx, const float* minv, const float* dv,
+                         const double* beta, const int* active, const float* Rr, float* P,
+                         float* PD);
+void deflate_free(gm_ctx* c);
 
 // Row-block tiles of K for the FP32 variance panels (gm_tiles.cu).
 gm_status tiles_build(gm_ctx* c);

@@ -903,6 +903,16 @@ static gm_status panel_product(gm_ctx* c, int64_t n, int64_t R, int nbx, dim3 gr
   return GM_OK;
 }
 
+gm_status panel_apply_B_f32(gm_ctx* c, int R, const float* dv, const float* P, const float* PD,
+                            float* Q, double* part) {
+  const int sms = sm_count(c);
+  const int nbx = std::max(1, (int)std::min<int64_t>(ceil_div(c->n, 8),
+                                                     (int64_t)(4 * sms * 32 / (R / 32 + 1)) + 1));
+  dim3 grid(nbx, (unsigned)(R / 32));
+  int nbu = nbx;
+  return panel_product<float, float>(c, c->n, R, nbx, grid, dv, P, PD, Q, part, &nbu);
+}
+
 // stars: the rows are the stars themselves (unit right-hand sides allowed,
 // and the solutions may seed the next call: warm start when the previous
 // call solved the stars in one panel of the same width).
@@ -931,10 +941,11 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   const int nbx = std::max(1, (int)std::min<int64_t>(ceil_div(n, 8), (int64_t)(4 * sms * 32 / (R / 32 + 1)) + 1));
   const size_t pbytes = (size_t)n * R * sizeof(TV);
   // partial rows: the panel product may write more rows (one per 128-row tile)
-  const int64_t npa = std::max<int64_t>(nbx, sizeof(TV) == 4 ? c->tc_nblk : 0);
+  // (+1: a row for the deflation term of r^T z)
+  const int64_t npa = std::max<int64_t>(nbx + 1, sizeof(TV) == 4 ? c->tc_nblk : 0);
   bool ok = ensure(c, ws.P_X, pbytes) && ensure(c, ws.P_R, pbytes) && ensure(c, ws.P_P, pbytes) &&
             ensure(c, ws.P_PD, pbytes) && ensure(c, ws.P_Q, pbytes) &&
-            ensure(c, ws.P_part, (size_t)(npa + nbx) * R * sizeof(double)) &&
+            ensure(c, ws.P_part, (size_t)(npa + nbx + 1) * R * sizeof(double)) &&
             ensure(c, ws.P_scal, 6 * (size_t)R * sizeof(double)) &&
             ensure(c, ws.P_active, (size_t)(R + 32) * sizeof(int));
   if (!ok) return set_error(c, GM_E_NOMEM, "variance panels");
@@ -956,6 +967,15 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   const int redb = (int)ceil_div(R, 256);
   int64_t total_it = 0;
   const int tb = (int)std::min<int64_t>(ceil_div(n, 256), 16 * sms);
+  // spectral deflation of the preconditioner (FP32 star panels of one field)
+  bool defl = false;
+  if (stars && sizeof(TV) == 4 && c->cfg.deflate > 0 && c->n_fields == 1) {
+    gm_status ds = deflate_prepare(c, (const float*)dv, (const float*)minv);
+    if (ds != GM_OK) return ds;
+    defl = deflate_ready(c);
+  }
+  const int nbr = defl ? nbx + 1 : nbx;  // partial rows read by the rz / rr reductions
+  double* corr = pa + (size_t)nbx * R;   // the deflation row of r^T z
   for (int64_t r0 = 0; r0 < n_cols_all; r0 += R) {
     const int64_t ncols = std::min<int64_t>(R, n_cols_all - r0);
     GM_CUDA_CHECK(c, cudaMemsetAsync(Rr, 0, pbytes, st));
@@ -987,9 +1007,18 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
       k_panel_init<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, X, Rr, P, PD, pa, pb);
       GM_LAUNCH_CHECK(c);
     }
+    if (defl) {
+      // z = M_d^-1 r for the initial residuals: P, PD and the rz row
+      GM_CUDA_CHECK(c, cudaMemsetAsync(pb + (size_t)nbx * R, 0, R * sizeof(double), st));
+      gm_status ds = deflate_rhs(c, (int)R, (const float*)Rr, corr);
+      if (ds == GM_OK)
+        ds = deflate_update(c, (int)R, nbx, (const float*)minv, (const float*)dv, nullptr, nullptr,
+                            (const float*)Rr, (float*)P, (float*)PD);
+      if (ds != GM_OK) return ds;
+    }
     GM_CUDA_CHECK(c, cudaMemsetAsync(n_active, 0, sizeof(int), st));
     GM_PROF(c, "k_panel_reduce");
-    k_panel_reduce<<<redb, 256, 0, st>>>(0, nbx, (int)R, ncols, tol2, 0, max_it, pa, pb, scal,
+    k_panel_reduce<<<redb, 256, 0, st>>>(0, nbr, (int)R, ncols, tol2, 0, max_it, pa, pb, scal,
                                          active, n_active, c->d_flags);
     GM_LAUNCH_CHECK(c);
     const int check = 8;
@@ -1009,14 +1038,24 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
       GM_PROF(c, "k_panel_update1");
       k_panel_update1<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, scal, X, Rr, P, Q, pa, pb);
       GM_LAUNCH_CHECK(c);
+      if (defl) {
+        gm_status ds = deflate_rhs(c, (int)R, (const float*)Rr, corr);
+        if (ds != GM_OK) return ds;
+      }
       GM_CUDA_CHECK(c, cudaMemsetAsync(n_active, 0, sizeof(int), st));
       GM_PROF(c, "k_panel_reduce");
-      k_panel_reduce<<<redb, 256, 0, st>>>(2, nbx, (int)R, ncols, tol2, it, max_it, pa, pb, scal,
+      k_panel_reduce<<<redb, 256, 0, st>>>(2, nbr, (int)R, ncols, tol2, it, max_it, pa, pb, scal,
                                            active, n_active, c->d_flags);
       GM_LAUNCH_CHECK(c);
-      GM_PROF(c, "k_panel_update2");
-      k_panel_update2<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, scal, active, Rr, P, PD);
-      GM_LAUNCH_CHECK(c);
+      if (defl) {
+        gm_status ds = deflate_update(c, (int)R, nbx, (const float*)minv, (const float*)dv,
+                                      scal + R, active, (const float*)Rr, (float*)P, (float*)PD);
+        if (ds != GM_OK) return ds;
+      } else {
+        GM_PROF(c, "k_panel_update2");
+        k_panel_update2<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, scal, active, Rr, P, PD);
+        GM_LAUNCH_CHECK(c);
+      }
       if (it % check == 0 || it == max_it) {
         GM_CUDA_CHECK(c, cudaMemcpyAsync(hn, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
         GM_CUDA_CHECK(c, cudaStreamSynchronize(st));

@@ -50,7 +50,7 @@ class Config(C.Structure):
                 ("taper", C.c_int32), ("precision", C.c_int32), ("likelihood", C.c_int32),
                 ("cg_max_iter", C.c_int32), ("damping", C.c_double), ("vc_floor", C.c_double),
                 ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("warm_start", C.c_int32),
-                ("cov_source", C.c_int32), ("reserved", C.c_int32),
+                ("cov_source", C.c_int32), ("deflate", C.c_int32),
                 ("surrogate_gate", C.c_double), ("probe_factor", C.c_double)]
 
 

@@ -43,6 +43,7 @@ def test_status_strings_and_defaults(L):
     assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2 + 4 * 2 + 8 + 8
     assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-4
     assert cfg.probe_factor == 0.0        # exact variances unless asked
+    assert cfg.deflate == 0
 
 
 def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
@@ -56,7 +57,8 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
     assert L.gm_ep_init(C.byref(h), C.byref(cfg), 4, x, None, x, x, x, None, None) == 1
     for field, bad in (("sigma2", -1.0), ("n_nodes", 1), ("damping", 0.0), ("cg_tol", 0.0),
                        ("precision", 7), ("outer_scale_pc", float("nan")), ("warm_start", 2),
-                       ("probe_factor", -1.0), ("probe_factor", float("inf"))):
+                       ("probe_factor", -1.0), ("probe_factor", float("inf")),
+                       ("deflate", 5), ("deflate", -64)):
         c2 = gm.default_config(**{field: bad})
         assert L.gm_ep_init(C.byref(h), C.byref(c2), 4, x, x, x, x, x, None, None) == 1, field
     assert not h.value
