@@ -28,7 +28,8 @@
 namespace gm {
 
 constexpr int kDefK = 64;          // deflation vectors
-constexpr int kDefIters = 8;       // subspace-iteration steps per refresh
+constexpr int kDefIters = 8;       // subspace-iteration steps, first refresh
+constexpr int kDefItersWarm = 3;   // ... later refreshes (warm start)
 constexpr int kDefRows = 256;      // rows per block of the Y^T R kernel
 
 struct Deflation {
@@ -37,7 +38,7 @@ struct Deflation {
   Buffer V, W, Y, Yw;              // n x k FP32 (row-major)
   Buffer P, PD, Q;                 // n x k panel product buffers
   Buffer part;                     // panel-product partials
-  Buffer G;                        // k x k FP64 Gram / projection
+  Buffer G, Gp;                    // k x k FP64 Gram / projection, partials per 64 rows
   Buffer Mk;                       // k x k FP32 matrix applied on the right
   Buffer ms;                       // n: M^-1/2
   Buffer Cp, C;                    // Y^T R: partials per row block, and the sum (k x R)
@@ -92,14 +93,42 @@ __global__ void k_df_scale_out(int64_t n, const float* __restrict__ ms, const fl
     W[e] = ms[e / kDefK] * Q[e];
 }
 
-// G[a][b] = sum_i X[i][a] Z[i][b] in FP64: block per a, thread per b with a
-// fixed row order (the block's 64 threads walk the rows together).
-__global__ void k_df_gram(int64_t n, const float* __restrict__ X, const float* __restrict__ Z,
-                          double* __restrict__ G) {
-  const int a = blockIdx.x, b = threadIdx.x;
+// Gp[rb][a][b] = sum over 64-row block rb of X[i][a] Z[i][b] (FP64); thread
+// tile 16 entries; the 64 x 64 row blocks of X and Z staged in shared memory.
+__global__ void __launch_bounds__(256) k_df_gram(int64_t n, const float* __restrict__ X,
+                                                 const float* __restrict__ Z,
+                                                 double* __restrict__ Gp) {
+  __shared__ float xs[64][kDefK], zs[64][kDefK];
+  const int t = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  for (int e = t; e < 64 * kDefK; e += 256) {
+    const int r = e / kDefK, k = e - r * kDefK;
+    const bool in = r0 + r < n;
+    xs[r][k] = in ? X[(r0 + r) * kDefK + k] : 0.f;
+    zs[r][k] = in ? Z[(r0 + r) * kDefK + k] : 0.f;
+  }
+  __syncthreads();
+  const int a = t >> 2, b0 = 16 * (t & 3);
+  double acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int r = 0; r < 64; ++r) {
+    const double xa = xs[r][a];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = fma(xa, (double)zs[r][b0 + q], acc[q]);
+  }
+  double* out = Gp + (int64_t)blockIdx.x * kDefK * kDefK + a * kDefK + b0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) out[q] = acc[q];
+}
+
+// G = sum over row blocks of Gp (fixed order)
+__global__ void k_df_gram_sum(int nb, const double* __restrict__ Gp, double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kDefK * kDefK) return;
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += (double)X[i * kDefK + a] * (double)Z[i * kDefK + b];
-  G[a * kDefK + b] = s;
+  for (int q = 0; q < nb; ++q) s += Gp[(int64_t)q * kDefK * kDefK + e];
+  G[e] = s;
 }
 
 // Out[i][:] = In[i][:] * M (k x k, row-major), row per thread group
@@ -141,64 +170,90 @@ __global__ void k_df_ms(int64_t n, const float* __restrict__ minv, float* __rest
     ms[i] = sqrtf(minv[i]);
 }
 
-// Cp[rb][j][c] = sum over the block's rows i of Y[i][j] R[i][c]; thread per
-// column c, the block's rows staged 32 at a time in shared memory.
-__global__ void __launch_bounds__(128) k_df_yt_r(int64_t n, int R, const float* __restrict__ Y,
+// Cp[rb][j][c] = sum over the block's rows i of Y[i][j] R[i][c] (split over
+// row blocks of kDefRows).  Block tile: all 64 j x 128 columns; thread tile
+// 4 j x 8 columns (register outer products), rows staged 32 at a time.
+__global__ void __launch_bounds__(256) k_df_yt_r(int64_t n, int R, const float* __restrict__ Y,
                                                  const float* __restrict__ Rr,
                                                  float* __restrict__ Cp) {
   __shared__ __align__(16) float ys[32][kDefK];
-  const int c = blockIdx.x * 128 + threadIdx.x;
+  __shared__ __align__(16) float rs[32][128];
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+  const int c0 = blockIdx.x * 128;
   const int64_t rb = blockIdx.y;
   const int64_t i0 = rb * kDefRows, i1 = min(i0 + kDefRows, n);
-  float acc[kDefK];
+  float acc[4][8];
 #pragma unroll
-  for (int j = 0; j < kDefK; ++j) acc[j] = 0.f;
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
   for (int64_t ib = i0; ib < i1; ib += 32) {
     const int cnt = (int)min((int64_t)32, i1 - ib);
     __syncthreads();
-    for (int e = threadIdx.x; e < 32 * kDefK; e += blockDim.x) {
-      const int r = e / kDefK, j = e - r * kDefK;
-      ys[r][j] = r < cnt ? Y[(ib + r) * kDefK + j] : 0.f;
+    for (int e = t; e < 32 * kDefK / 4; e += 256) {  // Y rows, float4
+      const int r = e / (kDefK / 4), q = e - r * (kDefK / 4);
+      reinterpret_cast<float4*>(ys[r])[q] =
+          r < cnt ? *reinterpret_cast<const float4*>(Y + (ib + r) * kDefK + 4 * q)
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int e = t; e < 32 * 32; e += 256) {  // R rows, 128 columns as float4
+      const int r = e >> 5, q = e & 31;
+      const int cc = c0 + 4 * q;
+      reinterpret_cast<float4*>(rs[r])[q] =
+          (r < cnt && cc < R) ? *reinterpret_cast<const float4*>(Rr + (ib + r) * R + cc)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    if (c < R) {
-      for (int r = 0; r < cnt; ++r) {
-        const float v = Rr[(ib + r) * R + c];
-        const float4* y4 = reinterpret_cast<const float4*>(ys[r]);
+    for (int r = 0; r < cnt; ++r) {
+      const float4 a = reinterpret_cast<const float4*>(ys[r])[ty];
+      const float4 b0 = reinterpret_cast<const float4*>(rs[r])[2 * tx];
+      const float4 b1 = reinterpret_cast<const float4*>(rs[r])[2 * tx + 1];
+      const float av[4] = {a.x, a.y, a.z, a.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int q = 0; q < kDefK / 4; ++q) {
-          const float4 y = y4[q];
-          acc[4 * q] = fmaf(y.x, v, acc[4 * q]);
-          acc[4 * q + 1] = fmaf(y.y, v, acc[4 * q + 1]);
-          acc[4 * q + 2] = fmaf(y.z, v, acc[4 * q + 2]);
-          acc[4 * q + 3] = fmaf(y.w, v, acc[4 * q + 3]);
-        }
-      }
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
     }
   }
-  if (c < R) {
 #pragma unroll
-    for (int j = 0; j < kDefK; ++j) Cp[(rb * kDefK + j) * R + c] = acc[j];
+  for (int u = 0; u < 4; ++u) {
+    const int j = 4 * ty + u;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int cc = c0 + 8 * tx + v;
+      if (cc < R) Cp[(rb * kDefK + j) * R + cc] = acc[u][v];
+    }
   }
 }
 
-// C[j][c] = sum_rb Cp[rb][j][c] (fixed order); corr[c] = sum_j w_j C[j][c]^2
-__global__ void k_df_sum(int R, int nrb, const float* __restrict__ Cp, const float* __restrict__ w,
-                         float* __restrict__ C, double* __restrict__ corr) {
+// C[j][c] = sum_rb Cp[rb][j][c] in row-block order; thread per (j, c)
+__global__ void k_df_sum(int R, int nrb, const float* __restrict__ Cp, float* __restrict__ C) {
+  const int64_t tot = (int64_t)kDefK * R;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int rb = 0; rb < nrb; ++rb) s += Cp[(int64_t)rb * tot + e];
+    C[e] = s;
+  }
+}
+
+// corr[c] = sum_j w_j C[j][c]^2 (FP64), thread per column
+__global__ void k_df_corr(int R, const float* __restrict__ C, const float* __restrict__ w,
+                          double* __restrict__ corr) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < R; c += gridDim.x * blockDim.x) {
     double cs = 0.0;
     for (int j = 0; j < kDefK; ++j) {
-      float s = 0.f;
-      for (int rb = 0; rb < nrb; ++rb) s += Cp[((int64_t)rb * kDefK + j) * R + c];
-      C[(int64_t)j * R + c] = s;
-      cs += (double)w[j] * (double)s * (double)s;
+      const double v = C[(int64_t)j * R + c];
+      cs += (double)w[j] * v * v;
     }
     corr[c] = cs;
   }
 }
 
-// P = M^-1 R + Yw C + beta P (columns active, or all when active is null),
-// PD = d o P.  Thread per column (its 64 C values in registers), rows strided.
+// P = M^-1 R + Yw C + beta P on active columns (all, beta 0, when active is
+// null), PD = d o P.  Block tile 64 rows x 128 columns with Yw (transposed)
+// and C staged in shared memory; thread tile 4 rows x 8 columns.
 __global__ void __launch_bounds__(256) k_df_update(int64_t n, int R, const float* __restrict__ minv,
                                                    const float* __restrict__ dv,
                                                    const double* __restrict__ beta,
@@ -207,31 +262,75 @@ __global__ void __launch_bounds__(256) k_df_update(int64_t n, int R, const float
                                                    const float* __restrict__ Yw,
                                                    const float* __restrict__ C,
                                                    float* __restrict__ P, float* __restrict__ PD) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int c = blockIdx.y * 32 + lane;
-  if (c >= R) return;
-  if (active && !active[c]) return;  // frozen column: P is never read with alpha != 0
-  const float be = beta ? (float)beta[c] : 0.f;
-  float cc[kDefK];
+  extern __shared__ __align__(16) float dsm[];
+  float* ywt = dsm;                  // [64 k][64 rows]
+  float* cs = dsm + kDefK * 64;      // [64 k][128 columns]
+  const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+  const int c0 = blockIdx.x * 128;
+  const int64_t r0 = (int64_t)blockIdx.y * 64;
+  for (int e = t; e < 64 * kDefK; e += 256) {  // Yw rows r0.., transposed
+    const int r = e / kDefK, k = e - r * kDefK;
+    ywt[k * 64 + r] = r0 + r < n ? Yw[(r0 + r) * kDefK + k] : 0.f;
+  }
+  for (int e = t; e < kDefK * 32; e += 256) {  // C, 128 columns as float4
+    const int k = e >> 5, q = e & 31;
+    const int cc = c0 + 4 * q;
+    reinterpret_cast<float4*>(cs + k * 128)[q] =
+        cc < R ? *reinterpret_cast<const float4*>(C + (int64_t)k * R + cc)
+               : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  __syncthreads();
+  float acc[4][8];
 #pragma unroll
-  for (int j = 0; j < kDefK; ++j) cc[j] = C[(int64_t)j * R + c];
-  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = w; i < n; i += nw) {
-    const float4* y4 = reinterpret_cast<const float4*>(Yw + i * kDefK);
-    float z = 0.f;
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int q = 0; q < kDefK / 4; ++q) {
-      const float4 y = __ldg(y4 + q);
-      z = fmaf(y.x, cc[4 * q], z);
-      z = fmaf(y.y, cc[4 * q + 1], z);
-      z = fmaf(y.z, cc[4 * q + 2], z);
-      z = fmaf(y.w, cc[4 * q + 3], z);
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < kDefK; ++k) {
+    const float4 a = reinterpret_cast<const float4*>(ywt + k * 64)[ty];
+    const float4 b0 = reinterpret_cast<const float4*>(cs + k * 128)[2 * tx];
+    const float4 b1 = reinterpret_cast<const float4*>(cs + k * 128)[2 * tx + 1];
+    const float av[4] = {a.x, a.y, a.z, a.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+  }
+  const int cb = c0 + 8 * tx;
+  if (cb >= R) return;
+  bool act[8];
+  float be[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    act[v] = active ? active[cb + v] != 0 : true;
+    be[v] = (beta && act[v]) ? (float)beta[cb + v] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = r0 + 4 * ty + u;
+    if (i >= n) break;
+    const float m = minv[i], d = dv[i];
+    const int64_t k0 = i * R + cb;
+    float rv[8], pv[8], dd[8];
+    *reinterpret_cast<float4*>(rv) = *reinterpret_cast<const float4*>(Rr + k0);
+    *reinterpret_cast<float4*>(rv + 4) = *reinterpret_cast<const float4*>(Rr + k0 + 4);
+    *reinterpret_cast<float4*>(pv) = *reinterpret_cast<const float4*>(P + k0);
+    *reinterpret_cast<float4*>(pv + 4) = *reinterpret_cast<const float4*>(P + k0 + 4);
+    *reinterpret_cast<float4*>(dd) = *reinterpret_cast<const float4*>(PD + k0);
+    *reinterpret_cast<float4*>(dd + 4) = *reinterpret_cast<const float4*>(PD + k0 + 4);
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      if (act[v]) {  // frozen columns keep P and PD
+        const float p = m * rv[v] + acc[u][v] + be[v] * pv[v];
+        pv[v] = p;
+        dd[v] = d * p;
+      }
     }
-    const int64_t k = i * R + c;
-    const float p = minv[i] * Rr[k] + z + be * P[k];
-    P[k] = p;
-    PD[k] = dv[i] * p;
+    *reinterpret_cast<float4*>(P + k0) = *reinterpret_cast<const float4*>(pv);
+    *reinterpret_cast<float4*>(P + k0 + 4) = *reinterpret_cast<const float4*>(pv + 4);
+    *reinterpret_cast<float4*>(PD + k0) = *reinterpret_cast<const float4*>(dd);
+    *reinterpret_cast<float4*>(PD + k0 + 4) = *reinterpret_cast<const float4*>(dd + 4);
   }
 }
 
@@ -320,8 +419,15 @@ static int eg(gm_ctx* c, int64_t work) {
 // G = X^T Z (FP64) brought to the host
 static gm_status gram(gm_ctx* c, Deflation& F, const float* X, const float* Z,
                       std::vector<double>& h) {
+  const int nb = (int)ceil_div(F.n, 64);
+  if (!ensure(c, F.Gp, (size_t)nb * kDefK * kDefK * sizeof(double)))
+    return set_error(c, GM_E_NOMEM, "deflation Gram partials");
   GM_PROF(c, "k_df_gram");
-  k_df_gram<<<kDefK, kDefK, 0, c->stream>>>(F.n, X, Z, (double*)F.G.p);
+  k_df_gram<<<nb, 256, 0, c->stream>>>(F.n, X, Z, (double*)F.Gp.p);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_df_gram_sum");
+  k_df_gram_sum<<<kDefK * kDefK / 256, 256, 0, c->stream>>>(nb, (const double*)F.Gp.p,
+                                                            (double*)F.G.p);
   GM_LAUNCH_CHECK(c);
   h.resize(kDefK * kDefK);
   GM_CUDA_CHECK(c, cudaMemcpyAsync(h.data(), F.G.p, h.size() * sizeof(double),
@@ -409,7 +515,8 @@ gm_status deflate_prepare(gm_ctx* c, const float* dv, const float* minv) {
     GM_LAUNCH_CHECK(c);
     return GM_OK;
   };
-  for (int it = 0; it < kDefIters; ++it) {
+  const int iters = F.have_v ? kDefItersWarm : kDefIters;
+  for (int it = 0; it < iters; ++it) {
     gm_status s = apply(V, Wb);
     if (s != GM_OK) return s;
     bool ok = false;
@@ -466,13 +573,16 @@ gm_status deflate_rhs(gm_ctx* c, int R, const float* Rr, double* corr_row) {
       !ensure(c, F.C, (size_t)kDefK * R * sizeof(float)))
     return set_error(c, GM_E_NOMEM, "deflation projections");
   GM_PROF(c, "k_df_yt_r");
-  k_df_yt_r<<<dim3((unsigned)ceil_div(R, 128), (unsigned)nrb), 128, 0, c->stream>>>(
+  k_df_yt_r<<<dim3((unsigned)ceil_div(R, 128), (unsigned)nrb), 256, 0, c->stream>>>(
       n, R, (const float*)F.Y.p, Rr, (float*)F.Cp.p);
   GM_LAUNCH_CHECK(c);
   GM_PROF(c, "k_df_sum");
-  k_df_sum<<<(int)ceil_div(R, 128), 128, 0, c->stream>>>(R, nrb, (const float*)F.Cp.p,
-                                                         (const float*)F.wv.p, (float*)F.C.p,
-                                                         corr_row);
+  k_df_sum<<<eg(c, (int64_t)kDefK * R), 256, 0, c->stream>>>(R, nrb, (const float*)F.Cp.p,
+                                                             (float*)F.C.p);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_df_corr");
+  k_df_corr<<<(int)ceil_div(R, 128), 128, 0, c->stream>>>(R, (const float*)F.C.p,
+                                                          (const float*)F.wv.p, corr_row);
   GM_LAUNCH_CHECK(c);
   return GM_OK;
 }
@@ -481,9 +591,12 @@ gm_status deflate_update(gm_ctx* c, int R, int nbx, const float* minv, const flo
                          const double* beta, const int* active, const float* Rr, float* P,
                          float* PD) {
   Deflation& F = D(c);
+  (void)nbx;
+  const int smem = (kDefK * 64 + kDefK * 128) * (int)sizeof(float);  // 48 KB
   GM_PROF(c, "k_df_update");
-  k_df_update<<<dim3((unsigned)nbx, (unsigned)(R / 32)), 256, 0, c->stream>>>(
-      c->n, R, minv, dv, beta, active, Rr, (const float*)F.Yw.p, (const float*)F.C.p, P, PD);
+  k_df_update<<<dim3((unsigned)ceil_div(R, 128), (unsigned)ceil_div(c->n, 64)), 256, smem,
+                c->stream>>>(c->n, R, minv, dv, beta, active, Rr, (const float*)F.Yw.p,
+                             (const float*)F.C.p, P, PD);
   GM_LAUNCH_CHECK(c);
   return GM_OK;
 }
