@@ -43,6 +43,7 @@ struct Deflation {
   Buffer ms;                       // n: M^-1/2
   Buffer Cp, C;                    // Y^T R: partials per row block, and the sum (k x R)
   Buffer wv;                       // k weights 1/theta - 1 (FP32)
+  Buffer cpart1, c1;               // single right-hand side: Y^T r partials and sum
   std::vector<double> theta;       // Ritz values of this refresh
   bool ready = false;              // Y, Yw, wv valid for this refresh
 };
@@ -334,6 +335,91 @@ __global__ void __launch_bounds__(256) k_df_update(int64_t n, int R, const float
   }
 }
 
+// ---- single right-hand side (the posterior-mean CG)
+// cpart[b][j] = sum over block b's rows of Y[i][j] r[i] (FP64); warp per row
+// (lanes j and j + 32), block partials summed over its warps in order.
+__global__ void __launch_bounds__(256) k_df1_part(int64_t n, const float* __restrict__ Y,
+                                                  const float* __restrict__ r,
+                                                  double* __restrict__ cpart) {
+  __shared__ double sh[8][kDefK];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double a0 = 0.0, a1 = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 8 + wib; i < n; i += (int64_t)gridDim.x * 8) {
+    const double ri = r[i];
+    a0 += (double)Y[i * kDefK + lane] * ri;
+    a1 += (double)Y[i * kDefK + 32 + lane] * ri;
+  }
+  sh[wib][lane] = a0;
+  sh[wib][32 + lane] = a1;
+  __syncthreads();
+  if (threadIdx.x < kDefK) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += sh[w][threadIdx.x];
+    cpart[(int64_t)blockIdx.x * kDefK + threadIdx.x] = s;
+  }
+}
+
+// c = sum_b cpart[b] (in order); rz_slot[0] += sum_j w_j c_j^2.  One block of
+// 64 threads.
+__global__ void k_df1_corr(int nb, const double* __restrict__ cpart, const float* __restrict__ w,
+                           float* __restrict__ cvec, double* __restrict__ rz_slot) {
+  __shared__ double sh[kDefK];
+  const int j = threadIdx.x;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += cpart[(int64_t)b * kDefK + j];
+  cvec[j] = (float)s;
+  sh[j] = (double)w[j] * s * s;
+  __syncthreads();
+  if (j == 0) {
+    double t = 0.0;
+    for (int q = 0; q < kDefK; ++q) t += sh[q];
+    rz_slot[0] += t;
+  }
+}
+
+// z = M^-1 r + Yw c; p = z + beta p; pd = d o p.  beta = rz_new / rz_prev from
+// the CG's per-block partial slots (each block sums them in the same order),
+// or 0 when part is null.
+__global__ void k_df1_update(int64_t n, const float* __restrict__ minv, const float* __restrict__ dv,
+                             const float* __restrict__ Yw, const float* __restrict__ cvec,
+                             const double* __restrict__ part, int G, int prev, int next,
+                             const float* __restrict__ r, float* __restrict__ p,
+                             float* __restrict__ pd) {
+  __shared__ float cs[kDefK];
+  __shared__ float sh_beta;
+  if (threadIdx.x < kDefK) cs[threadIdx.x] = cvec[threadIdx.x];
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    if (part) {
+      double rzp = 0.0, rzn = 0.0;
+      for (int k = 0; k < G; ++k) {
+        rzp += part[prev * G + k];
+        rzn += part[next * G + k];
+      }
+      b = rzp > 0 ? (float)(rzn / rzp) : 0.f;
+    }
+    sh_beta = b;
+  }
+  __syncthreads();
+  const float beta = sh_beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4* y4 = reinterpret_cast<const float4*>(Yw + i * kDefK);
+    float z = 0.f;
+#pragma unroll
+    for (int q = 0; q < kDefK / 4; ++q) {
+      const float4 y = __ldg(y4 + q);
+      z = fmaf(y.x, cs[4 * q], z);
+      z = fmaf(y.y, cs[4 * q + 1], z);
+      z = fmaf(y.z, cs[4 * q + 2], z);
+      z = fmaf(y.w, cs[4 * q + 3], z);
+    }
+    const float pi = minv[i] * r[i] + z + beta * p[i];
+    p[i] = pi;
+    pd[i] = dv[i] * pi;
+  }
+}
+
 // ---------------------------------------------------------------- host LA
 // Cholesky G = L L^T (in place, lower), FP64; false if not positive definite.
 static bool chol(std::vector<double>& G, int k) {
@@ -597,6 +683,36 @@ gm_status deflate_update(gm_ctx* c, int R, int nbx, const float* minv, const flo
   k_df_update<<<dim3((unsigned)ceil_div(R, 128), (unsigned)ceil_div(c->n, 64)), 256, smem,
                 c->stream>>>(c->n, R, minv, dv, beta, active, Rr, (const float*)F.Yw.p,
                              (const float*)F.C.p, P, PD);
+  GM_LAUNCH_CHECK(c);
+  return GM_OK;
+}
+
+// Single right-hand side: c = Y^T r, add sum_j w_j c_j^2 to rz_slot[0]
+gm_status deflate1_rhs(gm_ctx* c, const float* r, double* rz_slot) {
+  Deflation& F = D(c);
+  const int nb = 2 * sm_count(c);
+  if (!ensure(c, F.cpart1, (size_t)nb * kDefK * sizeof(double)) ||
+      !ensure(c, F.c1, kDefK * sizeof(float)))
+    return set_error(c, GM_E_NOMEM, "deflation projections");
+  GM_PROF(c, "k_df1_part");
+  k_df1_part<<<nb, 256, 0, c->stream>>>(c->n, (const float*)F.Y.p, r, (double*)F.cpart1.p);
+  GM_LAUNCH_CHECK(c);
+  GM_PROF(c, "k_df1_corr");
+  k_df1_corr<<<1, kDefK, 0, c->stream>>>(nb, (const double*)F.cpart1.p, (const float*)F.wv.p,
+                                         (float*)F.c1.p, rz_slot);
+  GM_LAUNCH_CHECK(c);
+  return GM_OK;
+}
+
+// p = M^-1 r + Yw c + beta p, pd = d o p (c from deflate1_rhs; beta from the
+// partial slots prev / next of part, or 0 when part is null)
+gm_status deflate1_update(gm_ctx* c, const float* minv, const float* dv, const double* part,
+                          int G, int prev, int next, const float* r, float* p, float* pd) {
+  Deflation& F = D(c);
+  GM_PROF(c, "k_df1_update");
+  k_df1_update<<<eg(c, c->n), 256, 0, c->stream>>>(c->n, minv, dv, (const float*)F.Yw.p,
+                                                    (const float*)F.c1.p, part, G, prev, next,
+                                                    r, p, pd);
   GM_LAUNCH_CHECK(c);
   return GM_OK;
 }

@@ -303,6 +303,11 @@ gm_status deflate_rhs(gm_ctx* c, int R, const float* Rr, double* corr_row);
 gm_status deflate_update(gm_ctx* c, int R, int nbx, const float* minv, const float* dv,
                          const double* beta, const int* active, const float* Rr, float* P,
                          float* PD);
+// Single right-hand side (posterior-mean CG): c = Y^T r, rz_slot[0] +=
+// sum_j w_j c_j^2; then p = M^-1 r + Yw c + beta p, pd = d o p.
+gm_status deflate1_rhs(gm_ctx* c, const float* r, double* rz_slot);
+gm_status deflate1_update(gm_ctx* c, const float* minv, const float* dv, const double* part,
+                          int G, int prev, int next, const float* r, float* p, float* pd);
 void deflate_free(gm_ctx* c);
 
 // Row-block tiles of K for the FP32 variance panels (gm_tiles.cu).

@@ -741,6 +741,15 @@ static gm_status cg_single(gm_ctx* c, const TV* rhs, TV* x, double tol, int max_
   GM_PROF(c, "k_cg_init");
   k_cg_init<TV><<<G, kBT, 0, st>>>(n, rhs, minv, dv, x, r, p, pd, part);
   GM_LAUNCH_CHECK(c);
+  // deflated preconditioner (FP32 contexts of one field, prepared this refresh)
+  const bool defl = sizeof(TV) == 4 && c->cfg.deflate > 0 && c->n_fields == 1 && deflate_ready(c);
+  if (defl) {
+    gm_status ds = deflate1_rhs(c, (const float*)r, part + G);  // rz slot of iteration 1
+    if (ds == GM_OK)
+      ds = deflate1_update(c, (const float*)minv, (const float*)dv, nullptr, G, 0, 0,
+                           (const float*)r, (float*)p, (float*)pd);
+    if (ds != GM_OK) return ds;
+  }
   GM_CUDA_CHECK(c, cudaMemcpyAsync(hp, part + 4 * G, G * sizeof(double), cudaMemcpyDeviceToHost, st));
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
   double bb = 0;
@@ -767,9 +776,18 @@ static gm_status cg_single(gm_ctx* c, const TV* rhs, TV* x, double tol, int max_
       if (!std::isfinite(rr)) return set_error(c, GM_E_NONFINITE, "CG residual is not finite");
       if (rr <= tol * tol * bb) break;
     }
-    GM_PROF(c, "k_cg_update2");
-    k_cg_update2<TV><<<G, kBT, 0, st>>>(n, it, minv, dv, r, p, pd, part);
-    GM_LAUNCH_CHECK(c);
+    if (defl) {
+      const int prev = (it & 1) ? 1 : 2, next = (it & 1) ? 2 : 1;
+      gm_status ds = deflate1_rhs(c, (const float*)r, part + next * G);
+      if (ds == GM_OK)
+        ds = deflate1_update(c, (const float*)minv, (const float*)dv, part, G, prev, next,
+                             (const float*)r, (float*)p, (float*)pd);
+      if (ds != GM_OK) return ds;
+    } else {
+      GM_PROF(c, "k_cg_update2");
+      k_cg_update2<TV><<<G, kBT, 0, st>>>(n, it, minv, dv, r, p, pd, part);
+      GM_LAUNCH_CHECK(c);
+    }
   }
   *iters = std::min(it, max_it);
   *rel_resid = std::sqrt(rr / bb);
@@ -968,12 +986,9 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   int64_t total_it = 0;
   const int tb = (int)std::min<int64_t>(ceil_div(n, 256), 16 * sms);
   // spectral deflation of the preconditioner (FP32 star panels of one field)
-  bool defl = false;
-  if (stars && sizeof(TV) == 4 && c->cfg.deflate > 0 && c->n_fields == 1) {
-    gm_status ds = deflate_prepare(c, (const float*)dv, (const float*)minv);
-    if (ds != GM_OK) return ds;
-    defl = deflate_ready(c);
-  }
+  // (the vectors are prepared per refresh, before the mean solve)
+  const bool defl =
+      stars && sizeof(TV) == 4 && c->cfg.deflate > 0 && c->n_fields == 1 && deflate_ready(c);
   const int nbr = defl ? nbx + 1 : nbx;  // partial rows read by the rz / rr reductions
   double* corr = pa + (size_t)nbx * R;   // the deflation row of r^T z
   for (int64_t r0 = 0; r0 < n_cols_all; r0 += R) {
@@ -1117,6 +1132,11 @@ gm_status refresh_posterior(gm_ctx* c) {
   int64_t it_m = 0, it_v = 0;
   double res_m = 0, res_v = 0;
   if (c->cfg.precision == GM_PREC_FP32) {
+    // deflation vectors for this refresh (mean CG and variance panels)
+    if (c->cfg.deflate > 0 && c->n_fields == 1) {
+      s = deflate_prepare(c, (const float*)W(c).dv.p, (const float*)W(c).minv.p);
+      if (s != GM_OK) return s;
+    }
     s = posterior_mean<float, float>(c, &it_m, &res_m);
     if (s == GM_OK && c->n_fields > 1)
       s = panels_fields(c, (const float*)W(c).dv.p, (const float*)W(c).minv.p,

@@ -1,6 +1,6 @@
-"""Spectral deflation of the FP32 variance panels' preconditioner: the same
-posterior as plain Jacobi-PCG (within the FP32 panel tolerance) in fewer CG
-iterations, exact and probed."""
+"""Spectral deflation of the FP32 preconditioner (variance panels and the
+posterior-mean CG): the same posterior as plain Jacobi-PCG (within the FP32
+panel tolerance) in fewer CG iterations, exact and probed."""
 import numpy as np
 import pytest
 
@@ -36,10 +36,14 @@ def test_deflated_panels_match_plain_in_fewer_iterations(gm, probe):
     t0, n0, m0, v0, s0 = out[0]
     t1, n1, m1, v1, s1 = out[64]
     rel = np.abs(v1 - v0) / v0
-    print("deflation (probe %g): variance CG iterations %d -> %d; var rel max %.2e, "
-          "mean %.2e" % (probe, s0["cg_iters_var"], s1["cg_iters_var"], rel.max(),
-                         np.abs(m1 - m0).max()))
+    print("deflation (probe %g): variance CG iterations %d -> %d, mean CG %d -> %d; "
+          "var rel max %.2e, mean %.2e" % (probe, s0["cg_iters_var"], s1["cg_iters_var"],
+                                           s0["cg_iters_mean"], s1["cg_iters_mean"], rel.max(),
+                                           np.abs(m1 - m0).max()))
     # both are FP32 panel solves stopped at 1e-5 relative residual
     assert rel.max() < 1e-3 and np.median(rel) < 1e-5
     assert np.abs(m1 - m0).max() < 1e-4
     assert s1["cg_iters_var"] < 0.7 * s0["cg_iters_var"]
+    assert s1["cg_iters_mean"] < 0.8 * s0["cg_iters_mean"]
+    # the refined mean solve reaches the same FP64-level residual
+    assert s1["cg_resid_mean"] < 1e-5
