@@ -265,7 +265,7 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, i
 }
 
 // Geometry of the panels.  One panel (single field): element (row, col) at
-// row * R + col, CTA (blockIdx.x = row block, blockIdx.y = column group),
+// row * R + col, CTA (blockIdx.x = column group, blockIdx.y = row block),
 // partials of P^T Q per (row block, column).  Packed fields: element (row,
 // col) of a field at base_b + row * W_b + col with base_b = P_f - row0_f W_f,
 // CTA = items[blockIdx.x] = (row block, column group of its field), no
@@ -303,8 +303,8 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
     brow0 = pk.row0[b];
     bend = pk.row0[b + 1];
   } else {
-    b = blockIdx.x;
-    c0 = blockIdx.y * kTcCols;
+    b = blockIdx.y;
+    c0 = blockIdx.x * kTcCols;
     W = R;
     base = 0;
     brow0 = b * kTcRows;
@@ -502,8 +502,8 @@ __global__ void __launch_bounds__(288, 2) k_panel_spmm_tc_ws(
     brow0 = pk.row0[b];
     bend = pk.row0[b + 1];
   } else {
-    b = blockIdx.x;
-    c0 = blockIdx.y * kTcCols;
+    b = blockIdx.y;
+    c0 = blockIdx.x * kTcCols;
     W = R;
     base = 0;
     brow0 = b * kTcRows;
@@ -812,7 +812,9 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
 
 gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const float* P,
                         const float* PD, float* Q, double* part_pq) {
-  dim3 grid((unsigned)c->tc_nblk, (unsigned)ceil_div(R, kTcCols));
+  // column groups vary fastest: the CTAs resident together share their row
+  // blocks' tile images (read from DRAM once instead of once per group)
+  dim3 grid((unsigned)ceil_div(R, kTcCols), (unsigned)c->tc_nblk);
   const TcPanels pk{nullptr, nullptr, nullptr, nullptr};
   gm_status s = tc_tune(c, grid, n, R, dv, P, PD, Q, part_pq, pk);
   if (s != GM_OK) return s;
