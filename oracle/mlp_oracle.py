@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY -- the CUDA library never imports or runs this file.
 
 The paper computes every covariance entry from the sightline integral
 (Sect. 3); the surrogate is this project's approximation of that integral,
-trained on the quadrature and judged by it.  Network: 5 inputs -> 3 hidden
+trained on the quadrature and checked against it.  Network: 5 inputs -> 3 hidden
 layers of 64 units with SiLU -> 2 outputs (the prediction y and a log error
 estimate e).  Inputs are the scale-free geometry of the pair in units of L0:
     f1 = ln(sqrt(s_i s_j)/L0) / 4          (mean distance),

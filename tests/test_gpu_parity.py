@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances (derived in the design doc):
+Tolerances, derived from the arithmetic:
   FP64 mode: covariance entries 1e-9 relative (cubic-table interpolation of
   the log-density kernel, < 2e-12 of g(0)); posterior means/variances 1e-6
   relative (the target the method is held to).
