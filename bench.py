@@ -84,6 +84,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(vals, device):
+    """Element-wise maximum of per-rank timings over all ranks (identity
+    without a process group): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_value(units_per_rank, world_size, t_max):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (replicas: each rank runs its own problem)."""
+    return world_size * units_per_rank / t_max
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -415,11 +433,8 @@ def run_gpu(a):
     ck = clocks.stop() if clocks else None
     t_step = sum(times) / len(times) / 1e3
     t_cov = sum(covt) / len(covt) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_step, t_cov], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step, t_cov = tt.tolist()
-    value = ws * n * a.sweeps / t_step
+    t_step, t_cov = max_over_ranks([t_step, t_cov], dev)
+    value = job_value(n * a.sweeps, ws, t_step)
     pairs_per_s = ws * st["n_pairs"] / t_cov
 
     # dominant kernel and its roofline
@@ -476,12 +491,8 @@ def run_gpu(a):
             torch.cuda.synchronize()
             et.append(time.perf_counter() - t0)
             c2.close()
-        te = sum(et) / len(et)
-        if ws > 1:
-            tt = torch.tensor([te], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = tt.item()
-        e2e = {"value": ws * n * a.sweeps / te, "unit": UNIT, "h2d_bytes_per_step": 5 * n * 8,
+        te = max_over_ranks([sum(et) / len(et)], dev)[0]
+        e2e = {"value": job_value(n * a.sweeps, ws, te), "unit": UNIT, "h2d_bytes_per_step": 5 * n * 8,
                "d2h_bytes_per_step": 2 * n * 8, "ms_per_step": 1e3 * te,
                "includes": "ep_init from pinned host arrays (H2D, spatial sort), build_cov, "
                            "sweeps, posterior D2H"}
