@@ -94,11 +94,14 @@ typedef struct {
                              cg_tol; resume from saved sites is then equal
                              within cg_tol, not bit for bit); 0: cold start   */
   int32_t cov_source;     /* GM_COV_QUADRATURE or GM_COV_SURROGATE            */
-  int32_t deflate;        /* 0 or 64: deflation vectors of the FP32 variance
-                             panels' preconditioner (spectral preconditioner
-                             from 64 Ritz vectors of the Jacobi-scaled B,
-                             refreshed per posterior update; single-field
-                             FP32 contexts, ignored otherwise)              */
+  int32_t deflate;        /* 0 or 64: deflation vectors of the FP32
+                             preconditioner (variance panels and mean CG):
+                             M^-1 + Y (Theta^-1 - I) Y^T from 64 Ritz pairs of
+                             the Jacobi-scaled B, refreshed per posterior
+                             update (the paper's PCG solves, App. A.2, with a
+                             stronger preconditioner; same results within
+                             cg_tol); single-field FP32 contexts, ignored
+                             otherwise.  Other values: GM_E_INVAL          */
   double surrogate_gate;  /* surrogate entries whose estimated absolute error
                              after the taper, W K |y - y_true|, exceeds this
                              are recomputed by quadrature (default 1e-4)      */
@@ -227,8 +230,9 @@ gm_status gm_get_perm(gm_ctx* ctx, int64_t* perm_out);
 gm_status gm_get_csr(gm_ctx* ctx, int64_t* row_ptr_out, int32_t* col_out,
                      double* val_out);
 
-/* Stored covariance entries K_ij (tapered, as used by the solves) for nq
- * caller index pairs (i[q], j[q]); 0 where the pair is beyond the cutoff.
+/* Stored covariance entries K_ij of the log-extinctions (Sect. 3, tapered as
+ * used by the solves) for nq caller index pairs (i[q], j[q]); 0 where the
+ * pair is beyond the cutoff.
  * i, j: int64, host or device; out: nq doubles, host or device.
  * GM_E_INVAL for an index outside [0, n); GM_E_STATE before gm_build_cov. */
 gm_status gm_get_entries(gm_ctx* ctx, int64_t nq, const int64_t* i, const int64_t* j,
@@ -236,7 +240,9 @@ gm_status gm_get_entries(gm_ctx* ctx, int64_t nq, const int64_t* i, const int64_
 
 /* Colour class of each star (caller order, int32, length n) when probing is
  * on (probe_factor > 0, after gm_build_cov); classes are numbered from 0 per
- * field.  GM_E_STATE if no colouring exists. */
+ * field; stars closer than probe_factor x cutoff have different classes.
+ * These classes share the variance solves of the EP marginals (App. A.2,
+ * eq. cavity).  GM_E_STATE if no colouring exists. */
 gm_status gm_get_probe_colours(gm_ctx* ctx, int32_t* colour_out);
 
 gm_status gm_get_stats(gm_ctx* ctx, gm_stats* out);
