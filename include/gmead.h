@@ -210,6 +210,19 @@ gm_status gm_ep_sweep(gm_ctx* ctx, int32_t n_sweeps, double tol,
 gm_status gm_predict(gm_ctx* ctx, int64_t nq, const double* l, const double* b,
                      const double* s, double* mean_out, double* var_out);
 
+/* Extinction pseudo-density dA/ds (Sect. 5): for each query (l, b, s) the
+ * joint posterior predictive of ln A at s and at s + ds on the same sightline
+ * (Sect. 2 eq. cond_GP0), and the mean and variance of (A2 - A1) / ds under
+ * the paper's condition A2 > A1 (closed-form truncated bivariate-lognormal
+ * moments where the paper samples).  ds > 0 (pc; the paper uses 10).
+ * Outputs, host or device: mean_out 2 nq (ln A at s, at s + ds per query),
+ * cov_out 3 nq (variance at s, variance at s + ds, their covariance),
+ * dens_out 2 nq (mean, variance of the pseudo-density, mag/pc).  Single-field
+ * contexts; GM_E_INVAL for ds <= 0 or a non-positive distance. */
+gm_status gm_predict_pairs(gm_ctx* ctx, int64_t nq, const double* l, const double* b,
+                           const double* s, double ds, double* mean_out, double* cov_out,
+                           double* dens_out);
+
 /* Marginal posterior mean and variance of ln A for every star under the
  * current sites (refreshed if the sites changed).  Length n each. */
 gm_status gm_get_posterior(gm_ctx* ctx, double* mean_out, double* var_out);

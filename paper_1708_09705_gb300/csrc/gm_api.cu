@@ -703,26 +703,18 @@ gm_status gm_get_stats(gm_ctx* c, gm_stats* out) {
   return GM_OK;
 }
 
-gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, const double* s,
-                     double* mean_out, double* var_out) {
-  if (!c || nq < 0 || (nq > 0 && (!l || !b || !s || !mean_out || !var_out))) return GM_E_INVAL;
-  if (c->n_fields > 1)
-    return set_error(c, GM_E_STATE, "prediction needs a single-field context");
-  if (nq == 0) return GM_OK;
-  c->launches = 0;
-  gm_status st = ensure_posterior(c);
-  if (st != GM_OK) return st;
+// Predictive means and variances at nq device-resident points (ql, qb, qs);
+// with pair_cross, rows (2p, 2p + 1) are pairs and pair_cross[p] receives
+// v_{2p+1}^T B^-1 v_{2p}.
+static gm_status predict_points(gm_ctx* c, int64_t nq, const double* ql, const double* qb,
+                                const double* qs, double* mean, double* var,
+                                double* pair_cross) {
   const size_t nb = nq * sizeof(double);
-  // query arrays: l, b, s, ux, uy, uz, kss, mq, mean, var
-  double* q = (double*)dev_alloc(c, 10 * nb);
+  // query work arrays: ux, uy, uz, kss, mq
+  double* q = (double*)dev_alloc(c, 5 * nb);
   int64_t* qptr = (int64_t*)dev_alloc(c, (nq + 1) * sizeof(int64_t));
   if (!q || !qptr) return set_error(c, GM_E_NOMEM, "query arrays");
-  double *ql = q, *qb = q + nq, *qs = q + 2 * nq, *ux = q + 3 * nq, *uy = q + 4 * nq,
-         *uz = q + 5 * nq, *kss = q + 6 * nq, *mq = q + 7 * nq, *mean = q + 8 * nq,
-         *var = q + 9 * nq;
-  if ((st = copy_in(c, ql, l, nb)) != GM_OK || (st = copy_in(c, qb, b, nb)) != GM_OK ||
-      (st = copy_in(c, qs, s, nb)) != GM_OK)
-    return st;
+  double *ux = q, *uy = q + nq, *uz = q + 2 * nq, *kss = q + 3 * nq, *mq = q + 4 * nq;
   GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned), c->stream));
   GM_PROF(c, "k_check_inputs");
   k_check_inputs<<<eb(c, nq), 256, 0, c->stream>>>(nq, qs, qs, qs, ql, qb, c->d_flags + 1);
@@ -733,7 +725,7 @@ gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, co
     GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
     if (*h) return set_error(c, GM_E_INVAL, "query distances must be finite and > 0");
   }
-  st = unit_vectors(c, nq, ql, qb, ux, uy, uz);
+  gm_status st = unit_vectors(c, nq, ql, qb, ux, uy, uz);
   if (st != GM_OK) return st;
   Buffer qcol;
   int64_t qnnz = 0;
@@ -757,15 +749,153 @@ gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, co
   int64_t it = 0;
   double res = 0;
   c->warm_R = 0;  // the query panels overwrite the saved star solutions
-  st = panel_variances(c, nq, qptr, (const int32_t*)qcol.p, qval, kss, var, &it, &res);
+  st = panel_variances(c, nq, qptr, (const int32_t*)qcol.p, qval, kss, var, &it, &res,
+                       pair_cross);
   if (st == GM_OK) st = read_flags(c);
   if (st != GM_OK) return st;
-  if ((st = copy_out(c, mean_out, mean, nb)) != GM_OK) return st;
-  if ((st = copy_out(c, var_out, var, nb)) != GM_OK) return st;
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
   dev_free_now(c, qval, std::max<int64_t>(qnnz, 1) * vs);
   dev_free_now(c, qcol.p, qcol.bytes);
   dev_free_now(c, qptr, (nq + 1) * sizeof(int64_t));
-  dev_free_now(c, q, 10 * nb);
+  dev_free_now(c, q, 5 * nb);
+  return GM_OK;
+}
+
+gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, const double* s,
+                     double* mean_out, double* var_out) {
+  if (!c || nq < 0 || (nq > 0 && (!l || !b || !s || !mean_out || !var_out))) return GM_E_INVAL;
+  if (c->n_fields > 1)
+    return set_error(c, GM_E_STATE, "prediction needs a single-field context");
+  if (nq == 0) return GM_OK;
+  c->launches = 0;
+  gm_status st = ensure_posterior(c);
+  if (st != GM_OK) return st;
+  const size_t nb = nq * sizeof(double);
+  double* q = (double*)dev_alloc(c, 5 * nb);  // l, b, s, mean, var
+  if (!q) return set_error(c, GM_E_NOMEM, "query arrays");
+  double *ql = q, *qb = q + nq, *qs = q + 2 * nq, *mean = q + 3 * nq, *var = q + 4 * nq;
+  if ((st = copy_in(c, ql, l, nb)) != GM_OK || (st = copy_in(c, qb, b, nb)) != GM_OK ||
+      (st = copy_in(c, qs, s, nb)) != GM_OK)
+    return st;
+  st = predict_points(c, nq, ql, qb, qs, mean, var, nullptr);
+  if (st != GM_OK) return st;
+  if ((st = copy_out(c, mean_out, mean, nb)) != GM_OK) return st;
+  if ((st = copy_out(c, var_out, var, nb)) != GM_OK) return st;
+  dev_free_now(c, q, 5 * nb);
+  c->stats.kernel_launches = c->launches;
+  return GM_OK;
+}
+
+// Pair points: (l, b, s) at row 2q, (l, b, s + ds) at row 2q + 1; and the
+// pair's own quadrature inputs (s, s + ds, chord 0).
+__global__ void k_pair_points(int64_t nq, double ds, const double* __restrict__ l,
+                              const double* __restrict__ b, const double* __restrict__ s,
+                              double* __restrict__ l2, double* __restrict__ b2,
+                              double* __restrict__ s2, double* __restrict__ si,
+                              double* __restrict__ sj, double* __restrict__ ch) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    l2[2 * q] = l2[2 * q + 1] = l[q];
+    b2[2 * q] = b2[2 * q + 1] = b[q];
+    s2[2 * q] = s[q];
+    s2[2 * q + 1] = s[q] + ds;
+    si[q] = s[q];
+    sj[q] = s[q] + ds;
+    ch[q] = 0.0;
+  }
+}
+
+// E[exp(c^T a) 1{d^T a > 0}] for a ~ N(mu, S), 2-vectors (completing the square)
+__device__ __forceinline__ double trunc_exp(double m1, double m2, double s11, double s22,
+                                            double s12, double c1, double c2) {
+  const double mx = c1 * m1 + c2 * m2;
+  const double vx = c1 * c1 * s11 + 2.0 * c1 * c2 * s12 + c2 * c2 * s22;
+  const double md = m2 - m1;
+  const double vd = s11 + s22 - 2.0 * s12;
+  const double cxd = (c2 - c1) * s12 + c2 * s22 - c1 * s11;  // Cov(c^T a, a2 - a1)
+  return exp(mx + 0.5 * vx) * normcdf((md + cxd) / sqrt(vd));
+}
+
+// Joint 2 x 2 posterior of each pair and the pseudo-density moments of
+// (A2 - A1) / ds given A2 > A1 (Sect. 5): mean_out[2q..], cov_out[3q..]
+// (var near, var far, cov), dens_out[2q..] (mean, variance).
+__global__ void k_pair_density(int64_t nq, double ds, double inv_cut, int taper,
+                               const double* __restrict__ mean, const double* __restrict__ var,
+                               const double* __restrict__ cross, const double* __restrict__ k12u,
+                               double* __restrict__ cov_out, double* __restrict__ dens_out,
+                               unsigned* __restrict__ flags) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const double h = ds * inv_cut;
+    double w = h <= 1.0 ? 1.0 : 0.0;
+    if (taper == GM_TAPER_WENDLAND) {
+      const double u = 1.0 - h;
+      w = h < 1.0 ? u * u * u * u * (4.0 * h + 1.0) : 0.0;
+    }
+    const double m1 = mean[2 * q], m2 = mean[2 * q + 1];
+    const double s11 = var[2 * q], s22 = var[2 * q + 1];
+    const double s12 = w * k12u[q] - cross[q];
+    cov_out[3 * q] = s11;
+    cov_out[3 * q + 1] = s22;
+    cov_out[3 * q + 2] = s12;
+    const double vd = s11 + s22 - 2.0 * s12;
+    double dm = NAN, dv = NAN;
+    if (vd > 0) {
+      const double pd = normcdf((m2 - m1) / sqrt(vd));
+      const double e1 = trunc_exp(m1, m2, s11, s22, s12, 1.0, 0.0);
+      const double e2 = trunc_exp(m1, m2, s11, s22, s12, 0.0, 1.0);
+      const double e11 = trunc_exp(m1, m2, s11, s22, s12, 2.0, 0.0);
+      const double e22 = trunc_exp(m1, m2, s11, s22, s12, 0.0, 2.0);
+      const double e12 = trunc_exp(m1, m2, s11, s22, s12, 1.0, 1.0);
+      const double mo1 = (e2 - e1) / pd, mo2 = (e22 - 2.0 * e12 + e11) / pd;
+      dm = mo1 / ds;
+      dv = (mo2 - mo1 * mo1) / (ds * ds);
+    }
+    if (!isfinite(dm) || !isfinite(dv)) atomicOr(flags, kFlagNonFinite);
+    dens_out[2 * q] = dm;
+    dens_out[2 * q + 1] = dv;
+  }
+}
+
+gm_status gm_predict_pairs(gm_ctx* c, int64_t nq, const double* l, const double* b,
+                           const double* s, double ds, double* mean_out, double* cov_out,
+                           double* dens_out) {
+  if (!c || nq < 0 || !(ds > 0) || !std::isfinite(ds) ||
+      (nq > 0 && (!l || !b || !s || !mean_out || !cov_out || !dens_out)))
+    return GM_E_INVAL;
+  if (c->n_fields > 1)
+    return set_error(c, GM_E_STATE, "prediction needs a single-field context");
+  if (nq == 0) return GM_OK;
+  c->launches = 0;
+  gm_status st = ensure_posterior(c);
+  if (st != GM_OK) return st;
+  const size_t nb = nq * sizeof(double);
+  // l, b, s (nq); l2, b2, s2, mean, var (2 nq); si, sj, ch, k12, cross (nq);
+  // cov (3 nq), dens (2 nq)
+  double* q = (double*)dev_alloc(c, 23 * nb);
+  if (!q) return set_error(c, GM_E_NOMEM, "pair arrays");
+  double *ql = q, *qb = q + nq, *qs = q + 2 * nq, *l2 = q + 3 * nq, *b2 = q + 5 * nq,
+         *s2 = q + 7 * nq, *mean = q + 9 * nq, *var = q + 11 * nq, *si = q + 13 * nq,
+         *sj = q + 14 * nq, *ch = q + 15 * nq, *k12 = q + 16 * nq, *cross = q + 17 * nq,
+         *cov = q + 18 * nq, *dens = q + 21 * nq;
+  if ((st = copy_in(c, ql, l, nb)) != GM_OK || (st = copy_in(c, qb, b, nb)) != GM_OK ||
+      (st = copy_in(c, qs, s, nb)) != GM_OK)
+    return st;
+  GM_PROF(c, "k_pair_points");
+  k_pair_points<<<eb(c, nq), 256, 0, c->stream>>>(nq, ds, ql, qb, qs, l2, b2, s2, si, sj, ch);
+  GM_LAUNCH_CHECK(c);
+  st = predict_points(c, 2 * nq, l2, b2, s2, mean, var, cross);
+  if (st == GM_OK) st = pairlist_quadrature(c, nq, si, sj, ch, k12);
+  if (st != GM_OK) return st;
+  GM_PROF(c, "k_pair_density");
+  k_pair_density<<<eb(c, nq), 256, 0, c->stream>>>(nq, ds, 1.0 / c->cfg.cutoff_pc, c->cfg.taper,
+                                                   mean, var, cross, k12, cov, dens, c->d_flags);
+  GM_LAUNCH_CHECK(c);
+  if ((st = read_flags(c)) != GM_OK) return st;
+  if ((st = copy_out(c, mean_out, mean, 2 * nb)) != GM_OK) return st;
+  if ((st = copy_out(c, cov_out, cov, 3 * nb)) != GM_OK) return st;
+  if ((st = copy_out(c, dens_out, dens, 2 * nb)) != GM_OK) return st;
+  dev_free_now(c, q, 23 * nb);
   c->stats.kernel_launches = c->launches;
   return GM_OK;
 }

@@ -321,7 +321,8 @@ gm_status refresh_posterior(gm_ctx* c);
 // (v_r = S^1/2 k_r); used for the stars themselves and for queries.
 gm_status panel_variances(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
                           const int32_t* col, const void* val, const double* kdiag_rows,
-                          double* var_out, int64_t* iters_out, double* resid_out);
+                          double* var_out, int64_t* iters_out, double* resid_out,
+                          double* pair_cross = nullptr);
 gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const void* val, const double* alpha,
                         const double* base, double* out);

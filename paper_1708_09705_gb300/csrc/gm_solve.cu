@@ -689,6 +689,30 @@ __global__ void k_panel_final(int64_t r0, int64_t n_cols, int R, const int64_t* 
   }
 }
 
+// Query pairs interleaved as rows (2p, 2p + 1) of a query panel: the cross
+// term v_{2p+1}^T B^-1 v_{2p} from the solution column of row 2p and the
+// stored entries of row 2p + 1 (both rows sit in the same panel group).
+template <typename TA, typename TV>
+__global__ void k_panel_pair_cross(int64_t r0, int64_t n_cols, int R,
+                                   const int64_t* __restrict__ row_ptr,
+                                   const int32_t* __restrict__ col, const TA* __restrict__ val,
+                                   const double* __restrict__ d64, const TV* __restrict__ X,
+                                   double* __restrict__ cross) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t cn = 2 * warp; cn + 1 < n_cols; cn += 2 * nw) {
+    const int64_t rf = r0 + cn + 1;  // far row; near column cn
+    double acc = 0;
+    for (int64_t e = row_ptr[rf] + lane; e < row_ptr[rf + 1]; e += 32) {
+      const int32_t j = col[e];
+      acc += d64[j] * (double)val[e] * (double)X[(int64_t)j * R + cn];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) cross[(r0 + cn) / 2] = acc;
+  }
+}
+
 // Probed variances: star r reads its estimate from the column of its colour
 // class (when that class is in this panel).
 template <typename TA, typename TV>
@@ -937,7 +961,8 @@ gm_status panel_apply_B_f32(gm_ctx* c, int R, const float* dv, const float* P, c
 template <typename TA, typename TV>
 static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                         const void* val, const double* kdiag_rows, double* var_out,
-                        int64_t* iters_out, double* resid_out, bool stars) {
+                        int64_t* iters_out, double* resid_out, bool stars,
+                        double* pair_cross = nullptr) {
   const bool warm = stars;
   // probed variances: one column per colour class instead of one per star
   const bool probe = stars && c->probe_colour && c->probe_factor_done > 0 && c->n_fields == 1;
@@ -1091,6 +1116,13 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
                                                 warm ? c->tau : nullptr, var_out, c->d_flags);
     }
     GM_LAUNCH_CHECK(c);
+    if (pair_cross && !probe) {  // R is even: a pair's rows share the group
+      GM_PROF(c, "k_panel_pair_cross");
+      k_panel_pair_cross<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col,
+                                                     (const TA*)val, (const double*)ws.d64.p, X,
+                                                     pair_cross);
+      GM_LAUNCH_CHECK(c);
+    }
   }
   // worst relative residual over the last panel's columns
   std::vector<double> h(2 * R);
@@ -1161,14 +1193,14 @@ gm_status refresh_posterior(gm_ctx* c) {
 
 gm_status panel_variances(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                           const void* val, const double* kdiag_rows, double* var_out,
-                          int64_t* iters_out, double* resid_out) {
+                          int64_t* iters_out, double* resid_out, double* pair_cross) {
   gm_status s = prepare_precond(c);
   if (s != GM_OK) return s;
   if (c->cfg.precision == GM_PREC_FP32)
     return panels<float, float>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out,
-                                resid_out, false);
+                                resid_out, false, pair_cross);
   return panels<double, double>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out,
-                                resid_out, false);
+                                resid_out, false, pair_cross);
 }
 
 gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,

@@ -35,7 +35,7 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_destroy", "gm_profile", "gm_kernel_time_count", "gm_kernel_time",
            "gm_site_update_noalloc", "gm_surrogate_param_count", "gm_surrogate_set_params",
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
-           "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries"]
+           "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries", "gm_predict_pairs"]
 
 
 class GmError(RuntimeError):
@@ -99,6 +99,7 @@ def lib():
         L.gm_get_perm.argtypes = [vp, vp]
         L.gm_get_probe_colours.argtypes = [vp, vp]
         L.gm_get_entries.argtypes = [vp, i64, vp, vp, vp]
+        L.gm_predict_pairs.argtypes = [vp, i64, vp, vp, vp, dbl, vp, vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.gm_stream.argtypes = [vp]
@@ -128,7 +129,8 @@ def lib():
                   "gm_get_sites", "gm_set_sites", "gm_get_prior", "gm_get_perm", "gm_get_csr",
                   "gm_get_stats", "gm_profile", "gm_kernel_time", "gm_surrogate_set_params",
                   "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
-                  "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries"):
+                  "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries",
+                  "gm_predict_pairs"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -211,6 +213,17 @@ class Context:
         pv, kv = _ptr(var)
         self._check(lib().gm_predict(self._h, nq, pl, pb, ps, pm, pv))
         return mean, var
+
+    def predict_pairs(self, l, b, s, ds=10.0):
+        """Joint predictive at s and s + ds per query and the pseudo-density
+        moments: (means (nq, 2), covariances (nq, 3), density (nq, 2))."""
+        l, b, s = (np.ascontiguousarray(v, dtype=np.float64) for v in (l, b, s))
+        nq = len(s)
+        mean, cov, dens = np.empty((nq, 2)), np.empty((nq, 3)), np.empty((nq, 2))
+        self._check(lib().gm_predict_pairs(self._h, nq, l.ctypes.data, b.ctypes.data,
+                                           s.ctypes.data, float(ds), mean.ctypes.data,
+                                           cov.ctypes.data, dens.ctypes.data))
+        return mean, cov, dens
 
     # ---- state
     def _pair_out(self, fn, out):
