@@ -812,7 +812,7 @@ __device__ __forceinline__ double trunc_exp(double m1, double m2, double s11, do
   const double vx = c1 * c1 * s11 + 2.0 * c1 * c2 * s12 + c2 * c2 * s22;
   const double md = m2 - m1;
   const double vd = s11 + s22 - 2.0 * s12;
-  const double cxd = (c2 - c1) * s12 + c2 * s22 - c1 * s11;  // Cov(c^T a, a2 - a1)
+  const double cxd = (c1 - c2) * s12 + c2 * s22 - c1 * s11;  // Cov(c^T a, a2 - a1)
   return exp(mx + 0.5 * vx) * normcdf((md + cxd) / sqrt(vd));
 }
 
