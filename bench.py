@@ -71,7 +71,7 @@ def parse():
                    help="deflation vectors of the FP32 variance preconditioner (0 = Jacobi)")
     p.add_argument("--no-exact", action="store_true",
                    help="skip the one-step exact-variance comparison")
-    p.add_argument("--workload", default="c2", choices=["c2", "c4_fields"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4_fields"],
                    help="c2: the 20,000-star field (bench line); c4_fields: 256 independent "
                         "fields solved together (batched path)")
     return p.parse_args()
@@ -548,6 +548,17 @@ def run_gpu(a):
 
 def main():
     a = parse()
+    if a.workload == "c3":
+        # the 200,000-star field (10 x 10 deg, outer scale 10 pc): the same
+        # step as the 20k bench; no exact-variance, forms or CPU legs (each
+        # exact refresh needs ~26k x 200k right-hand-side panels)
+        global WORKLOAD, WORKLOAD_DESC
+        WORKLOAD = "c3_mixed_200k"
+        WORKLOAD_DESC = ("200,000 stars in a 10x10 deg field (b in [-5, 5] deg), distances "
+                         "log-uniform 100-3000 pc, 64 nodes, L0 = 10 pc, cutoff 30 pc with "
+                         "Wendland taper, A_sigma uniform 0.03-0.1, truth from a 2 pc spectral "
+                         "GP draw, seed 0")
+        a.no_exact = a.no_forms = a.no_cpu = True
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "c4_fields":
