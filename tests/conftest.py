@@ -11,3 +11,23 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a)")
     config.addinivalue_line("markers", "slow: long CPU test")
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_golden_kv(name):
+    """key -> list of floats from a `key value...` fixture in tests/golden."""
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, *v = line.split()
+                out[k] = [float(x) for x in v]
+    return out
+
+
+@pytest.fixture(scope="session")
+def golden_kv():
+    return read_golden_kv

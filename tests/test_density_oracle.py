@@ -18,11 +18,11 @@ from synth import catalogue_subset, make_catalogue
     ([-2.0, -2.05], [[0.10, 0.09], [0.09, 0.10]]),   # difference often negative
     ([0.3, 0.9], [[0.2, -0.05], [-0.05, 0.3]]),
 ])
-def test_density_moments_against_sampling(mu, S):
+def test_density_moments_against_sampling(mu, S, golden_kv):
     rng = np.random.default_rng(11)
     a = rng.multivariate_normal(mu, S, size=2_000_000)
     keep = a[:, 1] > a[:, 0]
-    ds = 10.0
+    ds = golden_kv("sect5_setup.txt")["pair_offset_pc"][0]
     rho = (np.exp(a[keep, 1]) - np.exp(a[keep, 0])) / ds
     m, v = Dn.density_moments(mu, S, ds)
     se = rho.std() / np.sqrt(len(rho))
@@ -65,12 +65,12 @@ def test_pairs_marginals_equal_single_point_predictive(field):
     assert np.all(corr > 0.0) and np.all(corr < 1.0)
 
 
-def test_pairs_against_dense_gaussian_conditional(field):
+def test_pairs_against_dense_gaussian_conditional(field, golden_kv):
     """Joint prior over (stars, near points, far points), the sites as noisy
     pseudo-observations nu/tau with variance 1/tau: the conditional of the
     query points by the textbook formula (no B = I + S^1/2 K S^1/2)."""
     cat, cv, r, lq, bq, sq = field
-    ds = 10.0
+    ds = golden_kv("sect5_setup.txt")["pair_offset_pc"][0]
     mu, cov = Dn.predict_pairs(cat, cv["K"], cv["m"], r["tau"], r["nu"], lq, bq, sq, ds)
     assert np.all(r["tau"] > 0)
     nq = len(sq)
