@@ -15,7 +15,9 @@
  *     posterior marginals come from preconditioned conjugate-gradient
  *     solves driven by sparse matrix products;
  *   - the posterior predictive of a at query points (Sect. 2 eq. cond_GP0,
- *     Sect. 3.1 eq. map_dist).
+ *     Sect. 3.1 eq. map_dist), jointly for pairs or sightlines of points;
+ *   - the Sect. 5 products built on it: the extinction pseudo-density, and
+ *     samples of each sightline's predictive conditioned on dA/ds >= 0.
  *
  * Conventions for every call:
  *   - Angles in radians, distances in pc, extinctions in mag.  Returned
@@ -51,8 +53,10 @@ typedef enum {
   GM_E_INVAL = 1,      /* bad argument (null pointer, size, config value)   */
   GM_E_NOMEM = 2,      /* device allocation failed                          */
   GM_E_CUDA = 3,       /* CUDA runtime error (detail in gm_last_error)      */
-  GM_E_NOT_SPD = 4,    /* CG met p^T B p <= 0: the covariance is not PD     */
-  GM_E_NOCONV = 5,     /* CG hit its iteration cap above tolerance          */
+  GM_E_NOT_SPD = 4,    /* CG met p^T B p <= 0, or a sightline covariance
+                          has no Cholesky factor: not positive definite     */
+  GM_E_NOCONV = 5,     /* CG hit its iteration cap above tolerance, or a
+                          sampler step its wall-hit limit                   */
   GM_E_NONFINITE = 6,  /* a NaN or Inf appeared in K, the solves or sites   */
   GM_E_TIMEOUT = 7,    /* a bounded device wait gave up                     */
   GM_E_STATE = 8       /* call out of order (e.g. sweep before build_cov)   */
@@ -222,6 +226,40 @@ gm_status gm_predict(gm_ctx* ctx, int64_t nq, const double* l, const double* b,
 gm_status gm_predict_pairs(gm_ctx* ctx, int64_t nq, const double* l, const double* b,
                            const double* s, double ds, double* mean_out, double* cov_out,
                            double* dens_out);
+
+/* Joint posterior predictive of ln A at m points of each of nsl sightlines
+ * (Sect. 2 eq. cond_GP0 for the points of a sightline together; Sect. 5
+ * conditions these joint predictives on dA/ds >= 0).
+ * l, b: nsl directions (radians); s: nsl x m distances (pc), strictly
+ * increasing along each sightline (row q holds sightline q).  Host or device.
+ * mean_out: nsl x m; cov_out: nsl x m x m (row-major per sightline,
+ * symmetric).  The prior covariance of two points of one sightline uses the
+ * same quadrature (chord 0), cutoff and taper as K.  1 <= m <= 1024.
+ * Single-field contexts; GM_E_INVAL for distances that do not increase or are
+ * not finite and > 0. */
+gm_status gm_predict_sightlines(gm_ctx* ctx, int64_t nsl, int32_t m, const double* l,
+                                const double* b, const double* s, double* mean_out,
+                                double* cov_out);
+
+/* Samples of each sightline's Gaussian N(mean_q, cov_q) truncated to a
+ * non-decreasing sequence a_0 <= a_1 <= ... <= a_{m-1}: the condition
+ * dA/ds >= 0 of Sect. 5, by the exact Hamiltonian Monte Carlo of Pakman &
+ * Paninski (2014) that the paper uses.  Each step moves for time pi/2 from a
+ * fresh momentum and mirrors the velocity at every wall it meets; the chain
+ * starts from the running maximum of the mean (point i raised by 1e-9 i).
+ * mean: nsl x m; cov: nsl x m x m (the lower triangle is read), e.g. the
+ * output of gm_predict_sightlines; momenta: nsl x (n_burn + n_samples) x m
+ * standard normal draws (the caller supplies the randomness; step k of
+ * sightline q uses momenta[(q (n_burn + n_samples) + k) m ...]).
+ * samples_out: nsl x n_samples x m (the steps after the n_burn first);
+ * hits_out: nsl wall-hit counts, or NULL.  All host or device.  Needs no K
+ * (any context: its stream and allocator).  Errors: GM_E_NONFINITE (a mean
+ * or covariance entry not finite; nothing is written), GM_E_NOT_SPD (a covariance not positive
+ * definite: that sightline's samples are NaN, the others are written),
+ * GM_E_NOCONV (a step met 10,000 walls before its time was used). */
+gm_status gm_monotone_sample(gm_ctx* ctx, int64_t nsl, int32_t m, const double* mean,
+                             const double* cov, const double* momenta, int32_t n_burn,
+                             int32_t n_samples, double* samples_out, int64_t* hits_out);
 
 /* Marginal posterior mean and variance of ln A for every star under the
  * current sites (refreshed if the sites changed).  Length n each. */

@@ -900,6 +900,193 @@ gm_status gm_predict_pairs(gm_ctx* c, int64_t nq, const double* l, const double*
   return GM_OK;
 }
 
+// Index of the pair (a, c), a < c, among the m (m - 1) / 2 pairs of one
+// sightline in row-major order.
+__host__ __device__ inline int64_t sl_pair_index(int m, int a, int c) {
+  return (int64_t)a * m - (int64_t)a * (a + 1) / 2 + (c - a - 1);
+}
+
+// Pair points of every sightline: pair p = (q, a, c) has rows 2p (point a)
+// and 2p + 1 (point c) and quadrature inputs (s_a, s_c, chord 0).  Flags a
+// sightline whose distances do not increase.
+__global__ void k_sl_pairs(int64_t nsl, int m, const double* __restrict__ l,
+                           const double* __restrict__ b, const double* __restrict__ s,
+                           double* __restrict__ l2, double* __restrict__ b2,
+                           double* __restrict__ s2, double* __restrict__ si,
+                           double* __restrict__ sj, double* __restrict__ ch,
+                           unsigned* __restrict__ bad) {
+  const int64_t npq = (int64_t)m * (m - 1) / 2;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nsl * npq;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = p / npq;
+    int64_t k = p - q * npq;
+    int a = 0;
+    while (k >= m - 1 - a) {
+      k -= m - 1 - a;
+      ++a;
+    }
+    const int c = a + 1 + (int)k;
+    const double sa = s[q * m + a], sc = s[q * m + c];
+    if (!(sc > sa)) atomicOr(bad, 1u);
+    l2[2 * p] = l2[2 * p + 1] = l[q];
+    b2[2 * p] = b2[2 * p + 1] = b[q];
+    s2[2 * p] = sa;
+    s2[2 * p + 1] = sc;
+    si[p] = sa;
+    sj[p] = sc;
+    ch[p] = 0.0;
+  }
+}
+
+// Joint predictive of each sightline from its pairs: entry (a, c) of the
+// covariance is W(|s_c - s_a| / cutoff) k(s_a, s_c) - v_c^T B^-1 v_a, the
+// diagonal and the means come from a pair holding the point.
+__global__ void k_sl_assemble(int64_t nsl, int m, double inv_cut, int taper,
+                              const double* __restrict__ s, const double* __restrict__ mean2,
+                              const double* __restrict__ var2, const double* __restrict__ cross,
+                              const double* __restrict__ k12u, double* __restrict__ mean_out,
+                              double* __restrict__ cov_out) {
+  const int64_t npq = (int64_t)m * (m - 1) / 2;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nsl * mm;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / mm;
+    const int r = (int)(e - q * mm);
+    const int a = r / m, c = r - a * m;
+    if (a == c) {
+      const bool near = a < m - 1;
+      const int64_t p = q * npq + (near ? sl_pair_index(m, a, a + 1) : sl_pair_index(m, m - 2, m - 1));
+      const int64_t row = near ? 2 * p : 2 * p + 1;
+      cov_out[e] = var2[row];
+      mean_out[q * m + a] = mean2[row];
+    } else {
+      const int lo = a < c ? a : c, hi = a < c ? c : a;
+      const int64_t p = q * npq + sl_pair_index(m, lo, hi);
+      const double h = (s[q * m + hi] - s[q * m + lo]) * inv_cut;
+      double w = h <= 1.0 ? 1.0 : 0.0;
+      if (taper == GM_TAPER_WENDLAND) {
+        const double u = 1.0 - h;
+        w = h < 1.0 ? u * u * u * u * (4.0 * h + 1.0) : 0.0;
+      }
+      cov_out[e] = w * k12u[p] - cross[p];
+    }
+  }
+}
+
+gm_status gm_predict_sightlines(gm_ctx* c, int64_t nsl, int32_t m, const double* l,
+                                const double* b, const double* s, double* mean_out,
+                                double* cov_out) {
+  if (!c || nsl < 0 || m < 1 || m > kMaxSightlinePoints ||
+      (nsl > 0 && (!l || !b || !s || !mean_out || !cov_out)))
+    return GM_E_INVAL;
+  if (c->n_fields > 1)
+    return set_error(c, GM_E_STATE, "prediction needs a single-field context");
+  if (nsl == 0) return GM_OK;
+  c->launches = 0;
+  gm_status st = ensure_posterior(c);
+  if (st != GM_OK) return st;
+  const int64_t np = nsl * m;  // points
+  const int64_t mm = (int64_t)m * m;
+  if (m == 1) {  // no pairs: the single-point predictive
+    double* q = (double*)dev_alloc(c, 5 * np * sizeof(double));
+    if (!q) return set_error(c, GM_E_NOMEM, "sightline arrays");
+    if ((st = copy_in(c, q, l, np * sizeof(double))) != GM_OK ||
+        (st = copy_in(c, q + np, b, np * sizeof(double))) != GM_OK ||
+        (st = copy_in(c, q + 2 * np, s, np * sizeof(double))) != GM_OK)
+      return st;
+    st = predict_points(c, np, q, q + np, q + 2 * np, q + 3 * np, q + 4 * np, nullptr);
+    if (st != GM_OK) return st;
+    if ((st = copy_out(c, mean_out, q + 3 * np, np * sizeof(double))) != GM_OK) return st;
+    if ((st = copy_out(c, cov_out, q + 4 * np, np * sizeof(double))) != GM_OK) return st;
+    dev_free_now(c, q, 5 * np * sizeof(double));
+    c->stats.kernel_launches = c->launches;
+    return GM_OK;
+  }
+  const int64_t npr = nsl * ((int64_t)m * (m - 1) / 2);  // pairs
+  // l, b (nsl); s, mean (np); cov (nsl m^2); l2, b2, s2, mean2, var2 (2 npr);
+  // si, sj, ch, k12, cross (npr)
+  const size_t nd = 2 * nsl + 2 * np + nsl * mm + 15 * npr;
+  double* q = (double*)dev_alloc(c, nd * sizeof(double));
+  if (!q) return set_error(c, GM_E_NOMEM, "sightline pair arrays");
+  double *ql = q, *qb = ql + nsl, *qs = qb + nsl, *mean = qs + np, *cov = mean + np,
+         *l2 = cov + nsl * mm, *b2 = l2 + 2 * npr, *s2 = b2 + 2 * npr, *mean2 = s2 + 2 * npr,
+         *var2 = mean2 + 2 * npr, *si = var2 + 2 * npr, *sj = si + npr, *ch = sj + npr,
+         *k12 = ch + npr, *cross = k12 + npr;
+  if ((st = copy_in(c, ql, l, nsl * sizeof(double))) != GM_OK ||
+      (st = copy_in(c, qb, b, nsl * sizeof(double))) != GM_OK ||
+      (st = copy_in(c, qs, s, np * sizeof(double))) != GM_OK)
+    return st;
+  GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 2, 0, sizeof(unsigned), c->stream));
+  GM_PROF(c, "k_sl_pairs");
+  k_sl_pairs<<<eb(c, npr), 256, 0, c->stream>>>(nsl, m, ql, qb, qs, l2, b2, s2, si, sj, ch,
+                                                c->d_flags + 2);
+  GM_LAUNCH_CHECK(c);
+  {
+    unsigned* h = (unsigned*)c->h_pinned;
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags + 2, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                     c->stream));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    if (*h) return set_error(c, GM_E_INVAL, "sightline distances must increase");
+  }
+  st = predict_points(c, 2 * npr, l2, b2, s2, mean2, var2, cross);
+  if (st == GM_OK) st = pairlist_quadrature(c, npr, si, sj, ch, k12);
+  if (st != GM_OK) return st;
+  GM_PROF(c, "k_sl_assemble");
+  k_sl_assemble<<<eb(c, nsl * mm), 256, 0, c->stream>>>(nsl, m, 1.0 / c->cfg.cutoff_pc,
+                                                        c->cfg.taper, qs, mean2, var2, cross,
+                                                        k12, mean, cov);
+  GM_LAUNCH_CHECK(c);
+  if ((st = read_flags(c)) != GM_OK) return st;
+  if ((st = copy_out(c, mean_out, mean, np * sizeof(double))) != GM_OK) return st;
+  if ((st = copy_out(c, cov_out, cov, nsl * mm * sizeof(double))) != GM_OK) return st;
+  dev_free_now(c, q, nd * sizeof(double));
+  c->stats.kernel_launches = c->launches;
+  return GM_OK;
+}
+
+gm_status gm_monotone_sample(gm_ctx* c, int64_t nsl, int32_t m, const double* mean,
+                             const double* cov, const double* momenta, int32_t n_burn,
+                             int32_t n_samples, double* samples_out, int64_t* hits_out) {
+  if (!c || nsl < 0 || m < 1 || m > kMaxSightlinePoints || n_burn < 0 || n_samples < 0 ||
+      (nsl > 0 && (!mean || !cov || !momenta || (n_samples > 0 && !samples_out))))
+    return GM_E_INVAL;
+  if (nsl == 0 || (int64_t)n_burn + n_samples == 0) return GM_OK;
+  c->launches = 0;
+  const int64_t T = (int64_t)n_burn + n_samples;
+  const int64_t mm = (int64_t)m * m;
+  // mean (nsl m), cov (nsl m^2), momenta (nsl T m), samples (nsl n_samples m), hits (nsl)
+  const size_t nd = nsl * (m + mm + T * m + (int64_t)n_samples * m + 1);
+  double* q = (double*)dev_alloc(c, nd * sizeof(double));
+  if (!q) return set_error(c, GM_E_NOMEM, "sampler arrays");
+  double *dm = q, *dc = dm + nsl * m, *dp = dc + nsl * mm, *dout = dp + nsl * T * m;
+  int64_t* dh = (int64_t*)(dout + nsl * (int64_t)n_samples * m);
+  gm_status st;
+  if ((st = copy_in(c, dm, mean, nsl * m * sizeof(double))) != GM_OK ||
+      (st = copy_in(c, dc, cov, nsl * mm * sizeof(double))) != GM_OK ||
+      (st = copy_in(c, dp, momenta, nsl * T * m * sizeof(double))) != GM_OK)
+    return st;
+  GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 2, 0, sizeof(unsigned), c->stream));
+  st = monotone_sample(c, nsl, m, dm, dc, dp, n_burn, n_samples, dout, dh, c->d_flags + 2);
+  if (st != GM_OK) return st;
+  unsigned* h = (unsigned*)c->h_pinned;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags + 2, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                   c->stream));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  const unsigned f = *h;
+  if (f & kFlagNonFinite) return set_error(c, GM_E_NONFINITE, "non-finite mean or covariance");
+  if (n_samples > 0 &&
+      (st = copy_out(c, samples_out, dout, nsl * (int64_t)n_samples * m * sizeof(double))) != GM_OK)
+    return st;
+  if (hits_out && (st = copy_out(c, hits_out, dh, nsl * sizeof(int64_t))) != GM_OK) return st;
+  dev_free_now(c, q, nd * sizeof(double));
+  c->stats.kernel_launches = c->launches;
+  if (f & kFlagNotSPD)
+    return set_error(c, GM_E_NOT_SPD, "a sightline covariance is not positive definite");
+  if (f & kFlagHitLimit)
+    return set_error(c, GM_E_NOCONV, "a sampler step reached the wall-hit limit");
+  return GM_OK;
+}
+
 gm_status gm_profile(gm_ctx* c, int32_t enable) {
   if (!c) return GM_E_INVAL;
   prof_collect(c);

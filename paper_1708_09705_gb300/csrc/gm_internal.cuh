@@ -14,6 +14,7 @@ namespace gm {
 // ---------------------------------------------------------------- constants
 constexpr int kGH = 64;          // Gauss-Hermite nodes of the tilted rule
 constexpr int kMaxNodes = 128;   // Gauss-Legendre nodes per sightline (max)
+constexpr int kMaxSightlinePoints = 1024;  // points of one sightline (joint predictive, sampler)
 
 // Device status flags (OR-ed by kernels, read by the host after a call).
 enum : unsigned {
@@ -22,6 +23,7 @@ enum : unsigned {
   kFlagTimeout = 4u,
   kFlagProbeOverflow = 8u,
   kFlagBadIndex = 16u,
+  kFlagHitLimit = 32u,   // a sampler step used up its wall hits
 };
 
 // Log-spaced cubic table of g(x), x = r^2 / L0^2.  Segment k >= 0 covers
@@ -331,6 +333,14 @@ gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
 gm_status site_update(gm_ctx* c, double* max_delta, int64_t* skipped);
 
 void workspace_free(gm_ctx* c);
+
+// Exact-HMC samples of each sightline's predictive truncated to a
+// non-decreasing sequence (gm_sightline.cu).  Device arrays in the caller
+// layout of gm_monotone_sample; flags: a device word for kFlagNonFinite,
+// kFlagNotSPD and kFlagHitLimit.  Synchronises the stream.
+gm_status monotone_sample(gm_ctx* c, int64_t nsl, int m, const double* mean, const double* cov,
+                          const double* mom, int n_burn, int n_samples, double* out,
+                          int64_t* hits, unsigned* flags);
 
 // Packed per-field variance panels for multi-field contexts (gm_fields.cu).
 gm_status panels_fields(gm_ctx* c, const float* dv, const float* minv, const double* d64,

@@ -35,7 +35,8 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_destroy", "gm_profile", "gm_kernel_time_count", "gm_kernel_time",
            "gm_site_update_noalloc", "gm_surrogate_param_count", "gm_surrogate_set_params",
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
-           "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries", "gm_predict_pairs"]
+           "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries", "gm_predict_pairs",
+           "gm_predict_sightlines", "gm_monotone_sample"]
 
 
 class GmError(RuntimeError):
@@ -100,6 +101,8 @@ def lib():
         L.gm_get_probe_colours.argtypes = [vp, vp]
         L.gm_get_entries.argtypes = [vp, i64, vp, vp, vp]
         L.gm_predict_pairs.argtypes = [vp, i64, vp, vp, vp, dbl, vp, vp, vp]
+        L.gm_predict_sightlines.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
+        L.gm_monotone_sample.argtypes = [vp, i64, i32, vp, vp, vp, i32, i32, vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.gm_stream.argtypes = [vp]
@@ -224,6 +227,36 @@ class Context:
                                            s.ctypes.data, float(ds), mean.ctypes.data,
                                            cov.ctypes.data, dens.ctypes.data))
         return mean, cov, dens
+
+    def predict_sightlines(self, l, b, s):
+        """Joint predictive of the m points s[q, :] (increasing) on each
+        sightline (l[q], b[q]): (means (nsl, m), covariances (nsl, m, m))."""
+        l, b = (np.ascontiguousarray(v, dtype=np.float64) for v in (l, b))
+        s = np.ascontiguousarray(np.atleast_2d(s), dtype=np.float64)
+        nsl, m = s.shape
+        mean, cov = np.empty((nsl, m)), np.empty((nsl, m, m))
+        self._check(lib().gm_predict_sightlines(self._h, nsl, m, l.ctypes.data, b.ctypes.data,
+                                                s.ctypes.data, mean.ctypes.data,
+                                                cov.ctypes.data))
+        return mean, cov
+
+    def monotone_sample(self, mean, cov, momenta, n_burn):
+        """Exact-HMC samples of N(mean[q], cov[q]) truncated to a
+        non-decreasing sequence; momenta: (nsl, n_burn + n_samples, m)
+        standard normal draws.  Returns (samples (nsl, n_samples, m), wall
+        hits (nsl,))."""
+        mean = np.ascontiguousarray(np.atleast_2d(mean), dtype=np.float64)
+        nsl, m = mean.shape
+        cov = np.ascontiguousarray(cov, dtype=np.float64).reshape(nsl, m, m)
+        momenta = np.ascontiguousarray(momenta, dtype=np.float64)
+        T = momenta.shape[1]
+        assert momenta.shape == (nsl, T, m) and 0 <= n_burn <= T
+        ns = T - int(n_burn)
+        out, hits = np.empty((nsl, ns, m)), np.empty(nsl, dtype=np.int64)
+        self._check(lib().gm_monotone_sample(self._h, nsl, m, mean.ctypes.data, cov.ctypes.data,
+                                             momenta.ctypes.data, int(n_burn), ns,
+                                             out.ctypes.data, hits.ctypes.data))
+        return out, hits
 
     # ---- state
     def _pair_out(self, fn, out):
