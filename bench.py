@@ -71,9 +71,18 @@ def parse():
                    help="deflation vectors of the FP32 variance preconditioner (0 = Jacobi)")
     p.add_argument("--no-exact", action="store_true",
                    help="skip the one-step exact-variance comparison")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4_fields"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4_fields", "sightlines"],
                    help="c2: the 20,000-star field (bench line); c4_fields: 256 independent "
-                        "fields solved together (batched path)")
+                        "fields solved together (batched path); sightlines: the dA/ds >= 0 "
+                        "conditioning on the 20,000-star posterior (joint sightline "
+                        "predictive + exact-HMC sampler)")
+    p.add_argument("--sl-predict", type=int, default=256,
+                   help="sightlines of the joint-predictive leg (--workload sightlines)")
+    p.add_argument("--sl-sample", type=int, default=65536,
+                   help="sightlines of the sampler leg (--workload sightlines)")
+    p.add_argument("--sl-points", type=int, default=16, help="points per sightline")
+    p.add_argument("--sl-steps", type=int, default=120,
+                   help="HMC steps per sightline (the first 20 are burn-in)")
     return p.parse_args()
 
 
@@ -545,6 +554,108 @@ def run_gpu(a):
     if ws > 1:
         torch.distributed.destroy_process_group()
 
+def run_sightlines(a):
+    """The dA/ds >= 0 conditioning of Sect. 5 on the 20k field's posterior
+    after `--sweeps` EP sweeps (computed before timing): (1) the joint
+    predictive of `--sl-points` points on each of `--sl-predict` sightlines,
+    (2) the exact-HMC sampler on `--sl-sample` sightlines.  The sampler's
+    inputs are the first leg's predictives, repeated, with fresh momenta per
+    sightline (drawn on the device, outside the timed region)."""
+    import torch
+
+    import paper_1708_09705_gb300 as gm
+    from synth import make_catalogue
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cat = make_catalogue(WORKLOAD, n=a.n, seed=0)
+    n = len(cat["s"])
+    cfg = gm.config_from_catalogue(cat, precision=gm.PREC_FP32, probe_factor=a.probe,
+                                   deflate=a.deflate, cg_tol=1e-6)
+    ctx = gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"])
+    ctx.build_cov()
+    ctx.ep_sweep(a.sweeps, 0.0)
+    m, nsl = a.sl_points, a.sl_predict
+    rng = np.random.default_rng(0)
+    lo, hi = cat["l"].min(), cat["l"].max()
+    blo, bhi = cat["b"].min(), cat["b"].max()
+    lq = rng.uniform(lo, hi, nsl)
+    bq = rng.uniform(blo, bhi, nsl)
+    sq = np.tile(np.geomspace(150.0, 2800.0, m), (nsl, 1))
+    D = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in
+         (("l", lq), ("b", bq), ("s", sq))}
+    mean = torch.empty((nsl, m), dtype=torch.float64, device=dev)
+    cov = torch.empty((nsl, m, m), dtype=torch.float64, device=dev)
+    L = gm.lib()
+
+    def predict():
+        ctx._check(L.gm_predict_sightlines(ctx._h, nsl, m, D["l"].data_ptr(), D["b"].data_ptr(),
+                                           D["s"].data_ptr(), mean.data_ptr(), cov.data_ptr()))
+
+    T = a.sl_steps
+    burn = min(20, T - 1)
+    ns_ = a.sl_sample
+    rep = torch.arange(ns_, device=dev) % nsl
+    means, covs = mean[rep].contiguous(), cov[rep].contiguous()
+    mom = torch.empty((ns_, T, m), dtype=torch.float64, device=dev)
+    out = torch.empty((ns_, T - burn, m), dtype=torch.float64, device=dev)
+    hits = torch.empty(ns_, dtype=torch.int64, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+
+    def sample():
+        ctx._check(L.gm_monotone_sample(ctx._h, ns_, m, means.data_ptr(), covs.data_ptr(),
+                                        mom.data_ptr(), burn, T - burn, out.data_ptr(),
+                                        hits.data_ptr()))
+
+    res, kts = {}, {}
+    for name, fn in (("predict", predict), ("sample", sample)):
+        for _ in range(a.warmup):
+            if name == "sample":
+                mom.normal_(generator=gen)
+                means.copy_(mean[rep])
+                covs.copy_(cov[rep])
+            fn()
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ts = []
+        for _ in range(a.steps):
+            if name == "sample":
+                mom.normal_(generator=gen)
+            torch.cuda.synchronize()
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        kts[name] = ctx.kernel_times()
+        ctx.profile(False)
+        res[name] = sum(ts) / len(ts)
+    feasible = bool((out[:, :, 1:] >= out[:, :, :-1]).all())
+    ctx.close()
+    line = {"metric": "sightline conditioning on dA/ds >= 0 (Sect. 5)",
+            "value": ns_ * T / res["sample"], "unit": "HMC sightline-steps/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}; EP posterior after "
+                                   f"{a.sweeps} sweeps (FP32 form, probed, deflated)",
+                       "points_per_sightline": m,
+                       "distances_pc": "geometric 150-2800"},
+            "predict_sightlines": {"sightlines": nsl, "ms": 1e3 * res["predict"],
+                                   "points_per_s": nsl * m / res["predict"],
+                                   "query_columns": nsl * m * (m - 1)},
+            "monotone_sample": {"sightlines": ns_, "steps": T, "burn": burn,
+                                "ms": 1e3 * res["sample"],
+                                "k_monotone_hmc_ms": kts["sample"].get("k_monotone_hmc",
+                                                                       (0, 0.0))[1] / a.steps,
+                                "wall_hits_per_step": float(hits.double().mean()) / T,
+                                "all_samples_non_decreasing": feasible},
+            "kernels_ms": {k: [v[0], round(v[1], 3)] for kt in kts.values()
+                           for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])[:6]},
+            "gpu_launches": int(sum(v[0] for kt in kts.values() for v in kt.values()))}
+    print(json.dumps(line), flush=True)
+
 
 def main():
     a = parse()
@@ -563,6 +674,8 @@ def main():
         run_reference(a)
     elif a.workload == "c4_fields":
         run_fields(a)
+    elif a.workload == "sightlines":
+        run_sightlines(a)
     else:
         run_gpu(a)
 
