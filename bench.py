@@ -634,6 +634,22 @@ def run_sightlines(a):
         res[name] = sum(ts) / len(ts)
     feasible = bool((out[:, :, 1:] >= out[:, :, :-1]).all())
     ctx.close()
+    cpu = None
+    if not a.no_cpu:
+        # the oracle's chain on a bounded sample of the same sightlines
+        from oracle import monotone as Mo
+        ncpu = 32
+        mh, ch = mean.cpu().numpy(), cov.cpu().numpy()
+        mo = np.random.default_rng(1).standard_normal((ncpu, T, m))
+        t0 = time.perf_counter()
+        for q in range(ncpu):
+            Mo.monotone_sightline(mh[q % nsl], ch[q % nsl], T - burn, None, burn=burn,
+                                  momenta=mo[q])
+        tc = time.perf_counter() - t0
+        cpu = {"value": ncpu * T / tc, "unit": "HMC sightline-steps/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"{ncpu} of the sampled sightlines x {T} steps, oracle/monotone.py "
+                         f"(pure Python wall search, one core), {tc:.1f} s"}
     line = {"metric": "sightline conditioning on dA/ds >= 0 (Sect. 5)",
             "value": ns_ * T / res["sample"], "unit": "HMC sightline-steps/s",
             "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
@@ -651,6 +667,7 @@ def run_sightlines(a):
                                                                        (0, 0.0))[1] / a.steps,
                                 "wall_hits_per_step": float(hits.double().mean()) / T,
                                 "all_samples_non_decreasing": feasible},
+            "cpu_baseline": cpu,
             "kernels_ms": {k: [v[0], round(v[1], 3)] for kt in kts.values()
                            for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])[:6]},
             "gpu_launches": int(sum(v[0] for kt in kts.values() for v in kt.values()))}
