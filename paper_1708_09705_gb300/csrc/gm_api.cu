@@ -988,7 +988,8 @@ gm_status gm_predict_sightlines(gm_ctx* c, int64_t nsl, int32_t m, const double*
   const int64_t np = nsl * m;  // points
   const int64_t mm = (int64_t)m * m;
   if (m == 1) {  // no pairs: the single-point predictive
-    double* q = (double*)dev_alloc(c, 5 * np * sizeof(double));
+    ScopedDev buf(c, 5 * np * sizeof(double));
+    double* q = (double*)buf.p;
     if (!q) return set_error(c, GM_E_NOMEM, "sightline arrays");
     if ((st = copy_in(c, q, l, np * sizeof(double))) != GM_OK ||
         (st = copy_in(c, q + np, b, np * sizeof(double))) != GM_OK ||
@@ -998,7 +999,6 @@ gm_status gm_predict_sightlines(gm_ctx* c, int64_t nsl, int32_t m, const double*
     if (st != GM_OK) return st;
     if ((st = copy_out(c, mean_out, q + 3 * np, np * sizeof(double))) != GM_OK) return st;
     if ((st = copy_out(c, cov_out, q + 4 * np, np * sizeof(double))) != GM_OK) return st;
-    dev_free_now(c, q, 5 * np * sizeof(double));
     c->stats.kernel_launches = c->launches;
     return GM_OK;
   }
@@ -1006,7 +1006,8 @@ gm_status gm_predict_sightlines(gm_ctx* c, int64_t nsl, int32_t m, const double*
   // l, b (nsl); s, mean (np); cov (nsl m^2); l2, b2, s2, mean2, var2 (2 npr);
   // si, sj, ch, k12, cross (npr)
   const size_t nd = 2 * nsl + 2 * np + nsl * mm + 15 * npr;
-  double* q = (double*)dev_alloc(c, nd * sizeof(double));
+  ScopedDev buf(c, nd * sizeof(double));
+  double* q = (double*)buf.p;
   if (!q) return set_error(c, GM_E_NOMEM, "sightline pair arrays");
   double *ql = q, *qb = ql + nsl, *qs = qb + nsl, *mean = qs + np, *cov = mean + np,
          *l2 = cov + nsl * mm, *b2 = l2 + 2 * npr, *s2 = b2 + 2 * npr, *mean2 = s2 + 2 * npr,
@@ -1039,7 +1040,6 @@ gm_status gm_predict_sightlines(gm_ctx* c, int64_t nsl, int32_t m, const double*
   if ((st = read_flags(c)) != GM_OK) return st;
   if ((st = copy_out(c, mean_out, mean, np * sizeof(double))) != GM_OK) return st;
   if ((st = copy_out(c, cov_out, cov, nsl * mm * sizeof(double))) != GM_OK) return st;
-  dev_free_now(c, q, nd * sizeof(double));
   c->stats.kernel_launches = c->launches;
   return GM_OK;
 }
@@ -1056,7 +1056,8 @@ gm_status gm_monotone_sample(gm_ctx* c, int64_t nsl, int32_t m, const double* me
   const int64_t mm = (int64_t)m * m;
   // mean (nsl m), cov (nsl m^2), momenta (nsl T m), samples (nsl n_samples m), hits (nsl)
   const size_t nd = nsl * (m + mm + T * m + (int64_t)n_samples * m + 1);
-  double* q = (double*)dev_alloc(c, nd * sizeof(double));
+  ScopedDev buf(c, nd * sizeof(double));
+  double* q = (double*)buf.p;
   if (!q) return set_error(c, GM_E_NOMEM, "sampler arrays");
   double *dm = q, *dc = dm + nsl * m, *dp = dc + nsl * mm, *dout = dp + nsl * T * m;
   int64_t* dh = (int64_t*)(dout + nsl * (int64_t)n_samples * m);
@@ -1078,7 +1079,6 @@ gm_status gm_monotone_sample(gm_ctx* c, int64_t nsl, int32_t m, const double* me
       (st = copy_out(c, samples_out, dout, nsl * (int64_t)n_samples * m * sizeof(double))) != GM_OK)
     return st;
   if (hits_out && (st = copy_out(c, hits_out, dh, nsl * sizeof(int64_t))) != GM_OK) return st;
-  dev_free_now(c, q, nd * sizeof(double));
   c->stats.kernel_launches = c->launches;
   if (f & kFlagNotSPD)
     return set_error(c, GM_E_NOT_SPD, "a sightline covariance is not positive definite");

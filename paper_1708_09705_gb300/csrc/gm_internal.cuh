@@ -196,6 +196,20 @@ void* dev_alloc(gm_ctx* c, size_t bytes);            // owned until destroy
 void dev_free_now(gm_ctx* c, void* p, size_t bytes);
 bool ensure(gm_ctx* c, Buffer& b, size_t bytes);      // grow-only scratch
 
+// Device buffer of one call, released (stream-ordered) when the scope ends,
+// error returns included.
+struct ScopedDev {
+  gm_ctx* c;
+  void* p;
+  size_t bytes;
+  ScopedDev(gm_ctx* ctx, size_t n) : c(ctx), p(dev_alloc(ctx, n)), bytes(n) {}
+  ~ScopedDev() {
+    if (p) dev_free_now(c, p, bytes);
+  }
+  ScopedDev(const ScopedDev&) = delete;
+  ScopedDev& operator=(const ScopedDev&) = delete;
+};
+
 #define GM_CUDA_CHECK(ctx, expr)                                   \
   do {                                                             \
     cudaError_t _e = (expr);                                       \

@@ -54,7 +54,8 @@ gm_status monotone_sample(gm_ctx* c, int64_t nsl, int m, const double* mean, con
   const int64_t mm = (int64_t)m * m;
   // scratch: mu_t (m), S_t (m^2), L_t (m^2), y_t (m), w_t (m) per sightline
   const size_t bytes = (size_t)nsl * (3 * m + 2 * mm) * sizeof(double);
-  double* ws = (double*)dev_alloc(c, bytes);
+  ScopedDev buf(c, bytes);
+  double* ws = (double*)buf.p;
   if (!ws) return set_error(c, GM_E_NOMEM, "sampler scratch");
   double *mu_t = ws, *S_t = mu_t + nsl * m, *L_t = S_t + nsl * mm, *y_t = L_t + nsl * mm,
          *w_t = y_t + nsl * m;
@@ -69,17 +70,13 @@ gm_status monotone_sample(gm_ctx* c, int64_t nsl, int m, const double* mean, con
     GM_CUDA_CHECK(c, cudaMemcpyAsync(h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                      c->stream));
     GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
-    if (*h & kFlagNonFinite) {
-      dev_free_now(c, ws, bytes);
-      return GM_OK;  // the caller reads the flag and reports it
-    }
+    if (*h & kFlagNonFinite) return GM_OK;  // the caller reads the flag and reports it
   }
   GM_PROF(c, "k_monotone_hmc");
   k_monotone_hmc<<<(unsigned)ceil_div(nsl, 128), 128, 0, c->stream>>>(
       nsl, m, n_burn, n_samples, mu_t, S_t, L_t, y_t, w_t, mom, out, hits, flags);
   GM_LAUNCH_CHECK(c);
   GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
-  dev_free_now(c, ws, bytes);
   return GM_OK;
 }
 
