@@ -76,6 +76,13 @@ enum { GM_TAPER_WENDLAND = 0, GM_TAPER_HARD = 1 };
 enum { GM_COV_QUADRATURE = 0, GM_COV_SURROGATE = 1 };
 /* Per-star likelihood: A_obs ~ N(exp(a), sigma^2) or a_obs ~ N(a, sigma^2). */
 enum { GM_LIK_GAUSS_IN_A = 0, GM_LIK_GAUSS_IN_LNA = 1 };
+/* Node rule of the sightline double integral (Sect. 3): n_nodes-point
+ * Gauss-Legendre on each sightline, or the band rule (composite
+ * Gauss-Legendre in d = t - t' and m = (t + t')/2, panels graded towards the
+ * cusp of the kernel at zero separation, truncated at 40 outer scales),
+ * which converges where the distance is many outer scales (the global rule's
+ * nodes are s / n_nodes apart). */
+enum { GM_QUAD_GL = 0, GM_QUAD_BAND = 1 };
 
 typedef struct {
   double sigma2;          /* variance of the log-density GP (> 0)             */
@@ -116,6 +123,9 @@ typedef struct {
                              error is the neglected cross terms, which decay
                              with the distance (measured 4e-8 relative at
                              2 x cutoff on a 20,000-star 5-degree field)      */
+  int32_t quad_rule;      /* GM_QUAD_GL (default; n_nodes per sightline) or
+                             GM_QUAD_BAND (n_nodes unused).  The band rule
+                             needs cov_source = GM_COV_QUADRATURE          */
 } gm_config;
 
 /* Device memory hooks.  When given, every device allocation of the context

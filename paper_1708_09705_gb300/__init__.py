@@ -6,4 +6,4 @@ from .gmead import (Config, Context, GmError, build_cov, config_from_catalogue, 
                     default_config, ep_init, ep_sweep, get_posterior, lib, predict,
                     PREC_FP32, PREC_FP64, FORM_LINEAR, FORM_LOGNORMAL, TAPER_HARD,
                     TAPER_WENDLAND, LIK_GAUSS_IN_A, LIK_GAUSS_IN_LNA, EXPORTS, LIB_PATH,
-                    COV_QUADRATURE, COV_SURROGATE)
+                    COV_QUADRATURE, COV_SURROGATE, QUAD_GL, QUAD_BAND)

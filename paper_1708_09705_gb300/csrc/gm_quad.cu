@@ -16,11 +16,17 @@
 // in x^2 = r^2 / L0^2; each build refits the table of g for the current
 // sigma2 and the quadrature kernels interpolate it.  The separation is taken
 // in the cancellation-free chord form r^2 = (t - t')^2 + t t' |u_i - u_j|^2.
+//
+// Two node rules: the Q-node Gauss-Legendre rule on each sightline
+// (GM_QUAD_GL), and the band rule of gm_band.cuh (GM_QUAD_BAND), composite
+// Gauss-Legendre in d = t - t', m = (t + t')/2 graded towards the cusp of g,
+// which converges where s >> L0 (the Q-node rule's nodes are s / Q apart).
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
 
+#include "gm_band.cuh"
 #include "gm_internal.cuh"
 
 namespace gm {
@@ -320,6 +326,128 @@ __global__ void k_self_quad(QuadParams P, int64_t n_rows, const double* __restri
   }
 }
 
+// ------------------------------------------------------------ band rule
+// g by table lookup in the arithmetic type of the inner sums.
+template <typename T>
+struct GLook;
+template <>
+struct GLook<float> {
+  const float4* tab;
+  TabF32 t;
+  __device__ float operator()(float x) const { return g_lookup(tab, t, x); }
+};
+template <>
+struct GLook<double> {
+  const D4* tab;
+  TabF64 t;
+  __device__ double operator()(double x) const { return g_lookup(tab, t, x); }
+};
+
+// R = I / (s_i s_j) of one pair by the band rule (A = s_i / L0, B = s_j / L0,
+// c2 = |u_i - u_j|^2); the warp's lanes share the d-nodes.  Every lane
+// returns the sum.
+template <typename T>
+__device__ __forceinline__ double band_R_warp(double A, double B, double c2, const GLook<T>& g,
+                                              int lane) {
+  const gmband::Geometry geo = gmband::geometry(A, B, c2);
+  T acc = 0;
+  const int nk = gmband::d_nodes(geo);
+  for (int k = lane; k < nk; k += 32) acc += gmband::d_node<T>(geo, k, g);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  return (double)acc / (A * B);
+}
+
+template <typename T>
+__device__ __forceinline__ GLook<T> band_lookup(const void* gtab, TabF32 tf, TabF64 td,
+                                                unsigned char* smem) {
+  GLook<T> g;
+  if constexpr (sizeof(T) == 4) {
+    // the FP32 table lives in shared memory
+    float4* st = reinterpret_cast<float4*>(smem);
+    const float4* gt = reinterpret_cast<const float4*>(gtab);
+    for (int k = threadIdx.x; k <= tf.last; k += blockDim.x) st[k] = gt[k];
+    g.tab = st;
+    g.t = tf;
+  } else {
+    g.tab = reinterpret_cast<const D4*>(gtab);
+    g.t = td;
+  }
+  return g;
+}
+
+// The band-rule counterpart of k_pair_quad (same entries, taper, mirror
+// convention, diagonal and prior mean).
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_quad_band(
+    QuadParams P, int64_t n_rows, const double* __restrict__ rs, const double* __restrict__ rux,
+    const double* __restrict__ ruy, const double* __restrict__ ruz, const double* __restrict__ s,
+    const double* __restrict__ ux, const double* __restrict__ uy, const double* __restrict__ uz,
+    const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
+    T* __restrict__ val, const void* __restrict__ gtab, TabF32 tf, TabF64 td,
+    double* __restrict__ kdiag, double* __restrict__ prior_m, unsigned* __restrict__ flags,
+    const FieldGrid* __restrict__ fg, const int32_t* __restrict__ row_field) {
+  extern __shared__ unsigned char smem[];
+  const GLook<T> g = band_lookup<T>(gtab, tf, td, smem);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < nnz; e += nwarps) {
+    int64_t lo = 0, hi = n_rows;
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (row_ptr[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int64_t i = lo;
+    const int32_t j = col[e];
+    if (P.symmetric && j < i) continue;
+    const FieldGrid& fgi = fg[row_field ? row_field[i] : 0];
+    const double inv_L0 = fgi.inv_L0, inv_cut = fgi.inv_cut;
+    const double si = rs[i], sj = s[j];
+    const double dx = rux[i] - ux[j], dy = ruy[i] - uy[j], dz = ruz[i] - uz[j];
+    const double chord2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    const double R = band_R_warp<T>(si * inv_L0, sj * inv_L0, chord2, g, lane);
+    if (lane == 0) {
+      double K = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
+      if (P.taper == GM_TAPER_WENDLAND) {
+        double ds = si - sj;
+        double d = sqrt(fma(ds, ds, si * sj * chord2));
+        K *= wendland(d * inv_cut);
+      }
+      if (!isfinite(K)) atomicOr(flags, kFlagNonFinite);
+      val[e] = (T)K;
+      if (P.symmetric && j == i) {
+        kdiag[i] = (double)(T)K;
+        prior_m[i] = P.log_rho_bar + log(si) -
+                     (P.form == GM_FORM_LOGNORMAL ? 0.5 * (double)(T)K : 0.5 * P.sigma2);
+      }
+    }
+  }
+}
+
+// Band-rule self-covariance of query points (k_self_quad's counterpart).
+template <typename T>
+__global__ void __launch_bounds__(256) k_self_quad_band(QuadParams P, int64_t n_rows,
+                                                        const double* __restrict__ rs,
+                                                        const void* __restrict__ gtab, TabF32 tf,
+                                                        TabF64 td, double* __restrict__ out) {
+  extern __shared__ unsigned char smem[];
+  const GLook<T> g = band_lookup<T>(gtab, tf, td, smem);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n_rows; r += nwarps) {
+    const double a = rs[r] * P.inv_L0;
+    const double R = band_R_warp<T>(a, a, 0.0, g, lane);
+    if (lane == 0) {
+      const double K = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
+      out[r] = (double)(T)K;
+    }
+  }
+}
+
 // ------------------------------------------------------------ host side
 static TabF32 tab_f32() {
   TabF32 t;
@@ -411,6 +539,30 @@ static void launch_pair(gm_ctx* c, const QuadParams& P, int64_t n_rows, const do
                                          c->fgrid, row_field);
 }
 
+// Shared memory of the band kernels: the FP32 table (none for FP64).
+static size_t band_smem(bool f32) {
+  return f32 ? (size_t)(kTabF32.n_real() + 1) * sizeof(float4) : 0;
+}
+
+template <typename T>
+static void launch_pair_band(gm_ctx* c, const QuadParams& P, int64_t n_rows, const double* rs,
+                             const double* rux, const double* ruy, const double* ruz,
+                             const int32_t* row_field, const int64_t* row_ptr,
+                             const int32_t* col, int64_t nnz, void* val) {
+  const size_t smem = band_smem(sizeof(T) == 4);
+  auto kern = k_pair_quad_band<T>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  int blocks = std::max(1, per_sm) * sm_count(c);
+  blocks = (int)std::min<int64_t>(blocks, std::max<int64_t>(1, ceil_div(nnz * 32, 256)));
+  GM_PROF(c, "k_pair_quad_band");
+  kern<<<blocks, 256, smem, c->stream>>>(P, n_rows, rs, rux, ruy, ruz, c->s, c->ux, c->uy, c->uz,
+                                         row_ptr, col, nnz, (T*)val, c->gtab, tab_f32(),
+                                         tab_f64(), c->kdiag, c->prior_m, c->d_flags, c->fgrid,
+                                         row_field);
+}
+
 gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, const double* rux,
                           const double* ruy, const double* ruz, const int32_t* row_field,
                           const int64_t* row_ptr, const int32_t* col, int64_t nnz, void* val,
@@ -421,7 +573,10 @@ gm_status pair_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, const dou
   QuadParams P = quad_params(c, symmetric);
   const int Q = c->cfg.n_nodes;
   const bool f32 = c->cfg.precision == GM_PREC_FP32;
-  if (Q <= 32) {
+  if (c->cfg.quad_rule == GM_QUAD_BAND) {
+    if (f32) launch_pair_band<float>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
+    else launch_pair_band<double>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
+  } else if (Q <= 32) {
     if (f32) launch_pair<float, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
     else launch_pair<double, 1>(c, P, n_rows, rs, rux, ruy, ruz, row_field, row_ptr, col, nnz, val);
   } else if (Q <= 64) {
@@ -463,6 +618,21 @@ gm_status self_quadrature(gm_ctx* c, int64_t n_rows, const double* rs, double* k
   const int Q = c->cfg.n_nodes;
   const bool f32 = c->cfg.precision == GM_PREC_FP32;
   int blocks = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 8 * sm_count(c));
+  if (c->cfg.quad_rule == GM_QUAD_BAND) {
+    const size_t smem = band_smem(f32);
+    GM_PROF(c, "k_self_quad_band");
+    if (f32) {
+      cudaFuncSetAttribute(k_self_quad_band<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+      k_self_quad_band<float><<<blocks, 256, smem, c->stream>>>(P, n_rows, rs, c->gtab,
+                                                                tab_f32(), tab_f64(), kss);
+    } else {
+      k_self_quad_band<double><<<blocks, 256, 0, c->stream>>>(P, n_rows, rs, c->gtab, tab_f32(),
+                                                              tab_f64(), kss);
+    }
+    GM_LAUNCH_CHECK(c);
+    return GM_OK;
+  }
 #define GM_SELF(T, K)                                                                     \
   k_self_quad<T, K><<<blocks, 256, 0, c->stream>>>(P, n_rows, rs, c->gl_zeta, c->gl_w, \
                                                     c->gtab, tab_f32(), tab_f64(), kss)
@@ -551,6 +721,39 @@ __global__ void __launch_bounds__(256) k_pairlist_quad(
   }
 }
 
+// Band-rule counterpart of k_pairlist_quad.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pairlist_quad_band(
+    QuadParams P, int64_t n, const double* __restrict__ si, const double* __restrict__ sj,
+    const double* __restrict__ chord, double* __restrict__ out, const void* __restrict__ gtab,
+    TabF32 tf, TabF64 td) {
+  extern __shared__ unsigned char smem[];
+  const GLook<T> g = band_lookup<T>(gtab, tf, td, smem);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = warp; p < n; p += nwarps) {
+    const double R = band_R_warp<T>(si[p] * P.inv_L0, sj[p] * P.inv_L0, chord[p] * chord[p], g,
+                                    lane);
+    if (lane == 0) out[p] = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
+  }
+}
+
+template <typename T>
+static void launch_pairlist_band(gm_ctx* c, const QuadParams& P, int64_t n, const double* si,
+                                 const double* sj, const double* chord, double* out) {
+  const size_t smem = band_smem(sizeof(T) == 4);
+  auto kern = k_pairlist_quad_band<T>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  int blocks = std::max(1, per_sm) * sm_count(c);
+  blocks = (int)std::min<int64_t>(blocks, std::max<int64_t>(1, ceil_div(n * 32, 256)));
+  kern<<<blocks, 256, smem, c->stream>>>(P, n, si, sj, chord, out, c->gtab, tab_f32(),
+                                         tab_f64());
+}
+
 template <typename T, int KPL>
 static void launch_pairlist(gm_ctx* c, const QuadParams& P, int64_t n, const double* si,
                             const double* sj, const double* chord, double* out) {
@@ -574,6 +777,13 @@ gm_status pairlist_quadrature(gm_ctx* c, int64_t n, const double* si, const doub
   QuadParams P = quad_params(c, false);
   const int Q = c->cfg.n_nodes;
   const bool f32 = c->cfg.precision == GM_PREC_FP32;
+  if (c->cfg.quad_rule == GM_QUAD_BAND) {
+    GM_PROF(c, "k_pairlist_quad_band");
+    if (f32) launch_pairlist_band<float>(c, P, n, si, sj, chord, out);
+    else launch_pairlist_band<double>(c, P, n, si, sj, chord, out);
+    GM_LAUNCH_CHECK(c);
+    return GM_OK;
+  }
   GM_PROF(c, "k_pairlist_quad");
   if (Q <= 32) {
     if (f32) launch_pairlist<float, 1>(c, P, n, si, sj, chord, out);

@@ -24,6 +24,7 @@ FORM_LOGNORMAL, FORM_LINEAR = 0, 1
 TAPER_WENDLAND, TAPER_HARD = 0, 1
 LIK_GAUSS_IN_A, LIK_GAUSS_IN_LNA = 0, 1
 COV_QUADRATURE, COV_SURROGATE = 0, 1
+QUAD_GL, QUAD_BAND = 0, 1
 
 STATUS = {0: "GM_OK", 1: "GM_E_INVAL", 2: "GM_E_NOMEM", 3: "GM_E_CUDA", 4: "GM_E_NOT_SPD",
           5: "GM_E_NOCONV", 6: "GM_E_NONFINITE", 7: "GM_E_TIMEOUT", 8: "GM_E_STATE"}
@@ -52,7 +53,8 @@ class Config(C.Structure):
                 ("cg_max_iter", C.c_int32), ("damping", C.c_double), ("vc_floor", C.c_double),
                 ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("warm_start", C.c_int32),
                 ("cov_source", C.c_int32), ("deflate", C.c_int32),
-                ("surrogate_gate", C.c_double), ("probe_factor", C.c_double)]
+                ("surrogate_gate", C.c_double), ("probe_factor", C.c_double),
+                ("quad_rule", C.c_int32)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

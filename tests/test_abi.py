@@ -40,10 +40,11 @@ def test_status_strings_and_defaults(L):
     assert cfg.sigma2 == 1.0 and cfg.outer_scale_pc == 20.0 and cfg.cutoff_pc == 60.0
     assert cfg.precision == gm.PREC_FP64 and cfg.taper == gm.TAPER_WENDLAND
     assert cfg.warm_start == 1 and cfg.rhs_panel == 0
-    assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2 + 4 * 2 + 8 + 8
+    assert C.sizeof(gm.Config) == 8 * 4 + 4 * 6 + 8 * 3 + 4 * 2 + 4 * 2 + 8 + 8 + 8
     assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-4
     assert cfg.probe_factor == 0.0        # exact variances unless asked
     assert cfg.deflate == 0
+    assert cfg.quad_rule == gm.QUAD_GL
 
 
 def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
@@ -58,9 +59,12 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
     for field, bad in (("sigma2", -1.0), ("n_nodes", 1), ("damping", 0.0), ("cg_tol", 0.0),
                        ("precision", 7), ("outer_scale_pc", float("nan")), ("warm_start", 2),
                        ("probe_factor", -1.0), ("probe_factor", float("inf")),
-                       ("deflate", 5), ("deflate", -64)):
+                       ("deflate", 5), ("deflate", -64), ("quad_rule", 2)):
         c2 = gm.default_config(**{field: bad})
         assert L.gm_ep_init(C.byref(h), C.byref(c2), 4, x, x, x, x, x, None, None) == 1, field
+    # the band rule with the surrogate source is not offered
+    c3 = gm.default_config(quad_rule=gm.QUAD_BAND, cov_source=gm.COV_SURROGATE)
+    assert L.gm_ep_init(C.byref(h), C.byref(c3), 4, x, x, x, x, x, None, None) == 1
     assert not h.value
     # several fields: field ids required, FP32 form only, positive field scales
     fid = (C.c_int32 * 4)(0, 1, 0, 1)
