@@ -69,6 +69,10 @@ def parse():
                         "share one solve (0 = exact, one solve per star)")
     p.add_argument("--deflate", type=int, default=64, choices=[0, 64],
                    help="deflation vectors of the FP32 variance preconditioner (0 = Jacobi)")
+    p.add_argument("--quad", default="gl", choices=["gl", "band"],
+                   help="node rule of the covariance quadrature: gl = the workload's "
+                        "Gauss-Legendre nodes per sightline (bench line), band = the "
+                        "converged band rule (difference/mean coordinates, graded panels)")
     p.add_argument("--no-exact", action="store_true",
                    help="skip the one-step exact-variance comparison")
     p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4_fields", "sightlines"],
@@ -395,8 +399,10 @@ def run_gpu(a):
     cat = make_catalogue(WORKLOAD, n=a.n, seed=rank)
     n = len(cat["s"])
     prec = gm.PREC_FP32 if a.precision == "fp32" else gm.PREC_FP64
+    quad = gm.QUAD_BAND if a.quad == "band" else gm.QUAD_GL
     cfg = gm.config_from_catalogue(cat, precision=prec, probe_factor=a.probe, deflate=a.deflate,
-                                   cg_tol=1e-6 if a.precision == "fp32" else 1e-10)
+                                   cg_tol=1e-6 if a.precision == "fp32" else 1e-10,
+                                   quad_rule=quad)
     D = {k: torch.tensor(cat[k], dtype=torch.float64, device=dev)
          for k in ("l", "b", "s", "A_obs", "A_sigma")}
     ctx = gm.ep_init(cfg, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"])
@@ -459,7 +465,7 @@ def run_gpu(a):
     exact = None
     if a.probe > 0 and not a.no_exact:
         cfg_x = gm.config_from_catalogue(cat, precision=prec, probe_factor=0.0,
-                                         deflate=a.deflate, cg_tol=cfg.cg_tol)
+                                         deflate=a.deflate, cg_tol=cfg.cg_tol, quad_rule=quad)
         mu_x = torch.empty_like(mu)
         var_x = torch.empty_like(var)
         with gm.ep_init(cfg_x, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"]) as cx:
@@ -541,6 +547,9 @@ def run_gpu(a):
                           "preconditioner": ("Jacobi + spectral deflation with 64 Ritz vectors "
                                              "of the scaled B (per refresh)" if a.deflate
                                              and a.precision == "fp32" else "Jacobi"),
+                          "quadrature": ("band rule (difference/mean coordinates, graded "
+                                         "panels, converged)" if a.quad == "band" else
+                                         f"{cfg.n_nodes} Gauss-Legendre nodes per sightline"),
                           "l2": "inputs (CSR + panels) larger than L2; 256 MiB write between steps",
                           "parallelism": f"replicas x{ws}"},
                "pairs_per_s": pairs_per_s, "cov_ms": 1e3 * t_cov,
