@@ -271,6 +271,31 @@ gm_status gm_monotone_sample(gm_ctx* ctx, int64_t nsl, int32_t m, const double* 
                              const double* cov, const double* momenta, int32_t n_burn,
                              int32_t n_samples, double* samples_out, int64_t* hits_out);
 
+/* Posterior of the log-extinction u at R inducing points under the paper's
+ * partially independent conditional approximation (Sect. 4.1, simplified
+ * case; App. B): the stars are split into sub-catalogues that are
+ * conditionally independent given u, each with the exact GP conditional
+ * a_k | u ~ N(m_k + A_k (u - mu_u), K_kk - A_k K_uk), A_k = K_ku K_uu^-1, and
+ * a Gaussian observation of each a_n.  Block-site EP over u reaches its fixed
+ * point in one parallel sweep here (every factor is Gaussian), so the result
+ * is the PITC posterior:
+ *   cov = (K_uu^-1 + sum_k A_k^T C_k^-1 A_k)^-1,
+ *   mean = cov (K_uu^-1 mu_u + sum_k A_k^T C_k^-1 (a~_k - m_k + A_k mu_u)),
+ * C_k = K_kk - A_k K_uk + diag(sigma_k^2).  K_kk are the stored entries of K
+ * (gm_build_cov); K_ku, K_uu and the prior mean mu_u at the inducing points
+ * come from the same quadrature, cutoff and taper.
+ * block_of: sub-catalogue of each star, caller order, int32 in
+ * [0, n_blocks), host or device; at most 8192 stars per sub-catalogue.
+ * l, b, s: the R inducing points (radians, pc; 1 <= R <= 4096).
+ * mean_out: R; cov_out: R x R row-major; host or device.
+ * Needs a single-field FP64 context with GM_LIK_GAUSS_IN_LNA (the stars'
+ * observations are then a~ = ln A_obs with standard deviation obs_sigma) and
+ * the covariance built (else GM_E_STATE).  GM_E_NOT_SPD when K_uu, a C_k or
+ * the posterior precision has no Cholesky factor. */
+gm_status gm_pic_posterior(gm_ctx* ctx, int32_t n_blocks, const int32_t* block_of, int64_t R,
+                           const double* l, const double* b, const double* s,
+                           double* mean_out, double* cov_out);
+
 /* Marginal posterior mean and variance of ln A for every star under the
  * current sites (refreshed if the sites changed).  Length n each. */
 gm_status gm_get_posterior(gm_ctx* ctx, double* mean_out, double* var_out);

@@ -1090,6 +1090,81 @@ gm_status gm_monotone_sample(gm_ctx* c, int64_t nsl, int32_t m, const double* me
   return GM_OK;
 }
 
+gm_status gm_pic_posterior(gm_ctx* c, int32_t n_blocks, const int32_t* block_of, int64_t R,
+                           const double* l, const double* b, const double* s,
+                           double* mean_out, double* cov_out) {
+  if (!c || n_blocks < 1 || !block_of || R < 1 || R > kMaxPicInducing || !l || !b || !s ||
+      !mean_out || !cov_out)
+    return GM_E_INVAL;
+  if (!c->built) return set_error(c, GM_E_STATE, "gm_build_cov must come first");
+  if (c->n_fields > 1 || c->cfg.precision != GM_PREC_FP64 ||
+      c->cfg.likelihood != GM_LIK_GAUSS_IN_LNA)
+    return set_error(c, GM_E_STATE,
+                     "the PIC posterior needs a single-field FP64 context with the Gaussian "
+                     "likelihood in ln A");
+  c->launches = 0;
+  const int64_t n = c->n;
+  // block of each internal star (host)
+  std::vector<int32_t> blk(n);
+  std::vector<int64_t> perm(n);
+  if (is_device_ptr(block_of)) {
+    GM_CUDA_CHECK(c, cudaMemcpy(blk.data(), block_of, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(blk.data(), block_of, n * sizeof(int32_t));
+  }
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(perm.data(), c->perm, n * sizeof(int64_t),
+                                   cudaMemcpyDeviceToHost, c->stream));
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+  std::vector<int32_t> blk_int(n);
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t v = blk[perm[k]];
+    if (v < 0 || v >= n_blocks) return set_error(c, GM_E_INVAL, "block id out of range");
+    blk_int[k] = v;
+  }
+  const size_t nb_ = R * sizeof(double);
+  // l, b, s, ux, uy, uz (R); mean (R); cov (R^2)
+  ScopedDev buf(c, 7 * nb_ + R * nb_);
+  if (!buf.p) return set_error(c, GM_E_NOMEM, "inducing arrays");
+  double *ql = (double*)buf.p, *qb = ql + R, *qs = qb + R, *ux = qs + R, *uy = ux + R,
+         *uz = uy + R, *mean = uz + R, *cov = mean + R;
+  gm_status st;
+  if ((st = copy_in(c, ql, l, nb_)) != GM_OK || (st = copy_in(c, qb, b, nb_)) != GM_OK ||
+      (st = copy_in(c, qs, s, nb_)) != GM_OK)
+    return st;
+  GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned), c->stream));
+  GM_PROF(c, "k_check_inputs");
+  k_check_inputs<<<eb(c, R), 256, 0, c->stream>>>(R, qs, qs, qs, ql, qb, c->d_flags + 1);
+  GM_LAUNCH_CHECK(c);
+  {
+    unsigned* h = (unsigned*)c->h_pinned;
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                     c->stream));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    if (*h) return set_error(c, GM_E_INVAL, "inducing distances must be finite and > 0");
+  }
+  if ((st = unit_vectors(c, R, ql, qb, ux, uy, uz)) != GM_OK) return st;
+  if ((st = pic_posterior(c, (int)R, qs, ux, uy, uz, blk_int.data(), n_blocks, mean, cov)) !=
+      GM_OK)
+    return st;
+  {
+    unsigned* h = (unsigned*)c->h_pinned;
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                     c->stream));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    const unsigned f = *h;
+    if (f) GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream));
+    if (f & kFlagNonFinite) return set_error(c, GM_E_NONFINITE, "non-finite covariance value");
+    if (f & kFlagNotSPD)
+      return set_error(c, GM_E_NOT_SPD,
+                       "K_uu, a sub-catalogue's conditional covariance or the posterior "
+                       "precision of u has no Cholesky factor");
+  }
+  if ((st = copy_out(c, mean_out, mean, nb_)) != GM_OK) return st;
+  if ((st = copy_out(c, cov_out, cov, R * nb_)) != GM_OK) return st;
+  c->stats.kernel_launches = c->launches;
+  return GM_OK;
+}
+
 gm_status gm_profile(gm_ctx* c, int32_t enable) {
   if (!c) return GM_E_INVAL;
   prof_collect(c);

@@ -15,6 +15,8 @@ namespace gm {
 constexpr int kGH = 64;          // Gauss-Hermite nodes of the tilted rule
 constexpr int kMaxNodes = 128;   // Gauss-Legendre nodes per sightline (max)
 constexpr int kMaxSightlinePoints = 1024;  // points of one sightline (joint predictive, sampler)
+constexpr int kMaxPicBlock = 8192;         // stars of one sub-catalogue (dense PIC blocks)
+constexpr int kMaxPicInducing = 4096;      // inducing points of the PIC posterior
 
 // Device status flags (OR-ed by kernels, read by the host after a call).
 enum : unsigned {
@@ -347,6 +349,14 @@ gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
 gm_status site_update(gm_ctx* c, double* max_delta, int64_t* skipped);
 
 void workspace_free(gm_ctx* c);
+
+// PITC / PIC posterior of u at R inducing points (gm_pic.cu): us, ux, uy, uz
+// the inducing distances and unit vectors (device), h_block_int the block of
+// each internal star (host), mean (R) and cov (R x R) device outputs.
+// FP64 single-field contexts with the covariance built.  Synchronises.
+gm_status pic_posterior(gm_ctx* c, int R, const double* us, const double* ux, const double* uy,
+                        const double* uz, const int32_t* h_block_int, int nb, double* mean,
+                        double* cov);
 
 // Exact-HMC samples of each sightline's predictive truncated to a
 // non-decreasing sequence (gm_sightline.cu).  Device arrays in the caller

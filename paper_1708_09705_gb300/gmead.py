@@ -37,7 +37,7 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_site_update_noalloc", "gm_surrogate_param_count", "gm_surrogate_set_params",
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
            "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries", "gm_predict_pairs",
-           "gm_predict_sightlines", "gm_monotone_sample"]
+           "gm_predict_sightlines", "gm_monotone_sample", "gm_pic_posterior"]
 
 
 class GmError(RuntimeError):
@@ -105,6 +105,7 @@ def lib():
         L.gm_predict_pairs.argtypes = [vp, i64, vp, vp, vp, dbl, vp, vp, vp]
         L.gm_predict_sightlines.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
         L.gm_monotone_sample.argtypes = [vp, i64, i32, vp, vp, vp, i32, i32, vp, vp]
+        L.gm_pic_posterior.argtypes = [vp, i32, vp, i64, vp, vp, vp, vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.gm_stream.argtypes = [vp]
@@ -259,6 +260,19 @@ class Context:
                                              momenta.ctypes.data, int(n_burn), ns,
                                              out.ctypes.data, hits.ctypes.data))
         return out, hits
+
+    def pic_posterior(self, block_of, l, b, s):
+        """PITC / PIC posterior of ln A at the inducing points (l, b, s) with
+        the stars split into sub-catalogues block_of (caller order):
+        (mean (R,), covariance (R, R))."""
+        blk = np.ascontiguousarray(block_of, dtype=np.int32)
+        l, b, s = (np.ascontiguousarray(v, dtype=np.float64) for v in (l, b, s))
+        R = len(s)
+        mean, cov = np.empty(R), np.empty((R, R))
+        self._check(lib().gm_pic_posterior(self._h, int(blk.max()) + 1, blk.ctypes.data, R,
+                                           l.ctypes.data, b.ctypes.data, s.ctypes.data,
+                                           mean.ctypes.data, cov.ctypes.data))
+        return mean, cov
 
     # ---- state
     def _pair_out(self, fn, out):
