@@ -115,3 +115,156 @@ GM_HD inline void inverse_col(const double* L, int R, int c, double* col, int64_
 }
 
 }  // namespace gmdense
+
+namespace gmpic {
+
+// Sub-catalogue lists (host): blk[k] = block of star k.  boff[nb + 1]: first
+// row of each block in block order; coff[nb + 1]: offset of each block's
+// N_k x N_k matrix; bidx[n]: star of each block-order row (stars of a block
+// in increasing index); rowpos[n]: block-order row of each star; dims[nb]:
+// N_k.  False when a block holds more than max_block stars.
+inline bool block_lists(int64_t n, const int32_t* blk, int nb, int max_block, int64_t* boff,
+                        int64_t* coff, int64_t* bidx, int32_t* rowpos, int32_t* dims) {
+  for (int k = 0; k <= nb; ++k) boff[k] = coff[k] = 0;
+  for (int64_t k = 0; k < n; ++k) boff[blk[k] + 1]++;
+  for (int k = 0; k < nb; ++k) {
+    dims[k] = (int32_t)boff[k + 1];
+    if (dims[k] > max_block) return false;
+    boff[k + 1] += boff[k];
+    coff[k + 1] = coff[k] + (int64_t)dims[k] * dims[k];
+  }
+  for (int k = 0; k < nb; ++k) dims[k] = 0;  // fill counters
+  for (int64_t k = 0; k < n; ++k) {
+    const int b = blk[k];
+    const int64_t r = boff[b] + dims[b]++;
+    bidx[r] = k;
+    rowpos[k] = (int32_t)r;
+  }
+  return true;
+}
+
+// Pair (a, b), a >= b, of the p-th lower-triangle entry in row-major order.
+GM_HD inline void tri_index(int64_t p, int* a, int* b) {
+  int64_t r = (int64_t)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+  while (r * (r + 1) / 2 > p) --r;
+  while ((r + 1) * (r + 2) / 2 <= p) ++r;
+  *a = (int)r;
+  *b = (int)(p - r * (r + 1) / 2);
+}
+
+// Quadrature inputs of inducing pair p: distances and chord |u_a - u_b|.
+GM_HD inline void upair(int64_t p, const double* us, const double* ux, const double* uy,
+                        const double* uz, double* si, double* sj, double* ch) {
+  int a, b;
+  tri_index(p, &a, &b);
+  const double dx = ux[a] - ux[b], dy = uy[a] - uy[b], dz = uz[a] - uz[b];
+  si[p] = us[a];
+  sj[p] = us[b];
+  ch[p] = sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// K_uu[a][b] (lower) from the pair's untapered value kp[p], tapered by the
+// 3-D separation as K is (Wendland: taper 0, hard cutoff: 1), and the prior
+// mean at inducing point a when a == b (lognormal: form 0, first order: 1).
+GM_HD inline void kuu_entry(int64_t p, int R, double inv_cut, int taper, int form,
+                            double log_rho_bar, double sigma2, const double* us, const double* ch,
+                            const double* kp, double* Kuu, double* mu_u) {
+  int a, b;
+  tri_index(p, &a, &b);
+  const double sa = us[a], sb = us[b], ds = sa - sb;
+  const double d = sqrt(ds * ds + sa * sb * ch[p] * ch[p]);
+  const double h = d * inv_cut;
+  double w = h <= 1.0 ? 1.0 : 0.0;
+  if (taper == 0) {
+    const double u = 1.0 - h;
+    w = h < 1.0 ? u * u * u * u * (4.0 * h + 1.0) : 0.0;
+  }
+  const double v = a == b ? kp[p] : w * kp[p];
+  Kuu[(int64_t)a * R + b] = v;
+  if (a == b) mu_u[a] = log_rho_bar + log(sa) - (form == 0 ? 0.5 * v : 0.5 * sigma2);
+}
+
+// Entry e of the inducing points' CSR over the stars (row = inducing point,
+// column = internal star) into row rowpos[star] of K_ku (block order).
+GM_HD inline void kku_entry(int64_t e, int R, const int64_t* qptr, const int32_t* qcol,
+                            const double* qval, const int32_t* rowpos, double* Kku) {
+  int64_t lo = 0, hi = R;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (qptr[mid] <= e) lo = mid; else hi = mid;
+  }
+  Kku[(int64_t)rowpos[qcol[e]] * R + lo] = qval[e];
+}
+
+// Stored K_ij (0 when the pair is beyond the cutoff); columns sorted per row.
+GM_HD inline double csr_entry(const int64_t* row_ptr, const int32_t* col, const double* val,
+                              int64_t i, int32_t j) {
+  int64_t lo = row_ptr[i], hi = row_ptr[i + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (col[mid] < j) lo = mid + 1; else hi = mid;
+  }
+  return (lo < row_ptr[i + 1] && col[lo] == j) ? val[lo] : 0.0;
+}
+
+// Entry e of the concatenated blocks' C_k (lower triangles only).
+GM_HD inline void cmat_entry(int64_t e, int nb, const int64_t* coff, const int64_t* boff, int R,
+                             const int64_t* bidx, const int64_t* row_ptr, const int32_t* col,
+                             const double* val, const double* A, const double* Kku,
+                             const double* sig, double* C) {
+  int lo = 0, hi = nb;  // block k: coff[k] <= e < coff[k + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (coff[mid] <= e) lo = mid; else hi = mid;
+  }
+  const int k = lo;
+  const int64_t N = boff[k + 1] - boff[k];
+  const int64_t loc = e - coff[k];
+  const int64_t a = loc / N, b = loc - a * N;
+  if (b > a) return;
+  const int64_t ra = boff[k] + a, rb = boff[k] + b;
+  const int64_t ia = bidx[ra], ib = bidx[rb];
+  const double kab = csr_entry(row_ptr, col, val, ia, (int32_t)ib);
+  C[e] = gmdense::c_entry(kab, A + ra * R, Kku + rb * R, R, a == b, sig[ia] * sig[ia]);
+}
+
+// Task t of the forward solves: block t / (R + 1), column t % (R + 1) (the
+// last column is the right-hand side y).
+GM_HD inline void fsolve_task(int64_t t, int R, const int64_t* coff, const int64_t* boff,
+                              const double* C, double* X, double* yv) {
+  const int k = (int)(t / (R + 1));
+  const int c = (int)(t - (int64_t)k * (R + 1));
+  const int N = (int)(boff[k + 1] - boff[k]);
+  if (N == 0) return;
+  const double* L = C + coff[k];
+  if (c < R) gmdense::solve_lower(L, N, N, X + boff[k] * R + c, R);
+  else gmdense::solve_lower(L, N, N, yv + boff[k], 1);
+}
+
+// Task e < R^2: Lambda (lower); e >= R^2: eta.
+GM_HD inline void lambda_task(int64_t e, int64_t n, int R, const double* X, const double* yv,
+                              double* Lam, double* eta) {
+  if (e < (int64_t)R * R) {
+    const int r1 = (int)(e / R), r2 = (int)(e - (int64_t)r1 * R);
+    if (r2 <= r1) Lam[e] = gmdense::lambda_entry(X, n, R, r1, r2);
+  } else {
+    const int r = (int)(e - (int64_t)R * R);
+    eta[r] = gmdense::eta_entry(X, yv, n, R, r);
+  }
+}
+
+// Task e < R^2: P = K_uu^-1 + Lambda (lower); e >= R^2: h = K_uu^-1 mu_u + eta.
+GM_HD inline void prec_task(int64_t e, int R, const double* Kinv, const double* Lam,
+                            const double* mu_u, const double* eta, double* P, double* h) {
+  if (e < (int64_t)R * R) {
+    const int r1 = (int)(e / R), r2 = (int)(e - (int64_t)r1 * R);
+    if (r2 <= r1) P[e] = Kinv[e] + Lam[e];
+  } else {
+    const int r = (int)(e - (int64_t)R * R);
+    double v = eta[r];
+    for (int c = 0; c < R; ++c) v += Kinv[(int64_t)r * R + c] * mu_u[c];
+    h[r] = v;
+  }
+}
+
+}  // namespace gmpic

@@ -52,15 +52,6 @@ __global__ void __launch_bounds__(256) k_pic_chol(double* __restrict__ base,
   if (bad && threadIdx.x == 0) atomicOr(flags, kFlagNotSPD);
 }
 
-// Pair (a, b), a >= b, of the p-th lower-triangle entry in row-major order.
-__device__ __forceinline__ void tri_index(int64_t p, int* a, int* b) {
-  int64_t r = (int64_t)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-  while (r * (r + 1) / 2 > p) --r;
-  while ((r + 1) * (r + 2) / 2 <= p) ++r;
-  *a = (int)r;
-  *b = (int)(p - r * (r + 1) / 2);
-}
-
 // Quadrature inputs of the inducing pairs (a, b), a >= b, diagonal included.
 __global__ void k_pic_upairs(int R, const double* __restrict__ us, const double* __restrict__ ux,
                              const double* __restrict__ uy, const double* __restrict__ uz,
@@ -69,12 +60,7 @@ __global__ void k_pic_upairs(int R, const double* __restrict__ us, const double*
   const int64_t np = (int64_t)R * (R + 1) / 2;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
        p += (int64_t)gridDim.x * blockDim.x) {
-    int a, b;
-    tri_index(p, &a, &b);
-    const double dx = ux[a] - ux[b], dy = uy[a] - uy[b], dz = uz[a] - uz[b];
-    si[p] = us[a];
-    sj[p] = us[b];
-    ch[p] = sqrt(dx * dx + dy * dy + dz * dz);
+    gmpic::upair(p, us, ux, uy, uz, si, sj, ch);
   }
 }
 
@@ -87,20 +73,9 @@ __global__ void k_pic_kuu(int R, double inv_cut, int taper, int form, double log
   const int64_t np = (int64_t)R * (R + 1) / 2;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
        p += (int64_t)gridDim.x * blockDim.x) {
-    int a, b;
-    tri_index(p, &a, &b);
-    const double sa = us[a], sb = us[b], ds = sa - sb;
-    const double d = sqrt(ds * ds + sa * sb * ch[p] * ch[p]);
-    const double h = d * inv_cut;
-    double w = h <= 1.0 ? 1.0 : 0.0;
-    if (taper == GM_TAPER_WENDLAND) {
-      const double u = 1.0 - h;
-      w = h < 1.0 ? u * u * u * u * (4.0 * h + 1.0) : 0.0;
-    }
-    const double v = a == b ? kp[p] : w * kp[p];
-    Kuu[(int64_t)a * R + b] = v;
-    if (a == b)
-      mu_u[a] = log_rho_bar + log(sa) - (form == GM_FORM_LOGNORMAL ? 0.5 * v : 0.5 * sigma2);
+    gmpic::kuu_entry(p, R, inv_cut, taper == GM_TAPER_WENDLAND ? 0 : 1,
+                     form == GM_FORM_LOGNORMAL ? 0 : 1, log_rho_bar, sigma2, us, ch, kp, Kuu,
+                     mu_u);
   }
 }
 
@@ -111,12 +86,7 @@ __global__ void k_pic_kku(int R, const int64_t* __restrict__ qptr,
                           double* __restrict__ Kku) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < qnnz;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t lo = 0, hi = R;
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (qptr[mid] <= e) lo = mid; else hi = mid;
-    }
-    Kku[(int64_t)rowpos[qcol[e]] * R + lo] = qval[e];
+    gmpic::kku_entry(e, R, qptr, qcol, qval, rowpos, Kku);
   }
 }
 
@@ -125,19 +95,6 @@ __global__ void k_pic_arow(int64_t n, int R, const double* __restrict__ Lu,
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x)
     gmdense::a_row(Lu, R, Kku + j * R, A + j * R);
-}
-
-// Stored K_ij (0 when the pair is beyond the cutoff).
-__device__ __forceinline__ double csr_entry(const int64_t* __restrict__ row_ptr,
-                                            const int32_t* __restrict__ col,
-                                            const double* __restrict__ val, int64_t i,
-                                            int32_t j) {
-  int64_t lo = row_ptr[i], hi = row_ptr[i + 1];
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (col[mid] < j) lo = mid + 1; else hi = mid;
-  }
-  return (lo < row_ptr[i + 1] && col[lo] == j) ? val[lo] : 0.0;
 }
 
 // Lower triangle of every block's C_k = K_kk - A_k K_uk + diag(sigma^2).
@@ -150,20 +107,7 @@ __global__ void k_pic_cmat(int nb, const int64_t* __restrict__ coff,
   const int64_t total = coff[nb];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = nb;  // block k: coff[k] <= e < coff[k + 1]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (coff[mid] <= e) lo = mid; else hi = mid;
-    }
-    const int k = lo;
-    const int64_t N = boff[k + 1] - boff[k];
-    const int64_t loc = e - coff[k];
-    const int64_t a = loc / N, b = loc - a * N;
-    if (b > a) continue;
-    const int64_t ra = boff[k] + a, rb = boff[k] + b;
-    const int64_t ia = bidx[ra], ib = bidx[rb];
-    const double kab = csr_entry(row_ptr, col, val, ia, (int32_t)ib);
-    C[e] = gmdense::c_entry(kab, A + ra * R, Kku + rb * R, R, a == b, sig[ia] * sig[ia]);
+    gmpic::cmat_entry(e, nb, coff, boff, R, bidx, row_ptr, col, val, A, Kku, sig, C);
   }
 }
 
@@ -183,13 +127,7 @@ __global__ void k_pic_fsolve(int nb, int R, const int64_t* __restrict__ coff,
   const int64_t total = (int64_t)nb * (R + 1);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(t / (R + 1));
-    const int c = (int)(t - (int64_t)k * (R + 1));
-    const int N = (int)(boff[k + 1] - boff[k]);
-    if (N == 0) continue;
-    const double* L = C + coff[k];
-    if (c < R) gmdense::solve_lower(L, N, N, X + boff[k] * R + c, R);
-    else gmdense::solve_lower(L, N, N, yv + boff[k], 1);
+    gmpic::fsolve_task(t, R, coff, boff, C, X, yv);
   }
 }
 
@@ -200,13 +138,7 @@ __global__ void k_pic_lambda(int64_t n, int R, const double* __restrict__ X,
   const int64_t total = (int64_t)R * R + R;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < (int64_t)R * R) {
-      const int r1 = (int)(e / R), r2 = (int)(e - (int64_t)r1 * R);
-      if (r2 <= r1) Lam[e] = gmdense::lambda_entry(X, n, R, r1, r2);
-    } else {
-      const int r = (int)(e - (int64_t)R * R);
-      eta[r] = gmdense::eta_entry(X, yv, n, R, r);
-    }
+    gmpic::lambda_task(e, n, R, X, yv, Lam, eta);
   }
 }
 
@@ -223,15 +155,7 @@ __global__ void k_pic_prec(int R, const double* __restrict__ Kinv, const double*
   const int64_t total = (int64_t)R * R + R;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < (int64_t)R * R) {
-      const int r1 = (int)(e / R), r2 = (int)(e - (int64_t)r1 * R);
-      if (r2 <= r1) P[e] = Kinv[e] + Lam[e];
-    } else {
-      const int r = (int)(e - (int64_t)R * R);
-      double v = eta[r];
-      for (int c = 0; c < R; ++c) v += Kinv[(int64_t)r * R + c] * mu_u[c];
-      h[r] = v;
-    }
+    gmpic::prec_task(e, R, Kinv, Lam, mu_u, eta, P, h);
   }
 }
 
@@ -253,24 +177,11 @@ gm_status pic_posterior(gm_ctx* c, int R, const double* us, const double* ux, co
                         double* cov) {
   const int64_t n = c->n;
   // ---- block lists (host): stars of block k in internal order
-  std::vector<int64_t> boff(nb + 1, 0), coff(nb + 1, 0), bidx(n);
+  std::vector<int64_t> boff(nb + 1), coff(nb + 1), bidx(n);
   std::vector<int32_t> rowpos(n), dims(nb);
-  for (int64_t k = 0; k < n; ++k) boff[h_block_int[k] + 1]++;
-  for (int k = 0; k < nb; ++k) {
-    dims[k] = (int32_t)boff[k + 1];
-    if (dims[k] > kMaxPicBlock)
-      return set_error(c, GM_E_INVAL, "a sub-catalogue has more than 8192 stars");
-    boff[k + 1] += boff[k];
-    coff[k + 1] = coff[k] + (int64_t)dims[k] * dims[k];
-  }
-  {
-    std::vector<int64_t> fill(boff.begin(), boff.end() - 1);
-    for (int64_t k = 0; k < n; ++k) {
-      const int64_t r = fill[h_block_int[k]]++;
-      bidx[r] = k;
-      rowpos[k] = (int32_t)r;
-    }
-  }
+  if (!gmpic::block_lists(n, h_block_int, nb, kMaxPicBlock, boff.data(), coff.data(), bidx.data(),
+                          rowpos.data(), dims.data()))
+    return set_error(c, GM_E_INVAL, "a sub-catalogue has more than 8192 stars");
   const int64_t RR = (int64_t)R * R;
   const int64_t npair = (int64_t)R * (R + 1) / 2;
   // device buffers

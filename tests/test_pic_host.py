@@ -84,6 +84,53 @@ extern "C" int pic_host(long n, int R, int nb, const long* boff, const double* K
   for (int c = 0; c < R; ++c) inverse_col(Pm.data(), R, c, cov + c, R);
   return 0;
 }
+// the whole device pipeline after the quadrature and neighbour search, in
+// its launch order, from the stars' CSR and the inducing points' CSR
+extern "C" int pic_full_host(long n, int R, int nb, const int32_t* blk, const int64_t* row_ptr,
+                             const int32_t* col, const double* val, const int64_t* qptr,
+                             const int32_t* qcol, const double* qval, long qnnz,
+                             const double* us, const double* ux, const double* uy,
+                             const double* uz, const double* kp, double inv_cut, int taper,
+                             int form, double log_rho_bar, double sigma2, const double* obs,
+                             const double* sig, const double* prior_m, int nt, double* mean,
+                             double* cov, double* si, double* sj, double* ch) {
+  std::vector<int64_t> boff(nb + 1), coff(nb + 1), bidx(n);
+  std::vector<int32_t> rowpos(n), dims(nb);
+  if (!gmpic::block_lists(n, blk, nb, 8192, boff.data(), coff.data(), bidx.data(), rowpos.data(),
+                          dims.data()))
+    return 9;
+  const long RR = (long)R * R, np = (long)R * (R + 1) / 2;
+  std::vector<double> Kuu(RR, 0.0), Lu, mu_u(R), Kku(n * R, 0.0), A(n * R), X, yv(n),
+      C(coff[nb]), Lam(RR), eta(R), Kinv(RR), Pm(RR), h(R);
+  for (long e = 0; e < qnnz; ++e) gmpic::kku_entry(e, R, qptr, qcol, qval, rowpos.data(), Kku.data());
+  for (long p = 0; p < np; ++p) gmpic::upair(p, us, ux, uy, uz, si, sj, ch);
+  for (long p = 0; p < np; ++p)
+    gmpic::kuu_entry(p, R, inv_cut, taper, form, log_rho_bar, sigma2, us, ch, kp, Kuu.data(),
+                     mu_u.data());
+  Lu = Kuu;
+  if (!chol(Lu.data(), R, nt)) return 1;
+  for (long j = 0; j < n; ++j) a_row(Lu.data(), R, Kku.data() + j * R, A.data() + j * R);
+  for (long e = 0; e < coff[nb]; ++e)
+    gmpic::cmat_entry(e, nb, coff.data(), boff.data(), R, bidx.data(), row_ptr, col, val, A.data(),
+                      Kku.data(), sig, C.data());
+  for (int k = 0; k < nb; ++k)
+    if (dims[k] > 0 && !chol(C.data() + coff[k], dims[k], nt)) return 2;
+  for (long j = 0; j < n; ++j)
+    yv[j] = y_entry(obs[bidx[j]], prior_m[bidx[j]], A.data() + j * R, mu_u.data(), R);
+  X = A;
+  for (long t = 0; t < (long)nb * (R + 1); ++t)
+    gmpic::fsolve_task(t, R, coff.data(), boff.data(), C.data(), X.data(), yv.data());
+  for (long e = 0; e < RR + R; ++e) gmpic::lambda_task(e, n, R, X.data(), yv.data(), Lam.data(), eta.data());
+  for (int c = 0; c < R; ++c) inverse_col(Lu.data(), R, c, Kinv.data() + c, R);
+  for (long e = 0; e < RR + R; ++e)
+    gmpic::prec_task(e, R, Kinv.data(), Lam.data(), mu_u.data(), eta.data(), Pm.data(), h.data());
+  if (!chol(Pm.data(), R, nt)) return 3;
+  for (int r = 0; r < R; ++r) mean[r] = h[r];
+  solve_lower(Pm.data(), R, R, mean, 1);
+  solve_lower_t(Pm.data(), R, R, mean, 1);
+  for (int c = 0; c < R; ++c) inverse_col(Pm.data(), R, c, cov + c, R);
+  return 0;
+}
 """
 
 
@@ -102,6 +149,9 @@ def host_lib(tmp_path_factory):
     L.pic_host.argtypes = [C.c_long, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int,
                            vp, vp]
     L.pic_host.restype = C.c_int
+    L.pic_full_host.argtypes = [C.c_long, C.c_int, C.c_int] + [vp] * 7 + [C.c_long] + [vp] * 5 + \
+        [C.c_double, C.c_int, C.c_int, C.c_double, C.c_double] + [vp] * 3 + [C.c_int] + [vp] * 5
+    L.pic_full_host.restype = C.c_int
     return L
 
 
@@ -123,7 +173,7 @@ def setup():
     order = np.argsort(cat["l"])
     groups = [np.sort(g) for g in np.array_split(order, 5)]
     return dict(n=n, R=R, K=cv["K"], m=cv["m"], atil=atil, sig2=sig2, groups=groups,
-                u=np.arange(n, n + R))
+                u=np.arange(n, n + R), cat=cat, li=li, bi=bi, si=si)
 
 
 @pytest.mark.parametrize("nt", [1, 3, 32])
@@ -165,3 +215,62 @@ def test_host_cholesky_phases_detect_indefinite(host_lib, setup):
                            z.ctypes.data, z.ctypes.data, np.ones(1).ctypes.data, 2,
                            np.zeros(R).ctypes.data, np.zeros((R, R)).ctypes.data)
     assert rc == 1
+
+
+def test_host_full_pipeline_from_csr_matches_oracle(host_lib, setup):
+    """From the stars' CSR, the inducing points' CSR over the stars and the
+    inducing pairs' untapered values (the inputs the device gets from its
+    quadrature and neighbour search), in the device's launch order."""
+    from scipy import sparse
+    S = setup
+    K, m, u, R, n = S["K"], S["m"], S["u"], S["R"], S["n"]
+    cat = S["cat"]
+    Ks = sparse.csr_matrix(K[:n, :n])
+    Ks.sort_indices()
+    Kq = sparse.csr_matrix(K[np.ix_(u, np.arange(n))])
+    Kq.sort_indices()
+    row_ptr = Ks.indptr.astype(np.int64)
+    col = Ks.indices.astype(np.int32)
+    val = Ks.data.astype(np.float64)
+    qptr = Kq.indptr.astype(np.int64)
+    qcol = Kq.indices.astype(np.int32)
+    qval = Kq.data.astype(np.float64)
+    blk = np.zeros(n, dtype=np.int32)
+    for k, g in enumerate(S["groups"]):
+        blk[g] = k
+    us = S["si"]
+    uv = O.unit_vectors(S["li"], S["bi"])
+    ux, uy, uz = (np.ascontiguousarray(uv[:, k]) for k in range(3))
+    a_idx, b_idx = [], []
+    for a in range(R):
+        for b in range(a + 1):
+            a_idx.append(a)
+            b_idx.append(b)
+    a_idx, b_idx = np.array(a_idx), np.array(b_idx)
+    chord2 = ((uv[a_idx] - uv[b_idx]) ** 2).sum(1)
+    L0, sig2 = float(cat["outer_scale_pc"]), float(cat["sigma2"])
+    kp = O.K_from_R(O.pair_R(us[a_idx], us[b_idx], chord2,
+                             lambda r: O.g_of_r(r, sig2, L0), int(cat["n_nodes"])),
+                    O.FORM_LOGNORMAL)
+    np_ = len(kp)
+    si, sj, ch = np.zeros(np_), np.zeros(np_), np.zeros(np_)
+    mean, cov = np.zeros(R), np.zeros((R, R))
+    obs = np.ascontiguousarray(S["atil"])
+    sig = np.sqrt(S["sig2"])
+    pm = np.ascontiguousarray(m[:n])
+    rc = host_lib.pic_full_host(
+        n, R, len(S["groups"]), blk.ctypes.data, row_ptr.ctypes.data, col.ctypes.data,
+        val.ctypes.data, qptr.ctypes.data, qcol.ctypes.data, qval.ctypes.data, len(qval),
+        us.ctypes.data, ux.ctypes.data, uy.ctypes.data, uz.ctypes.data, kp.ctypes.data,
+        1.0 / float(cat["cutoff_pc"]), 0, 0, np.log(float(cat["rho_bar"])), sig2,
+        obs.ctypes.data, sig.ctypes.data, pm.ctypes.data, 4, mean.ctypes.data, cov.ctypes.data,
+        si.ctypes.data, sj.ctypes.data, ch.ctypes.data)
+    assert rc == 0
+    np.testing.assert_array_equal(si, us[a_idx])
+    np.testing.assert_array_equal(sj, us[b_idx])
+    np.testing.assert_allclose(ch * ch, chord2, rtol=1e-12, atol=1e-18)
+    blocks = [dict(Kku=K[np.ix_(g, u)], Kkk=K[np.ix_(g, g)], m=m[g], atil=S["atil"][g],
+                   sig2=S["sig2"][g]) for g in S["groups"]]
+    ref_m, ref_c = P.pitc_posterior_direct(K[np.ix_(u, u)], blocks, m[u])
+    np.testing.assert_allclose(mean, ref_m, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(cov, ref_c, rtol=1e-8, atol=1e-12)
