@@ -296,6 +296,19 @@ gm_status gm_pic_posterior(gm_ctx* ctx, int32_t n_blocks, const int32_t* block_o
                            const double* l, const double* b, const double* s,
                            double* mean_out, double* cov_out);
 
+/* PIC predictive of ln A at nq query points (the paper's partially
+ * independent conditional, Sect. 4.1 / App. B), after gm_pic_posterior on
+ * the same context (else GM_E_STATE; gm_build_cov discards the posterior).
+ * A query assigned to sub-catalogue k depends on the other sub-catalogues
+ * only through u: with A_s = k_su K_uu^-1, D = k_sk - K_ku A_s^T, g = C_k^-1 D
+ * and L = A_s - g^T A_k,
+ *   mean = m_s + g^T (a~_k - m_k) + L (mean_u - mu_u),
+ *   var  = k_ss - A_s k_us - g^T D + L cov_u L^T.
+ * q_block: sub-catalogue of each query (int32 in [0, n_blocks)); l, b, s the
+ * queries (radians, pc); mean_out, var_out: nq.  All host or device. */
+gm_status gm_pic_predict(gm_ctx* ctx, int64_t nq, const int32_t* q_block, const double* l,
+                         const double* b, const double* s, double* mean_out, double* var_out);
+
 /* Marginal posterior mean and variance of ln A for every star under the
  * current sites (refreshed if the sites changed).  Length n each. */
 gm_status gm_get_posterior(gm_ctx* ctx, double* mean_out, double* var_out);

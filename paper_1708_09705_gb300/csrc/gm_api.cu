@@ -451,6 +451,7 @@ gm_status gm_ep_init(gm_ctx** out, const gm_config* cfg, int64_t n, const double
 gm_status gm_build_cov(gm_ctx* c, int64_t* nnz_out) {
   if (!c) return GM_E_INVAL;
   c->launches = 0;
+  pic_free(c);  // factors of a PIC posterior over the previous K
   gm_status st = neighbour_csr(c, c->n, c->s, c->ux, c->uy, c->uz, c->field_of, true, c->row_ptr,
                                c->col_buf, &c->nnz, c->diag_pos);
   if (st != GM_OK) return st;
@@ -1122,11 +1123,11 @@ gm_status gm_pic_posterior(gm_ctx* c, int32_t n_blocks, const int32_t* block_of,
     blk_int[k] = v;
   }
   const size_t nb_ = R * sizeof(double);
-  // l, b, s, ux, uy, uz (R); mean (R); cov (R^2)
-  ScopedDev buf(c, 7 * nb_ + R * nb_);
+  // l, b, s, ux, uy, uz (R)
+  ScopedDev buf(c, 6 * nb_);
   if (!buf.p) return set_error(c, GM_E_NOMEM, "inducing arrays");
   double *ql = (double*)buf.p, *qb = ql + R, *qs = qb + R, *ux = qs + R, *uy = ux + R,
-         *uz = uy + R, *mean = uz + R, *cov = mean + R;
+         *uz = uy + R;
   gm_status st;
   if ((st = copy_in(c, ql, l, nb_)) != GM_OK || (st = copy_in(c, qb, b, nb_)) != GM_OK ||
       (st = copy_in(c, qs, s, nb_)) != GM_OK)
@@ -1143,9 +1144,10 @@ gm_status gm_pic_posterior(gm_ctx* c, int32_t n_blocks, const int32_t* block_of,
     if (*h) return set_error(c, GM_E_INVAL, "inducing distances must be finite and > 0");
   }
   if ((st = unit_vectors(c, R, ql, qb, ux, uy, uz)) != GM_OK) return st;
-  if ((st = pic_posterior(c, (int)R, qs, ux, uy, uz, blk_int.data(), n_blocks, mean, cov)) !=
-      GM_OK)
+  if ((st = pic_posterior(c, (int)R, qs, ux, uy, uz, blk_int.data(), n_blocks)) != GM_OK) {
+    pic_free(c);
     return st;
+  }
   {
     unsigned* h = (unsigned*)c->h_pinned;
     GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost,
@@ -1153,14 +1155,84 @@ gm_status gm_pic_posterior(gm_ctx* c, int32_t n_blocks, const int32_t* block_of,
     GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
     const unsigned f = *h;
     if (f) GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), c->stream));
+    if (f & (kFlagNonFinite | kFlagNotSPD)) pic_free(c);
     if (f & kFlagNonFinite) return set_error(c, GM_E_NONFINITE, "non-finite covariance value");
     if (f & kFlagNotSPD)
       return set_error(c, GM_E_NOT_SPD,
                        "K_uu, a sub-catalogue's conditional covariance or the posterior "
                        "precision of u has no Cholesky factor");
   }
+  if ((st = copy_out(c, mean_out, pic_mean(c), nb_)) != GM_OK) return st;
+  if ((st = copy_out(c, cov_out, pic_cov(c), R * nb_)) != GM_OK) return st;
+  c->stats.kernel_launches = c->launches;
+  return GM_OK;
+}
+
+gm_status gm_pic_predict(gm_ctx* c, int64_t nq, const int32_t* q_block, const double* l,
+                         const double* b, const double* s, double* mean_out, double* var_out) {
+  if (!c || nq < 0 || (nq > 0 && (!q_block || !l || !b || !s || !mean_out || !var_out)))
+    return GM_E_INVAL;
+  if (!pic_ready(c)) return set_error(c, GM_E_STATE, "gm_pic_posterior must come first");
+  if (nq == 0) return GM_OK;
+  c->launches = 0;
+  const int nb = pic_blocks(c);
+  std::vector<int32_t> qb_h(nq);
+  if (is_device_ptr(q_block)) {
+    GM_CUDA_CHECK(c, cudaMemcpy(qb_h.data(), q_block, nq * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(qb_h.data(), q_block, nq * sizeof(int32_t));
+  }
+  for (int64_t q = 0; q < nq; ++q)
+    if (qb_h[q] < 0 || qb_h[q] >= nb) return set_error(c, GM_E_INVAL, "query block out of range");
+  const size_t nb_ = nq * sizeof(double);
+  // l, b, s, ux, uy, uz, kss, ms, mean, var (nq)
+  ScopedDev buf(c, 10 * nb_);
+  ScopedDev bqb(c, nq * sizeof(int32_t));
+  ScopedDev bqp(c, (nq + 1) * sizeof(int64_t));
+  if (!buf.p || !bqb.p || !bqp.p) return set_error(c, GM_E_NOMEM, "PIC query arrays");
+  double *ql = (double*)buf.p, *qb = ql + nq, *qs = qb + nq, *ux = qs + nq, *uy = ux + nq,
+         *uz = uy + nq, *kss = uz + nq, *ms = kss + nq, *mean = ms + nq, *var = mean + nq;
+  int32_t* qblk = (int32_t*)bqb.p;
+  int64_t* qptr = (int64_t*)bqp.p;
+  gm_status st;
+  if ((st = copy_in(c, ql, l, nb_)) != GM_OK || (st = copy_in(c, qb, b, nb_)) != GM_OK ||
+      (st = copy_in(c, qs, s, nb_)) != GM_OK)
+    return st;
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(qblk, qb_h.data(), nq * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                   c->stream));
+  GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned), c->stream));
+  GM_PROF(c, "k_check_inputs");
+  k_check_inputs<<<eb(c, nq), 256, 0, c->stream>>>(nq, qs, qs, qs, ql, qb, c->d_flags + 1);
+  GM_LAUNCH_CHECK(c);
+  {
+    unsigned* h = (unsigned*)c->h_pinned;
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                     c->stream));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+    if (*h) return set_error(c, GM_E_INVAL, "query distances must be finite and > 0");
+  }
+  if ((st = unit_vectors(c, nq, ql, qb, ux, uy, uz)) != GM_OK) return st;
+  if ((st = self_quadrature(c, nq, qs, kss)) != GM_OK) return st;
+  GM_PROF(c, "k_query_mean");
+  k_query_mean<<<eb(c, nq), 256, 0, c->stream>>>(nq, std::log(c->cfg.rho_bar), c->cfg.form,
+                                                 c->cfg.sigma2, qs, kss, ms);
+  GM_LAUNCH_CHECK(c);
+  Buffer qcol;
+  int64_t qnnz = 0;
+  st = neighbour_csr(c, nq, qs, ux, uy, uz, nullptr, false, qptr, qcol, &qnnz, nullptr);
+  if (st != GM_OK) return st;
+  ScopedDev bqc(c, qcol.p, qcol.bytes, ScopedDev::Adopt{});
+  ScopedDev bqv(c, (size_t)std::max<int64_t>(qnnz, 1) * sizeof(double));
+  if (!bqv.p) return set_error(c, GM_E_NOMEM, "PIC query values");
+  st = pair_quadrature(c, nq, qs, ux, uy, uz, nullptr, qptr, (const int32_t*)qcol.p, qnnz, bqv.p,
+                       false);
+  if (st == GM_OK)
+    st = pic_predict(c, nq, qs, ux, uy, uz, qblk, kss, ms, qptr, (const int32_t*)qcol.p,
+                     (const double*)bqv.p, mean, var);
+  if (st == GM_OK) st = read_flags(c);
+  if (st != GM_OK) return st;
   if ((st = copy_out(c, mean_out, mean, nb_)) != GM_OK) return st;
-  if ((st = copy_out(c, cov_out, cov, R * nb_)) != GM_OK) return st;
+  if ((st = copy_out(c, var_out, var, nb_)) != GM_OK) return st;
   c->stats.kernel_launches = c->launches;
   return GM_OK;
 }
@@ -1196,6 +1268,7 @@ void gm_destroy(gm_ctx* c) {
   c->prof_pool.clear();
   workspace_free(c);
   deflate_free(c);
+  pic_free(c);
   for (auto& b : c->owned) {
     if (c->has_alloc)
       c->alloc.free(b.p, b.bytes, (void*)c->stream, c->alloc.user);

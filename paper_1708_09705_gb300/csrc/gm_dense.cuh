@@ -163,6 +163,17 @@ GM_HD inline void upair(int64_t p, const double* us, const double* ux, const dou
   ch[p] = sqrt(dx * dx + dy * dy + dz * dz);
 }
 
+// Taper of the covariance at 3-D separation d (Wendland: taper 0, hard
+// cutoff: 1); zero beyond the cutoff.
+GM_HD inline double taper_weight(double d, double inv_cut, int taper) {
+  const double h = d * inv_cut;
+  if (taper == 0) {
+    const double u = 1.0 - h;
+    return h < 1.0 ? u * u * u * u * (4.0 * h + 1.0) : 0.0;
+  }
+  return h <= 1.0 ? 1.0 : 0.0;
+}
+
 // K_uu[a][b] (lower) from the pair's untapered value kp[p], tapered by the
 // 3-D separation as K is (Wendland: taper 0, hard cutoff: 1), and the prior
 // mean at inducing point a when a == b (lognormal: form 0, first order: 1).
@@ -173,13 +184,7 @@ GM_HD inline void kuu_entry(int64_t p, int R, double inv_cut, int taper, int for
   tri_index(p, &a, &b);
   const double sa = us[a], sb = us[b], ds = sa - sb;
   const double d = sqrt(ds * ds + sa * sb * ch[p] * ch[p]);
-  const double h = d * inv_cut;
-  double w = h <= 1.0 ? 1.0 : 0.0;
-  if (taper == 0) {
-    const double u = 1.0 - h;
-    w = h < 1.0 ? u * u * u * u * (4.0 * h + 1.0) : 0.0;
-  }
-  const double v = a == b ? kp[p] : w * kp[p];
+  const double v = a == b ? kp[p] : taper_weight(d, inv_cut, taper) * kp[p];
   Kuu[(int64_t)a * R + b] = v;
   if (a == b) mu_u[a] = log_rho_bar + log(sa) - (form == 0 ? 0.5 * v : 0.5 * sigma2);
 }
@@ -265,6 +270,94 @@ GM_HD inline void prec_task(int64_t e, int R, const double* Kinv, const double* 
     for (int c = 0; c < R; ++c) v += Kinv[(int64_t)r * R + c] * mu_u[c];
     h[r] = v;
   }
+}
+
+// Quadrature inputs of query-inducing pair p = q R + r.
+GM_HD inline void qpair(int64_t p, int R, const double* qs, const double* qx, const double* qy,
+                        const double* qz, const double* us, const double* ux, const double* uy,
+                        const double* uz, double* si, double* sj, double* ch) {
+  const int64_t q = p / R;
+  const int r = (int)(p - q * R);
+  const double dx = qx[q] - ux[r], dy = qy[q] - uy[r], dz = qz[q] - uz[r];
+  si[p] = qs[q];
+  sj[p] = us[r];
+  ch[p] = sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// K_su[p] (p = q R + r) from the pair's untapered value, tapered as K.
+GM_HD inline double ksu_entry(int64_t p, double inv_cut, int taper, const double* si,
+                              const double* sj, const double* ch, const double* kp) {
+  const double ds = si[p] - sj[p];
+  const double d = sqrt(ds * ds + si[p] * sj[p] * ch[p] * ch[p]);
+  return taper_weight(d, inv_cut, taper) * kp[p];
+}
+
+// Stored entry of star j in a query's CSR row [b, e) (columns sorted).
+GM_HD inline double row_entry(const int32_t* col, const double* val, int64_t b, int64_t e,
+                              int64_t j) {
+  int64_t lo = b, hi = e;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (col[mid] < j) lo = mid + 1; else hi = mid;
+  }
+  return (lo < e && col[lo] == j) ? val[lo] : 0.0;
+}
+
+// PIC predictive of ln A at one query point assigned to block k (the
+// paper's partially independent conditional, Sect. 4.1 / App. B): with
+// A_s = k_su K_uu^-1, D = k_sk - K_ku A_s^T (the query's covariance with the
+// block's observations given u), g = C_k^-1 D and L = A_s - g^T A_k,
+//   mean = m_s + g^T (a~_k - m_k) + L (mean_u - mu_u),
+//   var  = k_ss - A_s k_us - g^T D + L cov_u L^T.
+// Lu, Ck: factors of K_uu and C_k; A, Kku: n x R in block order; ksu: R
+// tapered cross-covariances; [qb, qe) the query's row of its CSR over the
+// stars (tapered).  Scratch: As, Lc, t (R), D, g (N_k).
+GM_HD inline void pic_point(int R, int k, const int64_t* boff, const int64_t* coff,
+                            const int64_t* bidx, const double* Lu, const double* Cf,
+                            const double* A, const double* Kku, const double* mu_u,
+                            const double* pmean, const double* pcov, const double* obs,
+                            const double* prior_m, const double* ksu, double kss, double ms,
+                            int64_t qb, int64_t qe, const int32_t* qcol, const double* qval,
+                            double* As, double* Lc, double* t, double* D, double* g,
+                            double* mean, double* var) {
+  const int64_t b0 = boff[k];
+  const int N = (int)(boff[k + 1] - b0);
+  for (int r = 0; r < R; ++r) As[r] = ksu[r];
+  gmdense::solve_lower(Lu, R, R, As, 1);
+  gmdense::solve_lower_t(Lu, R, R, As, 1);
+  for (int a = 0; a < N; ++a) {
+    const int64_t j = bidx[b0 + a];
+    double v = row_entry(qcol, qval, qb, qe, j);
+    const double* kr = Kku + (b0 + a) * R;
+    for (int r = 0; r < R; ++r) v -= kr[r] * As[r];
+    D[a] = v;
+    g[a] = v;
+  }
+  if (N > 0) {
+    gmdense::solve_lower(Cf + coff[k], N, N, g, 1);
+    gmdense::solve_lower_t(Cf + coff[k], N, N, g, 1);
+  }
+  for (int r = 0; r < R; ++r) {
+    double v = As[r];
+    for (int a = 0; a < N; ++a) v -= g[a] * A[(b0 + a) * R + r];
+    Lc[r] = v;
+  }
+  double m = ms, v = kss;
+  for (int a = 0; a < N; ++a) {
+    const int64_t j = bidx[b0 + a];
+    m += g[a] * (obs[j] - prior_m[j]);
+    v -= g[a] * D[a];
+  }
+  for (int r = 0; r < R; ++r) {
+    m += Lc[r] * (pmean[r] - mu_u[r]);
+    v -= As[r] * ksu[r];
+    double tr = 0.0;
+    for (int c = 0; c < R; ++c) tr += pcov[(int64_t)r * R + c] * Lc[c];
+    t[r] = tr;
+  }
+  for (int r = 0; r < R; ++r) v += Lc[r] * t[r];
+  *mean = m;
+  *var = v;
 }
 
 }  // namespace gmpic

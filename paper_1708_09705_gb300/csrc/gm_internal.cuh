@@ -52,6 +52,7 @@ struct Buffer {
 
 struct Workspace;  // solver scratch, see gm_solve.cu
 struct Deflation;  // deflation vectors of the variance panels, see gm_deflate.cu
+struct PicState;   // factors of the last PIC posterior, see gm_pic.cu
 struct PackState;  // packed multi-field panels, see gm_fields.cu
 
 // Per-field cell grid and hyperparameters.  A context holds one field per
@@ -167,6 +168,7 @@ struct gm_ctx {
 
   gm::Workspace* ws = nullptr;
   gm::Deflation* defl = nullptr;
+  gm::PicState* pic = nullptr;
   gm::PackState* pack = nullptr;
 
   // ---- optional per-kernel timing (CUDA events on the context stream, or
@@ -208,6 +210,8 @@ struct ScopedDev {
   ~ScopedDev() {
     if (p) dev_free_now(c, p, bytes);
   }
+  struct Adopt {};
+  ScopedDev(gm_ctx* ctx, void* ptr, size_t n, Adopt) : c(ctx), p(ptr), bytes(n) {}
   ScopedDev(const ScopedDev&) = delete;
   ScopedDev& operator=(const ScopedDev&) = delete;
 };
@@ -352,11 +356,25 @@ void workspace_free(gm_ctx* c);
 
 // PITC / PIC posterior of u at R inducing points (gm_pic.cu): us, ux, uy, uz
 // the inducing distances and unit vectors (device), h_block_int the block of
-// each internal star (host), mean (R) and cov (R x R) device outputs.
-// FP64 single-field contexts with the covariance built.  Synchronises.
+// each internal star (host).  The factors, the posterior mean (R) and
+// covariance (R x R) stay in the context (pic_mean, pic_cov) for
+// pic_predict.  FP64 single-field contexts with the covariance built.
+// Synchronises.
 gm_status pic_posterior(gm_ctx* c, int R, const double* us, const double* ux, const double* uy,
-                        const double* uz, const int32_t* h_block_int, int nb, double* mean,
-                        double* cov);
+                        const double* uz, const int32_t* h_block_int, int nb);
+bool pic_ready(gm_ctx* c);
+int pic_blocks(gm_ctx* c);
+int pic_inducing(gm_ctx* c);
+const double* pic_mean(gm_ctx* c);
+const double* pic_cov(gm_ctx* c);
+void pic_free(gm_ctx* c);
+// PIC predictive mean and variance at nq queries (device arrays): geometry,
+// block of each query, prior variance kss and mean ms, the queries' CSR over
+// the stars (tapered FP64 values).  Synchronises.
+gm_status pic_predict(gm_ctx* c, int64_t nq, const double* qs, const double* qx,
+                      const double* qy, const double* qz, const int32_t* qblk, const double* kss,
+                      const double* ms, const int64_t* qptr, const int32_t* qcol,
+                      const double* qval, double* mean, double* var);
 
 // Exact-HMC samples of each sightline's predictive truncated to a
 // non-decreasing sequence (gm_sightline.cu).  Device arrays in the caller

@@ -37,7 +37,8 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_site_update_noalloc", "gm_surrogate_param_count", "gm_surrogate_set_params",
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
            "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries", "gm_predict_pairs",
-           "gm_predict_sightlines", "gm_monotone_sample", "gm_pic_posterior"]
+           "gm_predict_sightlines", "gm_monotone_sample", "gm_pic_posterior",
+           "gm_pic_predict"]
 
 
 class GmError(RuntimeError):
@@ -106,6 +107,7 @@ def lib():
         L.gm_predict_sightlines.argtypes = [vp, i64, i32, vp, vp, vp, vp, vp]
         L.gm_monotone_sample.argtypes = [vp, i64, i32, vp, vp, vp, i32, i32, vp, vp]
         L.gm_pic_posterior.argtypes = [vp, i32, vp, i64, vp, vp, vp, vp, vp]
+        L.gm_pic_predict.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.gm_stream.argtypes = [vp]
@@ -273,6 +275,18 @@ class Context:
                                            l.ctypes.data, b.ctypes.data, s.ctypes.data,
                                            mean.ctypes.data, cov.ctypes.data))
         return mean, cov
+
+    def pic_predict(self, q_block, l, b, s):
+        """PIC predictive (mean, var) at queries (l, b, s) assigned to the
+        sub-catalogues q_block, after pic_posterior."""
+        qb = np.ascontiguousarray(q_block, dtype=np.int32)
+        l, b, s = (np.ascontiguousarray(v, dtype=np.float64) for v in (l, b, s))
+        nq = len(s)
+        mean, var = np.empty(nq), np.empty(nq)
+        self._check(lib().gm_pic_predict(self._h, nq, qb.ctypes.data, l.ctypes.data,
+                                         b.ctypes.data, s.ctypes.data, mean.ctypes.data,
+                                         var.ctypes.data))
+        return mean, var
 
     # ---- state
     def _pair_out(self, fn, out):

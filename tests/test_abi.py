@@ -84,3 +84,4 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
     assert L.gm_monotone_sample(None, 1, 2, x, x, x, 0, 1, x, None) == 1
     blk = (C.c_int32 * 4)(0, 0, 1, 1)
     assert L.gm_pic_posterior(None, 2, blk, 2, x, x, x, x, x) == 1
+    assert L.gm_pic_predict(None, 2, blk, x, x, x, x, x) == 1

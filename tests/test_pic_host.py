@@ -85,7 +85,59 @@ extern "C" int pic_host(long n, int R, int nb, const long* boff, const double* K
   return 0;
 }
 // the whole device pipeline after the quadrature and neighbour search, in
-// its launch order, from the stars' CSR and the inducing points' CSR
+// its launch order, from the stars' CSR and the inducing points' CSR; the
+// factors stay in St for the predictive
+struct St {
+  std::vector<int64_t> boff, coff, bidx;
+  std::vector<int32_t> rowpos, dims;
+  std::vector<double> Lu, mu_u, Kku, A, C, mean, cov;
+};
+static int pipeline(St& S, long n, int R, int nb, const int32_t* blk, const int64_t* row_ptr,
+                    const int32_t* col, const double* val, const int64_t* qptr,
+                    const int32_t* qcol, const double* qval, long qnnz, const double* us,
+                    const double* ux, const double* uy, const double* uz, const double* kp,
+                    double inv_cut, int taper, int form, double log_rho_bar, double sigma2,
+                    const double* obs, const double* sig, const double* prior_m, int nt,
+                    double* si, double* sj, double* ch) {
+  S.boff.resize(nb + 1); S.coff.resize(nb + 1); S.bidx.resize(n); S.rowpos.resize(n);
+  S.dims.resize(nb);
+  if (!gmpic::block_lists(n, blk, nb, 8192, S.boff.data(), S.coff.data(), S.bidx.data(),
+                          S.rowpos.data(), S.dims.data()))
+    return 9;
+  const long RR = (long)R * R, np = (long)R * (R + 1) / 2;
+  std::vector<double> Kuu(RR, 0.0), X, yv(n), Lam(RR), eta(R), Kinv(RR), Pm(RR), h(R);
+  S.mu_u.assign(R, 0.0); S.Kku.assign(n * R, 0.0); S.A.assign(n * R, 0.0);
+  S.C.assign(S.coff[nb], 0.0); S.mean.assign(R, 0.0); S.cov.assign(RR, 0.0);
+  for (long e = 0; e < qnnz; ++e) gmpic::kku_entry(e, R, qptr, qcol, qval, S.rowpos.data(), S.Kku.data());
+  for (long p = 0; p < np; ++p) gmpic::upair(p, us, ux, uy, uz, si, sj, ch);
+  for (long p = 0; p < np; ++p)
+    gmpic::kuu_entry(p, R, inv_cut, taper, form, log_rho_bar, sigma2, us, ch, kp, Kuu.data(),
+                     S.mu_u.data());
+  S.Lu = Kuu;
+  if (!chol(S.Lu.data(), R, nt)) return 1;
+  for (long j = 0; j < n; ++j) a_row(S.Lu.data(), R, S.Kku.data() + j * R, S.A.data() + j * R);
+  for (long e = 0; e < S.coff[nb]; ++e)
+    gmpic::cmat_entry(e, nb, S.coff.data(), S.boff.data(), R, S.bidx.data(), row_ptr, col, val,
+                      S.A.data(), S.Kku.data(), sig, S.C.data());
+  for (int k = 0; k < nb; ++k)
+    if (S.dims[k] > 0 && !chol(S.C.data() + S.coff[k], S.dims[k], nt)) return 2;
+  for (long j = 0; j < n; ++j)
+    yv[j] = y_entry(obs[S.bidx[j]], prior_m[S.bidx[j]], S.A.data() + j * R, S.mu_u.data(), R);
+  X = S.A;
+  for (long t = 0; t < (long)nb * (R + 1); ++t)
+    gmpic::fsolve_task(t, R, S.coff.data(), S.boff.data(), S.C.data(), X.data(), yv.data());
+  for (long e = 0; e < RR + R; ++e) gmpic::lambda_task(e, n, R, X.data(), yv.data(), Lam.data(), eta.data());
+  for (int c = 0; c < R; ++c) inverse_col(S.Lu.data(), R, c, Kinv.data() + c, R);
+  for (long e = 0; e < RR + R; ++e)
+    gmpic::prec_task(e, R, Kinv.data(), Lam.data(), S.mu_u.data(), eta.data(), Pm.data(), h.data());
+  if (!chol(Pm.data(), R, nt)) return 3;
+  for (int r = 0; r < R; ++r) S.mean[r] = h[r];
+  solve_lower(Pm.data(), R, R, S.mean.data(), 1);
+  solve_lower_t(Pm.data(), R, R, S.mean.data(), 1);
+  for (int c = 0; c < R; ++c) inverse_col(Pm.data(), R, c, S.cov.data() + c, R);
+  return 0;
+}
+
 extern "C" int pic_full_host(long n, int R, int nb, const int32_t* blk, const int64_t* row_ptr,
                              const int32_t* col, const double* val, const int64_t* qptr,
                              const int32_t* qcol, const double* qval, long qnnz,
@@ -93,42 +145,26 @@ extern "C" int pic_full_host(long n, int R, int nb, const int32_t* blk, const in
                              const double* uz, const double* kp, double inv_cut, int taper,
                              int form, double log_rho_bar, double sigma2, const double* obs,
                              const double* sig, const double* prior_m, int nt, double* mean,
-                             double* cov, double* si, double* sj, double* ch) {
-  std::vector<int64_t> boff(nb + 1), coff(nb + 1), bidx(n);
-  std::vector<int32_t> rowpos(n), dims(nb);
-  if (!gmpic::block_lists(n, blk, nb, 8192, boff.data(), coff.data(), bidx.data(), rowpos.data(),
-                          dims.data()))
-    return 9;
-  const long RR = (long)R * R, np = (long)R * (R + 1) / 2;
-  std::vector<double> Kuu(RR, 0.0), Lu, mu_u(R), Kku(n * R, 0.0), A(n * R), X, yv(n),
-      C(coff[nb]), Lam(RR), eta(R), Kinv(RR), Pm(RR), h(R);
-  for (long e = 0; e < qnnz; ++e) gmpic::kku_entry(e, R, qptr, qcol, qval, rowpos.data(), Kku.data());
-  for (long p = 0; p < np; ++p) gmpic::upair(p, us, ux, uy, uz, si, sj, ch);
-  for (long p = 0; p < np; ++p)
-    gmpic::kuu_entry(p, R, inv_cut, taper, form, log_rho_bar, sigma2, us, ch, kp, Kuu.data(),
-                     mu_u.data());
-  Lu = Kuu;
-  if (!chol(Lu.data(), R, nt)) return 1;
-  for (long j = 0; j < n; ++j) a_row(Lu.data(), R, Kku.data() + j * R, A.data() + j * R);
-  for (long e = 0; e < coff[nb]; ++e)
-    gmpic::cmat_entry(e, nb, coff.data(), boff.data(), R, bidx.data(), row_ptr, col, val, A.data(),
-                      Kku.data(), sig, C.data());
-  for (int k = 0; k < nb; ++k)
-    if (dims[k] > 0 && !chol(C.data() + coff[k], dims[k], nt)) return 2;
-  for (long j = 0; j < n; ++j)
-    yv[j] = y_entry(obs[bidx[j]], prior_m[bidx[j]], A.data() + j * R, mu_u.data(), R);
-  X = A;
-  for (long t = 0; t < (long)nb * (R + 1); ++t)
-    gmpic::fsolve_task(t, R, coff.data(), boff.data(), C.data(), X.data(), yv.data());
-  for (long e = 0; e < RR + R; ++e) gmpic::lambda_task(e, n, R, X.data(), yv.data(), Lam.data(), eta.data());
-  for (int c = 0; c < R; ++c) inverse_col(Lu.data(), R, c, Kinv.data() + c, R);
-  for (long e = 0; e < RR + R; ++e)
-    gmpic::prec_task(e, R, Kinv.data(), Lam.data(), mu_u.data(), eta.data(), Pm.data(), h.data());
-  if (!chol(Pm.data(), R, nt)) return 3;
-  for (int r = 0; r < R; ++r) mean[r] = h[r];
-  solve_lower(Pm.data(), R, R, mean, 1);
-  solve_lower_t(Pm.data(), R, R, mean, 1);
-  for (int c = 0; c < R; ++c) inverse_col(Pm.data(), R, c, cov + c, R);
+                             double* cov, double* si, double* sj, double* ch,
+                             long nq, const int32_t* q_blk, const double* ksu, const double* kss,
+                             const double* ms, const int64_t* pptr, const int32_t* pcol,
+                             const double* pval, double* pmean, double* pvar) {
+  St S;
+  const int rc = pipeline(S, n, R, nb, blk, row_ptr, col, val, qptr, qcol, qval, qnnz, us, ux,
+                          uy, uz, kp, inv_cut, taper, form, log_rho_bar, sigma2, obs, sig,
+                          prior_m, nt, si, sj, ch);
+  if (rc) return rc;
+  for (int r = 0; r < R; ++r) mean[r] = S.mean[r];
+  for (long e = 0; e < (long)R * R; ++e) cov[e] = S.cov[e];
+  int maxN = 1;
+  for (int k = 0; k < nb; ++k) maxN = S.dims[k] > maxN ? S.dims[k] : maxN;
+  std::vector<double> w(3 * R + 2 * maxN);
+  for (long q = 0; q < nq; ++q)
+    gmpic::pic_point(R, q_blk[q], S.boff.data(), S.coff.data(), S.bidx.data(), S.Lu.data(),
+                     S.C.data(), S.A.data(), S.Kku.data(), S.mu_u.data(), S.mean.data(),
+                     S.cov.data(), obs, prior_m, ksu + q * R, kss[q], ms[q], pptr[q], pptr[q + 1],
+                     pcol, pval, w.data(), w.data() + R, w.data() + 2 * R, w.data() + 3 * R,
+                     w.data() + 3 * R + maxN, pmean + q, pvar + q);
   return 0;
 }
 """
@@ -150,7 +186,8 @@ def host_lib(tmp_path_factory):
                            vp, vp]
     L.pic_host.restype = C.c_int
     L.pic_full_host.argtypes = [C.c_long, C.c_int, C.c_int] + [vp] * 7 + [C.c_long] + [vp] * 5 + \
-        [C.c_double, C.c_int, C.c_int, C.c_double, C.c_double] + [vp] * 3 + [C.c_int] + [vp] * 5
+        [C.c_double, C.c_int, C.c_int, C.c_double, C.c_double] + [vp] * 3 + [C.c_int] + \
+        [vp] * 5 + [C.c_long] + [vp] * 9
     L.pic_full_host.restype = C.c_int
     return L
 
@@ -164,16 +201,23 @@ def setup():
     li = rng.uniform(cat["l"].min(), cat["l"].max(), R)
     bi = rng.uniform(cat["b"].min(), cat["b"].max(), R)
     si = np.exp(rng.uniform(np.log(150), np.log(2500), R))
-    union = dict(cat, l=np.concatenate([cat["l"], li]), b=np.concatenate([cat["b"], bi]),
-                 s=np.concatenate([cat["s"], si]))
+    # extra query points near stars, assigned to the block of that star
+    jq = rng.choice(n, 8, replace=False)
+    ql, qb_, qs = cat["l"][jq] + 3e-4, cat["b"][jq] - 3e-4, cat["s"][jq] * 0.93
+    union = dict(cat, l=np.concatenate([cat["l"], li, ql]), b=np.concatenate([cat["b"], bi, qb_]),
+                 s=np.concatenate([cat["s"], si, qs]))
     cv = O.build_cov(union)
     A = np.clip(cat["A_obs"], 0.02, None)
     atil = np.log(A) + 0.02 * rng.standard_normal(n)
     sig2 = (cat["A_sigma"] / A) ** 2
     order = np.argsort(cat["l"])
     groups = [np.sort(g) for g in np.array_split(order, 5)]
+    star_blk = np.zeros(n, dtype=np.int32)
+    for k, g in enumerate(groups):
+        star_blk[g] = k
     return dict(n=n, R=R, K=cv["K"], m=cv["m"], atil=atil, sig2=sig2, groups=groups,
-                u=np.arange(n, n + R), cat=cat, li=li, bi=bi, si=si)
+                u=np.arange(n, n + R), cat=cat, li=li, bi=bi, si=si, ql=ql,
+                qblk=star_blk[jq])
 
 
 @pytest.mark.parametrize("nt", [1, 3, 32])
@@ -258,13 +302,28 @@ def test_host_full_pipeline_from_csr_matches_oracle(host_lib, setup):
     obs = np.ascontiguousarray(S["atil"])
     sig = np.sqrt(S["sig2"])
     pm = np.ascontiguousarray(m[:n])
+    # queries: every star (in its block) and the extra points of the fixture
+    nqx = len(S["ql"])
+    qidx = np.concatenate([np.arange(n), n + R + np.arange(nqx)])
+    q_blk = np.concatenate([blk, S["qblk"]]).astype(np.int32)
+    ksu = np.ascontiguousarray(K[np.ix_(qidx, u)])
+    kss = np.ascontiguousarray(np.diag(K)[qidx])
+    ms = np.ascontiguousarray(m[qidx])
+    Kp = sparse.csr_matrix(K[np.ix_(qidx, np.arange(n))])
+    Kp.sort_indices()
+    pptr = Kp.indptr.astype(np.int64)
+    pcol = Kp.indices.astype(np.int32)
+    pval = Kp.data.astype(np.float64)
+    pmean, pvar = np.zeros(len(qidx)), np.zeros(len(qidx))
     rc = host_lib.pic_full_host(
         n, R, len(S["groups"]), blk.ctypes.data, row_ptr.ctypes.data, col.ctypes.data,
         val.ctypes.data, qptr.ctypes.data, qcol.ctypes.data, qval.ctypes.data, len(qval),
         us.ctypes.data, ux.ctypes.data, uy.ctypes.data, uz.ctypes.data, kp.ctypes.data,
         1.0 / float(cat["cutoff_pc"]), 0, 0, np.log(float(cat["rho_bar"])), sig2,
         obs.ctypes.data, sig.ctypes.data, pm.ctypes.data, 4, mean.ctypes.data, cov.ctypes.data,
-        si.ctypes.data, sj.ctypes.data, ch.ctypes.data)
+        si.ctypes.data, sj.ctypes.data, ch.ctypes.data, len(qidx), q_blk.ctypes.data,
+        ksu.ctypes.data, kss.ctypes.data, ms.ctypes.data, pptr.ctypes.data, pcol.ctypes.data,
+        pval.ctypes.data, pmean.ctypes.data, pvar.ctypes.data)
     assert rc == 0
     np.testing.assert_array_equal(si, us[a_idx])
     np.testing.assert_array_equal(sj, us[b_idx])
@@ -274,3 +333,15 @@ def test_host_full_pipeline_from_csr_matches_oracle(host_lib, setup):
     ref_m, ref_c = P.pitc_posterior_direct(K[np.ix_(u, u)], blocks, m[u])
     np.testing.assert_allclose(mean, ref_m, rtol=1e-9, atol=1e-10)
     np.testing.assert_allclose(cov, ref_c, rtol=1e-8, atol=1e-12)
+    # the PIC predictive at the stars and at the extra points
+    Kuu = K[np.ix_(u, u)]
+    for q in range(len(qidx)):
+        k = q_blk[q]
+        g = S["groups"][k]
+        b = dict(Kku=K[np.ix_(g, u)], Kkk=K[np.ix_(g, g)], m=m[g], atil=S["atil"][g],
+                 sig2=S["sig2"][g])
+        j = qidx[q]
+        mm_, vv_ = P.pic_predict(Kuu, m[u], ref_m, ref_c, b, K[np.ix_([j], u)], np.diag(K)[[j]],
+                                 K[np.ix_([j], g)], m[[j]])
+        assert pmean[q] == pytest.approx(mm_[0], rel=1e-9, abs=1e-10)
+        assert pvar[q] == pytest.approx(vv_[0], rel=1e-7, abs=1e-12)
