@@ -23,6 +23,7 @@
 // which converges where s >> L0 (the Q-node rule's nodes are s / Q apart).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(256) k_self_quad_band(QuadParams P, int64_t n_
 static TabF32 tab_f32() {
   TabF32 t;
   float xmin = ldexpf(1.0f, kTabF32.emin);
-  t.base = *reinterpret_cast<int*>(&xmin);
+  std::memcpy(&t.base, &xmin, sizeof(int));  // bit pattern of 2^emin
   t.shift = 23 - kTabF32.m;
   t.last = kTabF32.n_real();
   t.xmin = xmin;
@@ -462,7 +463,8 @@ static TabF32 tab_f32() {
 static TabF64 tab_f64() {
   TabF64 t;
   double xmin = std::ldexp(1.0, kTabF64.emin);
-  long long bits = *reinterpret_cast<long long*>(&xmin);
+  long long bits;
+  std::memcpy(&bits, &xmin, sizeof(bits));  // bit pattern of 2^emin
   t.base = (int)(bits >> 32);
   t.shift = 20 - kTabF64.m;
   t.last = kTabF64.n_real();
