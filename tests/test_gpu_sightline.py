@@ -59,9 +59,13 @@ def test_sightline_predictive_matches_oracle(gm, field, prec):
         np.testing.assert_allclose(mean, mu_o, rtol=1e-6, atol=1e-8)
         np.testing.assert_allclose(cov, S_o, rtol=1e-6, atol=1e-10)
     else:
-        # the single-point predictive's FP32 bounds (1e-3 in ln A, 1e-2 in variance)
+        # the single-point predictive's FP32 bounds (1e-3 in ln A, 1e-2 in
+        # variance); entries of points farther apart than the cutoff are only
+        # the solve term (~1e-7 here), where the FP32 panel CG (relative
+        # residual 1e-5) leaves absolute errors of a few 1e-7 (an FP32 CG
+        # emulation on the CPU gave 4e-7): atol 5e-6
         np.testing.assert_allclose(mean, mu_o, atol=1e-3)
-        np.testing.assert_allclose(cov, S_o, rtol=1e-2, atol=1e-6)
+        np.testing.assert_allclose(cov, S_o, rtol=1e-2, atol=5e-6)
 
 
 def _sampler_ctx(gm):
