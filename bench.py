@@ -75,11 +75,13 @@ def parse():
                         "converged band rule (difference/mean coordinates, graded panels)")
     p.add_argument("--no-exact", action="store_true",
                    help="skip the one-step exact-variance comparison")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4_fields", "sightlines"],
+    p.add_argument("--workload", default="c2",
+                   choices=["c2", "c3", "c4_fields", "sightlines", "pic"],
                    help="c2: the 20,000-star field (bench line); c4_fields: 256 independent "
                         "fields solved together (batched path); sightlines: the dA/ds >= 0 "
                         "conditioning on the 20,000-star posterior (joint sightline "
-                        "predictive + exact-HMC sampler)")
+                        "predictive + exact-HMC sampler); pic: the PIC posterior over 140 "
+                        "inducing points and 36 sub-catalogues (Sect. 4.1 simplified case)")
     p.add_argument("--sl-predict", type=int, default=256,
                    help="sightlines of the joint-predictive leg (--workload sightlines)")
     p.add_argument("--sl-sample", type=int, default=65536,
@@ -683,6 +685,73 @@ def run_sightlines(a):
     print(json.dumps(line), flush=True)
 
 
+def run_pic(a):
+    """The paper's PIC approximation in its simplified case on the 20k field:
+    36 sub-catalogues (a 6 x 6 grid in l and b), 140 inducing points (35
+    directions x 1, 2, 3, 4 kpc), Gaussian observations of ln A; one step =
+    gm_pic_posterior + gm_pic_predict at 10,000 query points (FP64)."""
+    import torch
+
+    import paper_1708_09705_gb300 as gm
+    from synth import make_catalogue
+
+    torch.cuda.set_device(0)
+    cat = make_catalogue(WORKLOAD, n=a.n, seed=0)
+    n = len(cat["s"])
+    A = np.clip(cat["A_obs"], 0.02, None)
+    atil = np.log(A)
+    sig = cat["A_sigma"] / A
+    l0, l1, b0, b1 = cat["l"].min(), cat["l"].max(), cat["b"].min(), cat["b"].max()
+    il = np.minimum((6 * (cat["l"] - l0) / (l1 - l0)).astype(int), 5)
+    ib = np.minimum((6 * (cat["b"] - b0) / (b1 - b0)).astype(int), 5)
+    blk = (il * 6 + ib).astype(np.int32)
+    rng = np.random.default_rng(0)
+    dl = rng.uniform(l0, l1, 35)
+    db = rng.uniform(b0, b1, 35)
+    ul = np.repeat(dl, 4)
+    ub = np.repeat(db, 4)
+    us = np.tile([1000.0, 2000.0, 3000.0, 4000.0], 35)
+    nq = 10000
+    ql = rng.uniform(l0, l1, nq)
+    qb = rng.uniform(b0, b1, nq)
+    qs = np.exp(rng.uniform(np.log(100.0), np.log(3000.0), nq))
+    qil = np.minimum((6 * (ql - l0) / (l1 - l0)).astype(int), 5)
+    qib = np.minimum((6 * (qb - b0) / (b1 - b0)).astype(int), 5)
+    qblk = (qil * 6 + qib).astype(np.int32)
+    cfg = gm.config_from_catalogue(cat, precision=gm.PREC_FP64, likelihood=gm.LIK_GAUSS_IN_LNA,
+                                   cg_tol=1e-10)
+    ctx = gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], atil, sig)
+    ctx.build_cov()
+    res = {"posterior": [], "predict": []}
+    for k in range(a.warmup + a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.pic_posterior(blk, ul, ub, us)
+        t1 = time.perf_counter()
+        pm, pv = ctx.pic_predict(qblk, ql, qb, qs)
+        t2 = time.perf_counter()
+        if k >= a.warmup:
+            res["posterior"].append(t1 - t0)
+            res["predict"].append(t2 - t1)
+    st = ctx.stats()
+    ctx.close()
+    tp = sum(res["posterior"]) / a.steps
+    tq = sum(res["predict"]) / a.steps
+    line = {"metric": "PIC posterior + predictive (Sect. 4.1 simplified case)",
+            "value": nq / (tp + tq), "unit": "predicted points/s (posterior included)",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}; 36 sub-catalogues (6 x 6 grid "
+                                   f"in l, b), 140 inducing points (35 random directions x 1-4 "
+                                   f"kpc), observations ln A with sd sigma_A / A",
+                       "n_stars": n, "queries": nq},
+            "posterior_ms": 1e3 * tp, "predict_ms": 1e3 * tq,
+            "timing": "host wall clock around each call (each call synchronises)",
+            "gpu_launches": st["kernel_launches"],
+            "predict_finite": bool(np.all(np.isfinite(pm)) and np.all(pv > 0))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.workload == "c3":
@@ -702,6 +771,8 @@ def main():
         run_fields(a)
     elif a.workload == "sightlines":
         run_sightlines(a)
+    elif a.workload == "pic":
+        run_pic(a)
     else:
         run_gpu(a)
 
