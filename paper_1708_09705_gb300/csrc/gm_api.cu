@@ -714,9 +714,10 @@ static gm_status predict_points(gm_ctx* c, int64_t nq, const double* ql, const d
                                 const double* qs, double* mean, double* var,
                                 double* pair_cross) {
   const size_t nb = nq * sizeof(double);
-  // query work arrays: ux, uy, uz, kss, mq
-  double* q = (double*)dev_alloc(c, 5 * nb);
-  int64_t* qptr = (int64_t*)dev_alloc(c, (nq + 1) * sizeof(int64_t));
+  // query work arrays: ux, uy, uz, kss, mq (released on every return)
+  ScopedDev bq(c, 5 * nb), bqp(c, (nq + 1) * sizeof(int64_t));
+  double* q = (double*)bq.p;
+  int64_t* qptr = (int64_t*)bqp.p;
   if (!q || !qptr) return set_error(c, GM_E_NOMEM, "query arrays");
   double *ux = q, *uy = q + nq, *uz = q + 2 * nq, *kss = q + 3 * nq, *mq = q + 4 * nq;
   GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 1, 0, sizeof(unsigned), c->stream));
@@ -735,8 +736,10 @@ static gm_status predict_points(gm_ctx* c, int64_t nq, const double* ql, const d
   int64_t qnnz = 0;
   st = neighbour_csr(c, nq, qs, ux, uy, uz, nullptr, false, qptr, qcol, &qnnz, nullptr);
   if (st != GM_OK) return st;
+  ScopedDev bqc(c, qcol.p, qcol.bytes, ScopedDev::Adopt{});
   const size_t vs = c->cfg.precision == GM_PREC_FP32 ? sizeof(float) : sizeof(double);
-  void* qval = dev_alloc(c, std::max<int64_t>(qnnz, 1) * vs);
+  ScopedDev bqv(c, std::max<int64_t>(qnnz, 1) * vs);
+  void* qval = bqv.p;
   if (!qval) return set_error(c, GM_E_NOMEM, "query values");
   st = pair_quadrature(c, nq, qs, ux, uy, uz, nullptr, qptr, (const int32_t*)qcol.p, qnnz, qval,
                        false);
@@ -758,10 +761,6 @@ static gm_status predict_points(gm_ctx* c, int64_t nq, const double* ql, const d
   if (st == GM_OK) st = read_flags(c);
   if (st != GM_OK) return st;
   GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
-  dev_free_now(c, qval, std::max<int64_t>(qnnz, 1) * vs);
-  dev_free_now(c, qcol.p, qcol.bytes);
-  dev_free_now(c, qptr, (nq + 1) * sizeof(int64_t));
-  dev_free_now(c, q, 5 * nb);
   return GM_OK;
 }
 
@@ -775,7 +774,8 @@ gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, co
   gm_status st = ensure_posterior(c);
   if (st != GM_OK) return st;
   const size_t nb = nq * sizeof(double);
-  double* q = (double*)dev_alloc(c, 5 * nb);  // l, b, s, mean, var
+  ScopedDev buf(c, 5 * nb);  // l, b, s, mean, var
+  double* q = (double*)buf.p;
   if (!q) return set_error(c, GM_E_NOMEM, "query arrays");
   double *ql = q, *qb = q + nq, *qs = q + 2 * nq, *mean = q + 3 * nq, *var = q + 4 * nq;
   if ((st = copy_in(c, ql, l, nb)) != GM_OK || (st = copy_in(c, qb, b, nb)) != GM_OK ||
@@ -785,7 +785,6 @@ gm_status gm_predict(gm_ctx* c, int64_t nq, const double* l, const double* b, co
   if (st != GM_OK) return st;
   if ((st = copy_out(c, mean_out, mean, nb)) != GM_OK) return st;
   if ((st = copy_out(c, var_out, var, nb)) != GM_OK) return st;
-  dev_free_now(c, q, 5 * nb);
   c->stats.kernel_launches = c->launches;
   return GM_OK;
 }
@@ -876,7 +875,8 @@ gm_status gm_predict_pairs(gm_ctx* c, int64_t nq, const double* l, const double*
   const size_t nb = nq * sizeof(double);
   // l, b, s (nq); l2, b2, s2, mean, var (2 nq); si, sj, ch, k12, cross (nq);
   // cov (3 nq), dens (2 nq)
-  double* q = (double*)dev_alloc(c, 23 * nb);
+  ScopedDev buf(c, 23 * nb);
+  double* q = (double*)buf.p;
   if (!q) return set_error(c, GM_E_NOMEM, "pair arrays");
   double *ql = q, *qb = q + nq, *qs = q + 2 * nq, *l2 = q + 3 * nq, *b2 = q + 5 * nq,
          *s2 = q + 7 * nq, *mean = q + 9 * nq, *var = q + 11 * nq, *si = q + 13 * nq,
@@ -899,7 +899,6 @@ gm_status gm_predict_pairs(gm_ctx* c, int64_t nq, const double* l, const double*
   if ((st = copy_out(c, mean_out, mean, 2 * nb)) != GM_OK) return st;
   if ((st = copy_out(c, cov_out, cov, 3 * nb)) != GM_OK) return st;
   if ((st = copy_out(c, dens_out, dens, 2 * nb)) != GM_OK) return st;
-  dev_free_now(c, q, 23 * nb);
   c->stats.kernel_launches = c->launches;
   return GM_OK;
 }
