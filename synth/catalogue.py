@@ -77,8 +77,15 @@ def _unit(l, b):
     return np.stack([cb * np.cos(l), cb * np.sin(l), np.sin(b)], axis=-1)
 
 
-def _truth_fft(rng, l, b, s, sigma2, L0, rho_bar, h=2.0, pad_factor=3.0):
-    """Line integrals of exp(f) for a spectrally synthesised log-density f."""
+def _truth_fft(rng, l, b, s, sigma2, L0, rho_bar, h=2.0, pad_factor=3.0, order=1):
+    """Line integrals of exp(f) for a spectrally synthesised log-density f.
+
+    order: how f is read at the integration points, 1 = trilinear
+    interpolation of the grid, 0 = the value of the nearest cell.  Trilinear
+    interpolation averages cells whose correlation is well below 1 (the
+    Kolmogorov correlation has a cusp at zero separation: phi(0.1) = 0.8), so
+    it lowers the variance of the sampled log-density and E[exp f] with it;
+    nearest-cell values keep the variance sigma2."""
     from scipy import fft as sfft
     from scipy.ndimage import map_coordinates
 
@@ -137,7 +144,7 @@ def _truth_fft(rng, l, b, s, sigma2, L0, rho_bar, h=2.0, pad_factor=3.0):
         tm = 0.5 * (t0 + t1)
         p = (u[idx][star] * tm[:, None]) @ R.T
         g = ((p - lo) / h).T
-        fv = map_coordinates(f, g, order=1, mode="nearest")
+        fv = map_coordinates(f, g, order=order, mode="nearest")
         A[idx] = np.bincount(star, weights=np.exp(mu_f + fv) * (t1 - t0),
                              minlength=len(idx))
     return A
@@ -147,7 +154,10 @@ def make_catalogue(wl: Workload | str, n: int | None = None, seed: int | None = 
                    truth: str = "fft"):
     """Draw a catalogue for workload `wl` (optionally overriding n and seed).
 
-    truth='fft'  : spectral synthesis of the log-density on a 2 pc grid.
+    truth='fft'  : spectral synthesis of the log-density on a 2 pc grid,
+                   read by trilinear interpolation.
+    truth='fft_nearest' : the same field read at the nearest cell (keeps the
+                   log-density's variance; see _truth_fft).
     truth='mean' : A_true = rho_bar * s (no turbulence; fast, for unit tests).
     Returns a dict of float64 arrays l, b (radians), s (pc), A_obs, A_sigma,
     A_true (mag) plus the workload's hyperparameters.
@@ -159,8 +169,9 @@ def make_catalogue(wl: Workload | str, n: int | None = None, seed: int | None = 
     ss = np.random.SeedSequence([seed, n, 1708_09705])
     r_pos, r_truth, r_noise = [np.random.default_rng(c) for c in ss.spawn(3)]
     l, b, s = _field_positions(r_pos, n, wl.l_deg, wl.b_deg, wl.s_pc)
-    if truth == "fft":
-        A_true = _truth_fft(r_truth, l, b, s, wl.sigma2, wl.outer_scale_pc, wl.rho_bar)
+    if truth in ("fft", "fft_nearest"):
+        A_true = _truth_fft(r_truth, l, b, s, wl.sigma2, wl.outer_scale_pc, wl.rho_bar,
+                            order=1 if truth == "fft" else 0)
     elif truth == "mean":
         A_true = wl.rho_bar * s
     else:

@@ -37,3 +37,48 @@ def test_fields_and_subset():
     assert len(f) == 4 and all(len(c["s"]) >= 1 for c in f)
     c = catalogue_subset(make_catalogue("c1_plain_400", truth="mean"), np.arange(10))
     assert len(c["l"]) == 10 and c["sigma2"] == 1.0
+
+
+def _truth_draws(order, n_draws=400):
+    """Extinctions of 6 stars (60-140 pc, outer scale 20 pc) over independent
+    draws of the spectrally synthesised field, and the model covariance
+    rho_bar^2 I_ij of Sect. 3 (converged band rule of the oracle)."""
+    import oracle as O
+    from oracle import band as Bd
+    from synth.catalogue import _field_positions, _truth_fft
+    L0, sigma2, rho = 20.0, 1.0, 1e-3
+    l, b, s = _field_positions(np.random.default_rng(5), 6, (0.0, 4.0), (0.0, 4.0),
+                               (60.0, 140.0))
+    A = np.array([_truth_fft(np.random.default_rng([7, k]), l, b, s, sigma2, L0, rho,
+                             order=order) for k in range(n_draws)])
+    u = O.unit_vectors(l, b)
+    g = lambda r: O.g_of_r(r, sigma2, L0)  # noqa: E731
+    n = len(s)
+    M = np.zeros((n, n))
+    for i in range(n):
+        for j in range(i, n):
+            R, _ = Bd.pair_R_band(s[i], s[j], ((u[i] - u[j]) ** 2).sum(), g, L0)
+            M[i, j] = M[j, i] = rho * rho * R[0] * s[i] * s[j]
+    return A, s, rho, M
+
+
+def test_truth_covariance_matches_the_model():
+    """Monte Carlo of the truth simulator (nearest-cell reading of the field):
+    E[A] = rho_bar s and Cov(A_i, A_j) = rho_bar^2 I_ij, the lognormal moment
+    match of Sect. 3 with g = expm1(sigma2 phi), within the sampling error of
+    400 draws (about 3 % on the mean, 8 % on variances)."""
+    A, s, rho, M = _truth_draws(order=0)
+    C = np.cov(A.T)
+    iu = np.triu_indices(len(s), 1)
+    assert abs(np.mean(A.mean(0) / (rho * s)) - 1.0) < 0.05
+    assert abs(np.mean(np.diag(C) / np.diag(M)) - 1.0) < 0.1
+    assert abs(np.mean(C[iu] / M[iu]) - 1.0) < 0.1
+
+
+def test_trilinear_reading_lowers_the_field_variance():
+    """Trilinear interpolation of 2 pc cells averages values whose
+    correlation is about 0.8 (the Kolmogorov cusp), so the sampled
+    log-density has less variance and E[exp f] < rho_bar."""
+    A, s, rho, M = _truth_draws(order=1)
+    assert np.mean(A.mean(0) / (rho * s)) < 0.97
+    assert np.mean(np.diag(np.cov(A.T)) / np.diag(M)) < 0.95
