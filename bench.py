@@ -76,12 +76,13 @@ def parse():
     p.add_argument("--no-exact", action="store_true",
                    help="skip the one-step exact-variance comparison")
     p.add_argument("--workload", default="c2",
-                   choices=["c2", "c3", "c4_fields", "sightlines", "pic"],
+                   choices=["c2", "c3", "c4_fields", "sightlines", "pic", "density"],
                    help="c2: the 20,000-star field (bench line); c4_fields: 256 independent "
                         "fields solved together (batched path); sightlines: the dA/ds >= 0 "
                         "conditioning on the 20,000-star posterior (joint sightline "
                         "predictive + exact-HMC sampler); pic: the PIC posterior over 140 "
-                        "inducing points and 36 sub-catalogues (Sect. 4.1 simplified case)")
+                        "inducing points and 36 sub-catalogues (Sect. 4.1 simplified case); "
+                        "density: the pseudo-density map (Sect. 5) on a grid")
     p.add_argument("--sl-predict", type=int, default=256,
                    help="sightlines of the joint-predictive leg (--workload sightlines)")
     p.add_argument("--sl-sample", type=int, default=65536,
@@ -752,6 +753,74 @@ def run_pic(a):
     print(json.dumps(line), flush=True)
 
 
+def run_density(a):
+    """The extinction pseudo-density map of Sect. 5 on the 20k field's
+    posterior after `--sweeps` EP sweeps (computed before timing): for each
+    point of a 16 x 16 x 16 grid (l, b over the field, distance 150-2800 pc
+    geometric) the joint predictive at the point and 10 pc further, and the
+    density's first two moments given A2 > A1 (gm_predict_pairs)."""
+    import torch
+
+    import paper_1708_09705_gb300 as gm
+    from synth import make_catalogue
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    cat = make_catalogue(WORKLOAD, n=a.n, seed=0)
+    cfg = gm.config_from_catalogue(cat, precision=gm.PREC_FP32, probe_factor=a.probe,
+                                   deflate=a.deflate, cg_tol=1e-6)
+    ctx = gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"])
+    ctx.build_cov()
+    ctx.ep_sweep(a.sweeps, 0.0)
+    g = 16
+    L, B, S = np.meshgrid(np.linspace(cat["l"].min(), cat["l"].max(), g),
+                          np.linspace(cat["b"].min(), cat["b"].max(), g),
+                          np.geomspace(150.0, 2800.0, g), indexing="ij")
+    nq = L.size
+    D = {k: torch.tensor(v.ravel(), dtype=torch.float64, device=dev)
+         for k, v in (("l", L), ("b", B), ("s", S))}
+    mean = torch.empty(2 * nq, dtype=torch.float64, device=dev)
+    cov = torch.empty(3 * nq, dtype=torch.float64, device=dev)
+    dens = torch.empty(2 * nq, dtype=torch.float64, device=dev)
+    Lb = gm.lib()
+
+    def step():
+        ctx._check(Lb.gm_predict_pairs(ctx._h, nq, D["l"].data_ptr(), D["b"].data_ptr(),
+                                       D["s"].data_ptr(), 10.0, mean.data_ptr(), cov.data_ptr(),
+                                       dens.data_ptr()))
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ts = []
+    for _ in range(a.steps):
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    kt = ctx.kernel_times()
+    ctx.profile(False)
+    ctx.close()
+    t = sum(ts) / len(ts)
+    d = dens.view(nq, 2).cpu().numpy()
+    line = {"metric": "pseudo-density map points/s (Sect. 5)", "value": nq / t,
+            "unit": "grid points/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}; EP posterior after "
+                                   f"{a.sweeps} sweeps (FP32 form, probed, deflated)",
+                       "grid": "16 x 16 x 16 (l, b over the field; 150-2800 pc geometric)",
+                       "pair_offset_pc": 10.0},
+            "ms_per_step": 1e3 * t,
+            "kernels_ms": {k: [v[0], round(v[1], 3)] for k, v in
+                           sorted(kt.items(), key=lambda kv: -kv[1][1])[:6]},
+            "gpu_launches": int(sum(v[0] for v in kt.values())),
+            "density_finite": bool(np.all(np.isfinite(d)))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.workload == "c3":
@@ -773,6 +842,8 @@ def main():
         run_sightlines(a)
     elif a.workload == "pic":
         run_pic(a)
+    elif a.workload == "density":
+        run_density(a)
     else:
         run_gpu(a)
 
