@@ -69,6 +69,9 @@ def parse():
                         "share one solve (0 = exact, one solve per star)")
     p.add_argument("--deflate", type=int, default=64, choices=[0, 64],
                    help="deflation vectors of the FP32 variance preconditioner (0 = Jacobi)")
+    p.add_argument("--tc-products", type=int, default=6, choices=[6, 3],
+                   help="BF16 products per step of the tensor-core panel product (6: "
+                        "FP32-grade, 3: the mixed form)")
     p.add_argument("--quad", default="gl", choices=["gl", "band"],
                    help="node rule of the covariance quadrature: gl = the workload's "
                         "Gauss-Legendre nodes per sightline (bench line), band = the "
@@ -405,7 +408,7 @@ def run_gpu(a):
     quad = gm.QUAD_BAND if a.quad == "band" else gm.QUAD_GL
     cfg = gm.config_from_catalogue(cat, precision=prec, probe_factor=a.probe, deflate=a.deflate,
                                    cg_tol=1e-6 if a.precision == "fp32" else 1e-10,
-                                   quad_rule=quad)
+                                   quad_rule=quad, tc_products=a.tc_products)
     D = {k: torch.tensor(cat[k], dtype=torch.float64, device=dev)
          for k in ("l", "b", "s", "A_obs", "A_sigma")}
     ctx = gm.ep_init(cfg, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"])
@@ -468,7 +471,8 @@ def run_gpu(a):
     exact = None
     if a.probe > 0 and not a.no_exact:
         cfg_x = gm.config_from_catalogue(cat, precision=prec, probe_factor=0.0,
-                                         deflate=a.deflate, cg_tol=cfg.cg_tol, quad_rule=quad)
+                                         deflate=a.deflate, cg_tol=cfg.cg_tol, quad_rule=quad,
+                                         tc_products=a.tc_products)
         mu_x = torch.empty_like(mu)
         var_x = torch.empty_like(var)
         with gm.ep_init(cfg_x, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"]) as cx:
@@ -550,6 +554,9 @@ def run_gpu(a):
                           "preconditioner": ("Jacobi + spectral deflation with 64 Ritz vectors "
                                              "of the scaled B (per refresh)" if a.deflate
                                              and a.precision == "fp32" else "Jacobi"),
+                          "tensor_products": (f"{a.tc_products} BF16 products per step"
+                                              + (" (mixed form)" if a.tc_products == 3
+                                                 else " (FP32-grade)")),
                           "quadrature": ("band rule (difference/mean coordinates, graded "
                                          "panels, converged)" if a.quad == "band" else
                                          f"{cfg.n_nodes} Gauss-Legendre nodes per sightline"),

@@ -126,6 +126,13 @@ typedef struct {
   int32_t quad_rule;      /* GM_QUAD_GL (default; n_nodes per sightline) or
                              GM_QUAD_BAND (n_nodes unused).  The band rule
                              needs cov_source = GM_COV_QUADRATURE          */
+  int32_t tc_products;    /* BF16 products per step of the FP32 tensor-core
+                             panel product: 6 (default; 0 reads as 6),
+                             FP32-grade products from three-piece splits of
+                             both operands; or 3 (K1 PD2 + K2 PD1 + K1 PD1,
+                             the "mixed" form: half the tensor work, product
+                             errors ~1e-5 relative).  Used by FP32 contexts
+                             on the tensor-core product, ignored otherwise  */
 } gm_config;
 
 /* Device memory hooks.  When given, every device allocation of the context

@@ -268,6 +268,7 @@ static gm_status validate(const gm_config* f) {
   if (f->cov_source != GM_COV_QUADRATURE && f->cov_source != GM_COV_SURROGATE) return GM_E_INVAL;
   if (f->quad_rule != GM_QUAD_GL && f->quad_rule != GM_QUAD_BAND) return GM_E_INVAL;
   if (f->quad_rule == GM_QUAD_BAND && f->cov_source != GM_COV_QUADRATURE) return GM_E_INVAL;
+  if (f->tc_products != 0 && f->tc_products != 3 && f->tc_products != 6) return GM_E_INVAL;
   if (!(f->surrogate_gate > 0)) return GM_E_INVAL;
   if (!(f->probe_factor >= 0) || !std::isfinite(f->probe_factor)) return GM_E_INVAL;
   if (f->deflate != 0 && f->deflate != 64) return GM_E_INVAL;
@@ -301,6 +302,7 @@ void gm_config_default(gm_config* f) {
   f->cov_source = GM_COV_QUADRATURE;
   f->surrogate_gate = 1e-4;
   f->quad_rule = GM_QUAD_GL;
+  f->tc_products = 6;
 }
 
 const char* gm_status_str(gm_status s) {

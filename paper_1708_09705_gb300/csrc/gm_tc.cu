@@ -278,7 +278,9 @@ struct TcPanels {
 };
 
 // PF: gathered panel values are loaded PF steps ahead (indices PF + 1).
-template <int PF>
+// NP: BF16 products per K-step, 6 (FP32-grade) or 3 (K1 PD2 + K2 PD1 +
+// K1 PD1, the "mixed" form).
+template <int PF, int NP>
 __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
     int64_t n, int R, const int64_t* __restrict__ kbase, const int32_t* __restrict__ upad,
     const uint4* __restrict__ img, const float* __restrict__ dv, const float* __restrict__ P,
@@ -409,12 +411,18 @@ __global__ void __launch_bounds__(256, 2) k_panel_spmm_tc(
       const uint64_t A1 = tc_desc(a), A2 = tc_desc(a + kTcA), A3 = tc_desc(a + 2 * kTcA);
       const uint64_t B1 = tc_desc(bb), B2 = tc_desc(bb + kTcB), B3 = tc_desc(bb + 2 * kTcB);
       // small terms first
-      tc_mma(tmem, A3, B1, ks > 0 ? 1u : 0u);
-      tc_mma(tmem, A2, B2, 1u);
-      tc_mma(tmem, A1, B3, 1u);
-      tc_mma(tmem, A2, B1, 1u);
-      tc_mma(tmem, A1, B2, 1u);
-      tc_mma(tmem, A1, B1, 1u);
+      if constexpr (NP == 3) {
+        tc_mma(tmem, A2, B1, ks > 0 ? 1u : 0u);
+        tc_mma(tmem, A1, B2, 1u);
+        tc_mma(tmem, A1, B1, 1u);
+      } else {
+        tc_mma(tmem, A3, B1, ks > 0 ? 1u : 0u);
+        tc_mma(tmem, A2, B2, 1u);
+        tc_mma(tmem, A1, B3, 1u);
+        tc_mma(tmem, A2, B1, 1u);
+        tc_mma(tmem, A1, B2, 1u);
+        tc_mma(tmem, A1, B1, 1u);
+      }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               tc_smem(&mbar[s])));
@@ -477,6 +485,7 @@ __device__ __forceinline__ bool tc_wait_or_abort(uint32_t mbar, uint32_t parity,
   return false;
 }
 
+template <int NP>
 __global__ void __launch_bounds__(288, 2) k_panel_spmm_tc_ws(
     int64_t n, int R, const int64_t* __restrict__ kbase, const int32_t* __restrict__ upad,
     const uint4* __restrict__ img, const float* __restrict__ dv, const float* __restrict__ P,
@@ -605,12 +614,18 @@ __global__ void __launch_bounds__(288, 2) k_panel_spmm_tc_ws(
       const uint32_t a = tc_smem(smem + s * kTcStage), bb = a + 3 * kTcA;
       const uint64_t A1 = tc_desc(a), A2 = tc_desc(a + kTcA), A3 = tc_desc(a + 2 * kTcA);
       const uint64_t B1 = tc_desc(bb), B2 = tc_desc(bb + kTcB), B3 = tc_desc(bb + 2 * kTcB);
-      tc_mma(tmem, A3, B1, ks > 0 ? 1u : 0u);
-      tc_mma(tmem, A2, B2, 1u);
-      tc_mma(tmem, A1, B3, 1u);
-      tc_mma(tmem, A2, B1, 1u);
-      tc_mma(tmem, A1, B2, 1u);
-      tc_mma(tmem, A1, B1, 1u);
+      if constexpr (NP == 3) {
+        tc_mma(tmem, A2, B1, ks > 0 ? 1u : 0u);
+        tc_mma(tmem, A1, B2, 1u);
+        tc_mma(tmem, A1, B1, 1u);
+      } else {
+        tc_mma(tmem, A3, B1, ks > 0 ? 1u : 0u);
+        tc_mma(tmem, A2, B2, 1u);
+        tc_mma(tmem, A1, B3, 1u);
+        tc_mma(tmem, A2, B1, 1u);
+        tc_mma(tmem, A1, B2, 1u);
+        tc_mma(tmem, A1, B1, 1u);
+      }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               tc_smem(&empty[s])));
@@ -756,15 +771,27 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
   const int64_t* kb = (const int64_t*)c->tc_kbase.p;
   const int32_t* up = (const int32_t*)c->tc_upad.p;
   const uint4* im = (const uint4*)c->tc_img.p;
+  if (c->cfg.tc_products == 3) {
+    if (pf == 3)
+      k_panel_spmm_tc_ws<3><<<grid, 288, kTcSmemWs, st>>>(n, R, kb, up, im, dv, P, PD, Q,
+                                                          part_pq, pk, c->d_flags);
+    else if (pf == 2)
+      k_panel_spmm_tc<2, 3><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq,
+                                                        pk, c->d_flags);
+    else
+      k_panel_spmm_tc<1, 3><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq,
+                                                        pk, c->d_flags);
+    return GM_OK;
+  }
   if (pf == 3)
-    k_panel_spmm_tc_ws<<<grid, 288, kTcSmemWs, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
-                                                     c->d_flags);
+    k_panel_spmm_tc_ws<6><<<grid, 288, kTcSmemWs, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq,
+                                                        pk, c->d_flags);
   else if (pf == 2)
-    k_panel_spmm_tc<2><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
-                                                   c->d_flags);
+    k_panel_spmm_tc<2, 6><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
+                                                      c->d_flags);
   else
-    k_panel_spmm_tc<1><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
-                                                   c->d_flags);
+    k_panel_spmm_tc<1, 6><<<grid, 256, kTcSmem, st>>>(n, R, kb, up, im, dv, P, PD, Q, part_pq, pk,
+                                                      c->d_flags);
   return GM_OK;
 }
 
@@ -775,11 +802,17 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
 static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv, const float* P,
                          const float* PD, float* Q, double* part_pq, TcPanels pk) {
   if (c->tc_pf) return GM_OK;
-  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<1>,
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<1, 6>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
-  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<2>,
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<2, 6>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
-  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc_ws,
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc_ws<6>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemWs));
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<1, 3>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<2, 3>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc_ws<3>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemWs));
   if (const char* e = std::getenv("GM_TC_PREFETCH")) {
     const int v = std::atoi(e);

@@ -55,7 +55,7 @@ class Config(C.Structure):
                 ("cg_tol", C.c_double), ("rhs_panel", C.c_int32), ("warm_start", C.c_int32),
                 ("cov_source", C.c_int32), ("deflate", C.c_int32),
                 ("surrogate_gate", C.c_double), ("probe_factor", C.c_double),
-                ("quad_rule", C.c_int32)]
+                ("quad_rule", C.c_int32), ("tc_products", C.c_int32)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

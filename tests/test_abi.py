@@ -44,7 +44,7 @@ def test_status_strings_and_defaults(L):
     assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-4
     assert cfg.probe_factor == 0.0        # exact variances unless asked
     assert cfg.deflate == 0
-    assert cfg.quad_rule == gm.QUAD_GL
+    assert cfg.quad_rule == gm.QUAD_GL and cfg.tc_products == 6
 
 
 def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
@@ -59,7 +59,8 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
     for field, bad in (("sigma2", -1.0), ("n_nodes", 1), ("damping", 0.0), ("cg_tol", 0.0),
                        ("precision", 7), ("outer_scale_pc", float("nan")), ("warm_start", 2),
                        ("probe_factor", -1.0), ("probe_factor", float("inf")),
-                       ("deflate", 5), ("deflate", -64), ("quad_rule", 2)):
+                       ("deflate", 5), ("deflate", -64), ("quad_rule", 2),
+                       ("tc_products", 4)):
         c2 = gm.default_config(**{field: bad})
         assert L.gm_ep_init(C.byref(h), C.byref(c2), 4, x, x, x, x, x, None, None) == 1, field
     # the band rule with the surrogate source is not offered
