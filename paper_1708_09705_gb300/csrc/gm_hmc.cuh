@@ -174,3 +174,116 @@ GM_HD inline unsigned sample_sightline(const double* mu, const double* S, double
 }
 
 }  // namespace gmhmc
+
+// ---------------------------------------------------------------------------
+// The same chain with one warp per sightline (m <= 32): lane i holds point i.
+// A step is a sequence of phases; between phases the lanes synchronise (a
+// warp barrier on the device, lane after lane on the host), and every value a
+// lane reads from another lane goes through the per-warp arrays of WarpState.
+// The arithmetic of each value is the one of sample_sightline (same formulas,
+// same order of the sums), so both give the same chain.
+namespace gmhmc {
+
+constexpr int kWarpMax = 32;
+
+struct WarpState {
+  double* S;   // m x m, both triangles (from the lower one)
+  double* L;   // m x m, lower
+  double y[kWarpMax], w[kWarpMax], p[kWarpMax], t[kWarpMax];
+  double mu[kWarpMax];
+  double t_left, fref;
+  int64_t nhits;
+  unsigned status;
+  int pad;
+};
+
+// Staging by lane i: mu_i, row i of S (from the lower triangle), the start.
+GM_HD inline void w_stage(WarpState& W, int i, int m, const double* mu, const double* S,
+                          int64_t st) {
+  if (i >= m) return;
+  W.mu[i] = mu[(int64_t)i * st];
+  for (int k = 0; k < m; ++k) W.S[i * m + k] = sym(S, m, st, i, k);
+}
+
+// Lane 0: Cholesky factor, start, counters (after w_stage).
+GM_HD inline void w_setup(WarpState& W, int m) {
+  W.status = cholesky(W.S, W.L, m, 1) ? 0u : (unsigned)kNotPD;
+  double run = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double mi = W.mu[i];
+    run = (i == 0 || mi > run) ? mi : run;
+    W.y[i] = (run + 1e-9 * i) - mi;
+  }
+  W.nhits = 0;
+}
+
+// Lane i: its momentum, then (next phase) its velocity w_i = sum_k L_ik p_k.
+GM_HD inline void w_momentum(WarpState& W, int i, int m, const double* pk) {
+  if (i < m) W.p[i] = pk[i];
+}
+GM_HD inline void w_velocity(WarpState& W, int i, int m) {
+  if (i >= m) return;
+  double acc = 0.0;
+  for (int k = 0; k <= i; ++k) acc += W.L[i * m + k] * W.p[k];
+  W.w[i] = acc;
+}
+
+// Lane j < m - 1: the first outward hit of wall j within t_left (or -1).
+GM_HD inline void w_hit(WarpState& W, int j, int m) {
+  if (j + 1 >= m) return;
+  W.t[j] = -1.0;
+  const double a = W.y[j + 1] - W.y[j];
+  const double b = W.w[j + 1] - W.w[j];
+  const double c = W.mu[j + 1] - W.mu[j];
+  const double r = hypot(a, b);
+  if (r <= fabs(c)) return;
+  const double ph = atan2(b, a);
+  const double ac = acos(-c / r);
+  double bt = -1.0;
+  for (int s = 0; s < 2; ++s) {
+    double t = fmod(s == 0 ? ph + ac : ph - ac, kTwoPi);
+    if (t < 0.0) t += kTwoPi;
+    if (t > kHitEps && t <= W.t_left) {
+      const double deriv = -a * sin(t) + b * cos(t);
+      if (deriv < 0.0 && (bt < 0.0 || t < bt)) bt = t;
+    }
+  }
+  W.t[j] = bt;
+}
+
+// Any lane (all compute the same): the earliest wall, lowest index on ties.
+GM_HD inline int w_best(const WarpState& W, int m, double* tb) {
+  int best = -1;
+  double bt = 0.0;
+  for (int j = 0; j + 1 < m; ++j)
+    if (W.t[j] >= 0.0 && (best < 0 || W.t[j] < bt)) {
+      best = j;
+      bt = W.t[j];
+    }
+  *tb = bt;
+  return best;
+}
+
+// Lane i: rotate its own (y_i, w_i) by t.
+GM_HD inline void w_rotate(WarpState& W, int i, int m, double t) {
+  if (i >= m) return;
+  const double ct = cos(t), sn = sin(t);
+  const double yi = W.y[i], wi = W.w[i];
+  W.y[i] = yi * ct + wi * sn;
+  W.w[i] = -yi * sn + wi * ct;
+}
+
+// Lane 0: the reflection factor of wall j from the rotated velocity.
+GM_HD inline void w_reflect_factor(WarpState& W, int m, int j) {
+  const double b = W.w[j + 1] - W.w[j];
+  const double nn = W.S[(j + 1) * m + j + 1] + W.S[j * m + j] - 2.0 * W.S[(j + 1) * m + j];
+  W.fref = 2.0 * b / nn;
+}
+
+// Lane i: mirror its velocity component in wall j.
+GM_HD inline void w_reflect(WarpState& W, int i, int m, int j) {
+  if (i >= m) return;
+  W.w[i] -= W.fref * (W.S[i * m + j + 1] - W.S[i * m + j]);
+}
+
+}  // namespace gmhmc

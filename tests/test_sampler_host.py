@@ -38,6 +38,59 @@ extern "C" unsigned hmc_host(int64_t nsl, int m, const double* mean, const doubl
                                   n_burn, n_samples, &hits[q]);
   return st;
 }
+// the warp kernel's phase sequence, its 32 lanes run one after another
+// between the warp barriers
+extern "C" unsigned hmc_warp_host(int64_t nsl, int m, const double* mean, const double* cov,
+                                  const double* mom, int n_burn, int n_samples, double* out,
+                                  int64_t* hits) {
+  std::vector<double> mu_t(m * nsl), S_t((size_t)m * m * nsl), SL(2 * m * m);
+  for (int64_t q = 0; q < nsl; ++q) {
+    for (int i = 0; i < m; ++i) mu_t[i * nsl + q] = mean[q * m + i];
+    for (int e = 0; e < m * m; ++e) S_t[e * nsl + q] = cov[q * m * m + e];
+  }
+  const int64_t T = n_burn + n_samples;
+  unsigned flags = 0;
+  for (int64_t q = 0; q < nsl; ++q) {
+    gmhmc::WarpState W;
+    W.S = SL.data();
+    W.L = SL.data() + m * m;
+    for (int l = 0; l < 32; ++l) gmhmc::w_stage(W, l, m, &mu_t[q], &S_t[q], nsl);
+    gmhmc::w_setup(W, m);
+    double* o = out + q * (int64_t)n_samples * m;
+    if (W.status) {
+      for (int64_t k = 0; k < (int64_t)n_samples * m; ++k) o[k] = NAN;
+      hits[q] = 0;
+      flags |= 1u;
+      continue;
+    }
+    for (int64_t it = 0; it < T; ++it) {
+      for (int l = 0; l < 32; ++l) gmhmc::w_momentum(W, l, m, mom + (q * T + it) * m);
+      for (int l = 0; l < 32; ++l) gmhmc::w_velocity(W, l, m);
+      W.t_left = gmhmc::kHalfPi;
+      int n = 0;
+      for (; n < gmhmc::kMaxWallHits; ++n) {
+        for (int l = 0; l < 32; ++l) gmhmc::w_hit(W, l, m);
+        double tb;
+        const int j = gmhmc::w_best(W, m, &tb);
+        if (j < 0) {
+          const double tl = W.t_left;
+          for (int l = 0; l < 32; ++l) gmhmc::w_rotate(W, l, m, tl);
+          break;
+        }
+        for (int l = 0; l < 32; ++l) gmhmc::w_rotate(W, l, m, tb);
+        gmhmc::w_reflect_factor(W, m, j);
+        for (int l = 0; l < 32; ++l) gmhmc::w_reflect(W, l, m, j);
+        W.t_left -= tb;
+        W.nhits++;
+      }
+      if (n == gmhmc::kMaxWallHits) flags |= 2u;
+      if (it >= n_burn)
+        for (int l = 0; l < m; ++l) o[(it - n_burn) * m + l] = W.mu[l] + W.y[l];
+    }
+    hits[q] = W.nhits;
+  }
+  return flags;
+}
 """
 
 
@@ -55,17 +108,20 @@ def host_lib(tmp_path_factory):
     vp = C.c_void_p
     L.hmc_host.argtypes = [C.c_int64, C.c_int, vp, vp, vp, C.c_int, C.c_int, vp, vp]
     L.hmc_host.restype = C.c_uint
+    L.hmc_warp_host.argtypes = L.hmc_host.argtypes
+    L.hmc_warp_host.restype = C.c_uint
     return L
 
 
-def run(L, mu, S, mom, burn):
+def run(L, mu, S, mom, burn, warp=False):
     nsl, m = mu.shape
     ns = mom.shape[1] - burn
     out = np.zeros((nsl, ns, m))
     hits = np.zeros(nsl, np.int64)
     mu, S, mom = (np.ascontiguousarray(a, dtype=np.float64) for a in (mu, S, mom))
-    st = L.hmc_host(nsl, m, mu.ctypes.data, S.ctypes.data, mom.ctypes.data, burn, ns,
-                    out.ctypes.data, hits.ctypes.data)
+    fn = L.hmc_warp_host if warp else L.hmc_host
+    st = fn(nsl, m, mu.ctypes.data, S.ctypes.data, mom.ctypes.data, burn, ns,
+            out.ctypes.data, hits.ctypes.data)
     return st, out, hits
 
 
@@ -113,3 +169,28 @@ def test_not_positive_definite_gives_nan_and_status(host_lib):
     st, out, _ = run(host_lib, mu, S, mom, 1)
     assert st == 1
     assert np.all(np.isfinite(out[0])) and np.all(np.isnan(out[1]))
+
+
+@pytest.mark.parametrize("m", [2, 9, 32])
+def test_warp_phases_give_the_thread_chain(host_lib, m):
+    """The warp kernel's phases (one lane per point) run lane by lane give the
+    one-thread chain and the oracle's chain, wall hits included."""
+    rng = np.random.default_rng(40 + m)
+    nsl, burn, ns = 6, 5, 20
+    mu, S = sightlines(rng, nsl, m)
+    mom = rng.standard_normal((nsl, burn + ns, m))
+    st_t, out_t, hits_t = run(host_lib, mu, S, mom, burn)
+    st_w, out_w, hits_w = run(host_lib, mu, S, mom, burn, warp=True)
+    assert st_t == st_w == 0
+    np.testing.assert_array_equal(hits_w, hits_t)
+    np.testing.assert_allclose(out_w, out_t, rtol=0, atol=1e-13)
+    ref = np.array([M.monotone_sightline(mu[q], S[q], ns, None, burn=burn, momenta=mom[q])
+                    for q in range(nsl)])
+    np.testing.assert_allclose(out_w, ref, rtol=0, atol=1e-12)
+
+
+def test_warp_phases_not_positive_definite(host_lib):
+    mu = np.zeros((2, 2))
+    S = np.array([np.eye(2), [[1.0, 2.0], [2.0, 1.0]]])
+    st, out, _ = run(host_lib, mu, S, np.ones((2, 3, 2)), 1, warp=True)
+    assert st == 1 and np.all(np.isnan(out[1])) and np.all(np.isfinite(out[0]))
