@@ -93,6 +93,8 @@ def parse():
     p.add_argument("--sl-points", type=int, default=16, help="points per sightline")
     p.add_argument("--sl-steps", type=int, default=120,
                    help="HMC steps per sightline (the first 20 are burn-in)")
+    p.add_argument("--hmc-warp", action="store_true",
+                   help="sampler with one warp per sightline instead of one thread")
     return p.parse_args()
 
 
@@ -587,6 +589,8 @@ def run_sightlines(a):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    if a.hmc_warp:
+        os.environ["GM_HMC_WARP"] = "1"
     cat = make_catalogue(WORKLOAD, n=a.n, seed=0)
     n = len(cat["s"])
     cfg = gm.config_from_catalogue(cat, precision=gm.PREC_FP32, probe_factor=a.probe,
@@ -681,9 +685,12 @@ def run_sightlines(a):
                                    "points_per_s": nsl * m / res["predict"],
                                    "query_columns": nsl * m * (m - 1)},
             "monotone_sample": {"sightlines": ns_, "steps": T, "burn": burn,
+                                "kernel": "one warp per sightline" if a.hmc_warp
+                                else "one thread per sightline",
                                 "ms": 1e3 * res["sample"],
-                                "k_monotone_hmc_ms": kts["sample"].get("k_monotone_hmc",
-                                                                       (0, 0.0))[1] / a.steps,
+                                "kernel_ms": kts["sample"].get(
+                                    "k_monotone_hmc_warp" if a.hmc_warp else "k_monotone_hmc",
+                                    (0, 0.0))[1] / a.steps,
                                 "wall_hits_per_step": float(hits.double().mean()) / T,
                                 "all_samples_non_decreasing": feasible},
             "cpu_baseline": cpu,
