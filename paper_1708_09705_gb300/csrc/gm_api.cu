@@ -711,10 +711,11 @@ gm_status gm_get_stats(gm_ctx* c, gm_stats* out) {
 
 // Predictive means and variances at nq device-resident points (ql, qb, qs);
 // with pair_cross, rows (2p, 2p + 1) are pairs and pair_cross[p] receives
-// v_{2p+1}^T B^-1 v_{2p}.
+// v_{2p+1}^T B^-1 v_{2p} (cross_group = 2), or rows come in groups of
+// cross_group and pair_cross receives every pair a < b of each group.
 static gm_status predict_points(gm_ctx* c, int64_t nq, const double* ql, const double* qb,
                                 const double* qs, double* mean, double* var,
-                                double* pair_cross) {
+                                double* pair_cross, int cross_group = 2) {
   const size_t nb = nq * sizeof(double);
   // query work arrays: ux, uy, uz, kss, mq (released on every return)
   ScopedDev bq(c, 5 * nb), bqp(c, (nq + 1) * sizeof(int64_t));
@@ -759,7 +760,7 @@ static gm_status predict_points(gm_ctx* c, int64_t nq, const double* ql, const d
   double res = 0;
   c->warm_R = 0;  // the query panels overwrite the saved star solutions
   st = panel_variances(c, nq, qptr, (const int32_t*)qcol.p, qval, kss, var, &it, &res,
-                       pair_cross);
+                       pair_cross, cross_group);
   if (st == GM_OK) st = read_flags(c);
   if (st != GM_OK) return st;
   GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
@@ -978,6 +979,75 @@ __global__ void k_sl_assemble(int64_t nsl, int m, double inv_cut, int taper,
   }
 }
 
+// Grouped sightline inputs: point rows q m + a (direction of sightline q)
+// and the quadrature inputs (s_a, s_c, chord 0) of every pair a < c.
+__global__ void k_sl_group_inputs(int64_t nsl, int m, const double* __restrict__ l,
+                                  const double* __restrict__ b, const double* __restrict__ s,
+                                  double* __restrict__ l2, double* __restrict__ b2,
+                                  double* __restrict__ si, double* __restrict__ sj,
+                                  double* __restrict__ ch, unsigned* __restrict__ bad) {
+  const int64_t np = nsl * m;
+  const int64_t npq = (int64_t)m * (m - 1) / 2;
+  const int64_t total = np > nsl * npq ? np : nsl * npq;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < np) {
+      l2[e] = l[e / m];
+      b2[e] = b[e / m];
+    }
+    if (e < nsl * npq) {
+      const int64_t q = e / npq;
+      int64_t k = e - q * npq;
+      int a = 0;
+      while (k >= m - 1 - a) {
+        k -= m - 1 - a;
+        ++a;
+      }
+      const int c = a + 1 + (int)k;
+      const double sa = s[q * m + a], sc = s[q * m + c];
+      if (!(sc > sa)) atomicOr(bad, 1u);
+      si[e] = sa;
+      sj[e] = sc;
+      ch[e] = 0.0;
+    }
+  }
+}
+
+// Joint predictive of each sightline from its point rows (means, variances)
+// and the grouped cross terms: entry (a, c) = W(|s_c - s_a| / cutoff)
+// k(s_a, s_c) - v_c^T B^-1 v_a.
+__global__ void k_sl_assemble_group(int64_t nsl, int m, double inv_cut, int taper,
+                                    const double* __restrict__ s,
+                                    const double* __restrict__ mp,
+                                    const double* __restrict__ vp,
+                                    const double* __restrict__ cross,
+                                    const double* __restrict__ k12u,
+                                    double* __restrict__ mean_out,
+                                    double* __restrict__ cov_out) {
+  const int64_t npq = (int64_t)m * (m - 1) / 2;
+  const int64_t mm = (int64_t)m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nsl * mm;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / mm;
+    const int r = (int)(e - q * mm);
+    const int a = r / m, c = r - a * m;
+    if (a == c) {
+      cov_out[e] = vp[q * m + a];
+      mean_out[q * m + a] = mp[q * m + a];
+    } else {
+      const int lo = a < c ? a : c, hi = a < c ? c : a;
+      const int64_t p = q * npq + sl_pair_index(m, lo, hi);
+      const double h = (s[q * m + hi] - s[q * m + lo]) * inv_cut;
+      double w = h <= 1.0 ? 1.0 : 0.0;
+      if (taper == GM_TAPER_WENDLAND) {
+        const double u = 1.0 - h;
+        w = h < 1.0 ? u * u * u * u * (4.0 * h + 1.0) : 0.0;
+      }
+      cov_out[e] = w * k12u[p] - cross[p];
+    }
+  }
+}
+
 gm_status gm_predict_sightlines(gm_ctx* c, int64_t nsl, int32_t m, const double* l,
                                 const double* b, const double* s, double* mean_out,
                                 double* cov_out) {
@@ -1008,6 +1078,47 @@ gm_status gm_predict_sightlines(gm_ctx* c, int64_t nsl, int32_t m, const double*
     return GM_OK;
   }
   const int64_t npr = nsl * ((int64_t)m * (m - 1) / 2);  // pairs
+  if (m == 4 || m == 8 || m == 16 || m == 32) {
+    // a sightline's m points are m consecutive query columns of one panel
+    // group (m divides the panel width): every cross term comes from the m
+    // solves, no pair columns
+    // l, b (nsl); s, mean, l2, b2, mp, vp (np); cov (nsl m^2); si, sj, ch, k12, cross (npr)
+    const size_t ndg = 2 * nsl + 6 * np + nsl * mm + 5 * npr;
+    ScopedDev bufg(c, ndg * sizeof(double));
+    double* g = (double*)bufg.p;
+    if (!g) return set_error(c, GM_E_NOMEM, "sightline arrays");
+    double *gl = g, *gb = gl + nsl, *gs = gb + nsl, *gmean = gs + np, *l2 = gmean + np,
+           *b2 = l2 + np, *mp = b2 + np, *vp = mp + np, *gcov = vp + np, *si = gcov + nsl * mm,
+           *sj = si + npr, *ch = sj + npr, *k12 = ch + npr, *cross = k12 + npr;
+    if ((st = copy_in(c, gl, l, nsl * sizeof(double))) != GM_OK ||
+        (st = copy_in(c, gb, b, nsl * sizeof(double))) != GM_OK ||
+        (st = copy_in(c, gs, s, np * sizeof(double))) != GM_OK)
+      return st;
+    GM_CUDA_CHECK(c, cudaMemsetAsync(c->d_flags + 2, 0, sizeof(unsigned), c->stream));
+    GM_PROF(c, "k_sl_group_inputs");
+    k_sl_group_inputs<<<eb(c, std::max(np, npr)), 256, 0, c->stream>>>(
+        nsl, m, gl, gb, gs, l2, b2, si, sj, ch, c->d_flags + 2);
+    GM_LAUNCH_CHECK(c);
+    {
+      unsigned* h = (unsigned*)c->h_pinned;
+      GM_CUDA_CHECK(c, cudaMemcpyAsync(h, c->d_flags + 2, sizeof(unsigned),
+                                       cudaMemcpyDeviceToHost, c->stream));
+      GM_CUDA_CHECK(c, cudaStreamSynchronize(c->stream));
+      if (*h) return set_error(c, GM_E_INVAL, "sightline distances must increase");
+    }
+    st = predict_points(c, np, l2, b2, gs, mp, vp, cross, m);
+    if (st == GM_OK) st = pairlist_quadrature(c, npr, si, sj, ch, k12);
+    if (st != GM_OK) return st;
+    GM_PROF(c, "k_sl_assemble_group");
+    k_sl_assemble_group<<<eb(c, nsl * mm), 256, 0, c->stream>>>(
+        nsl, m, 1.0 / c->cfg.cutoff_pc, c->cfg.taper, gs, mp, vp, cross, k12, gmean, gcov);
+    GM_LAUNCH_CHECK(c);
+    if ((st = read_flags(c)) != GM_OK) return st;
+    if ((st = copy_out(c, mean_out, gmean, np * sizeof(double))) != GM_OK) return st;
+    if ((st = copy_out(c, cov_out, gcov, nsl * mm * sizeof(double))) != GM_OK) return st;
+    c->stats.kernel_launches = c->launches;
+    return GM_OK;
+  }
   // l, b (nsl); s, mean (np); cov (nsl m^2); l2, b2, s2, mean2, var2 (2 npr);
   // si, sj, ch, k12, cross (npr)
   const size_t nd = 2 * nsl + 2 * np + nsl * mm + 15 * npr;

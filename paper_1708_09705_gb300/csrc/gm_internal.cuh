@@ -340,11 +340,14 @@ gm_status panel_spmm_tiled(gm_ctx* c, int64_t n, int R, int nbx, const float* dv
 // Posterior of the current sites: mu, var, alpha (gm_solve.cu).
 gm_status refresh_posterior(gm_ctx* c);
 // Variances k_rr - v_r^T B^-1 v_r for rows of an arbitrary CSR over stars
-// (v_r = S^1/2 k_r); used for the stars themselves and for queries.
+// (v_r = S^1/2 k_r); used for the stars themselves and for queries.  With
+// pair_cross, the cross terms v_b^T B^-1 v_a of consecutive rows: pairs
+// (2p, 2p + 1) when cross_group = 2, else all pairs a < b within groups of
+// cross_group rows (a power of two up to 32, dividing the panel width).
 gm_status panel_variances(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
                           const int32_t* col, const void* val, const double* kdiag_rows,
                           double* var_out, int64_t* iters_out, double* resid_out,
-                          double* pair_cross = nullptr);
+                          double* pair_cross = nullptr, int cross_group = 2);
 gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const void* val, const double* alpha,
                         const double* base, double* out);

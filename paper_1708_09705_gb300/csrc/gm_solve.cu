@@ -713,6 +713,41 @@ __global__ void k_panel_pair_cross(int64_t r0, int64_t n_cols, int R,
   }
 }
 
+// Groups of G consecutive rows (a sightline's points) in one panel group:
+// cross[g * G (G - 1) / 2 + k] = v_b^T B^-1 v_a for the k-th pair a < b of
+// group g (row-major over a), i.e. the far row's entries against the near
+// column's solution.  Rows r0 .. r0 + n_cols - 1 are whole groups.
+template <typename TA, typename TV>
+__global__ void k_panel_group_cross(int64_t r0, int64_t n_cols, int R, int G,
+                                    const int64_t* __restrict__ row_ptr,
+                                    const int32_t* __restrict__ col, const TA* __restrict__ val,
+                                    const double* __restrict__ d64, const TV* __restrict__ X,
+                                    double* __restrict__ cross) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int npq = G * (G - 1) / 2;
+  const int64_t ng = n_cols / G;
+  for (int64_t t = warp; t < ng * npq; t += nw) {
+    const int64_t gl = t / npq;
+    int k = (int)(t - gl * npq), a = 0;
+    while (k >= G - 1 - a) {
+      k -= G - 1 - a;
+      ++a;
+    }
+    const int b = a + 1 + k;
+    const int64_t cn = gl * G + a;         // near column
+    const int64_t rf = r0 + gl * G + b;    // far row
+    double acc = 0;
+    for (int64_t e = row_ptr[rf] + lane; e < row_ptr[rf + 1]; e += 32) {
+      const int32_t j = col[e];
+      acc += d64[j] * (double)val[e] * (double)X[(int64_t)j * R + cn];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) cross[(r0 / G + gl) * npq + (t - gl * npq)] = acc;
+  }
+}
+
 // Probed variances: star r reads its estimate from the column of its colour
 // class (when that class is in this panel).
 template <typename TA, typename TV>
@@ -962,7 +997,7 @@ template <typename TA, typename TV>
 static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                         const void* val, const double* kdiag_rows, double* var_out,
                         int64_t* iters_out, double* resid_out, bool stars,
-                        double* pair_cross = nullptr) {
+                        double* pair_cross = nullptr, int cross_group = 2) {
   const bool warm = stars;
   // probed variances: one column per colour class instead of one per star
   const bool probe = stars && c->probe_colour && c->probe_factor_done > 0 && c->n_fields == 1;
@@ -1116,7 +1151,13 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
                                                 warm ? c->tau : nullptr, var_out, c->d_flags);
     }
     GM_LAUNCH_CHECK(c);
-    if (pair_cross && !probe) {  // R is even: a pair's rows share the group
+    if (pair_cross && !probe && cross_group > 2) {  // G divides R: groups share the panel
+      GM_PROF(c, "k_panel_group_cross");
+      k_panel_group_cross<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, cross_group, row_ptr,
+                                                      col, (const TA*)val,
+                                                      (const double*)ws.d64.p, X, pair_cross);
+      GM_LAUNCH_CHECK(c);
+    } else if (pair_cross && !probe) {  // R is even: a pair's rows share the group
       GM_PROF(c, "k_panel_pair_cross");
       k_panel_pair_cross<TA, TV><<<rb, 256, 0, st>>>(r0, ncols, (int)R, row_ptr, col,
                                                      (const TA*)val, (const double*)ws.d64.p, X,
@@ -1193,14 +1234,15 @@ gm_status refresh_posterior(gm_ctx* c) {
 
 gm_status panel_variances(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                           const void* val, const double* kdiag_rows, double* var_out,
-                          int64_t* iters_out, double* resid_out, double* pair_cross) {
+                          int64_t* iters_out, double* resid_out, double* pair_cross,
+                          int cross_group) {
   gm_status s = prepare_precond(c);
   if (s != GM_OK) return s;
   if (c->cfg.precision == GM_PREC_FP32)
     return panels<float, float>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out,
-                                resid_out, false, pair_cross);
+                                resid_out, false, pair_cross, cross_group);
   return panels<double, double>(c, n_rows, row_ptr, col, val, kdiag_rows, var_out, iters_out,
-                                resid_out, false, pair_cross);
+                                resid_out, false, pair_cross, cross_group);
 }
 
 gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
