@@ -683,7 +683,8 @@ def run_sightlines(a):
                        "distances_pc": "geometric 150-2800"},
             "predict_sightlines": {"sightlines": nsl, "ms": 1e3 * res["predict"],
                                    "points_per_s": nsl * m / res["predict"],
-                                   "query_columns": nsl * m * (m - 1)},
+                                   "query_columns": nsl * m if m in (4, 8, 16, 32)
+                                   else nsl * m * (m - 1)},
             "monotone_sample": {"sightlines": ns_, "steps": T, "burn": burn,
                                 "kernel": "one warp per sightline" if a.hmc_warp
                                 else "one thread per sightline",
