@@ -23,7 +23,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import oracle as O  # noqa: E402
+from oracle import band as Bd  # noqa: E402
 from oracle import density as Dn  # noqa: E402
+from oracle import monotone as Mo  # noqa: E402
 from synth import catalogue_subset, make_catalogue  # noqa: E402
 
 N_EP = 40
@@ -103,7 +105,54 @@ def density_moments():
             f.write(" ".join("%.17e" % v for v in (m1, m2, s11, s22, s12, dm, dv)) + "\n")
 
 
+BAND_CASES = [  # (si, sj, chord^2) in pc, outer scale 20 pc, sigma2 1
+    (40.0, 40.0, 0.0), (1000.0, 1000.0, 0.0), (3000.0, 2950.0, 0.0), (100.0, 120.0, 0.04),
+    (1000.0, 1020.0, 1e-4), (500.0, 480.0, 0.0064),
+]
+BAND_RULE = dict(n=6, h0=1e-3, q=3.0, m0=0.25, K=40.0)
+
+
+def band_rule():
+    path = os.path.join(HERE, "band_rule.txt")
+    g = lambda r: O.g_of_r(r, 1.0, 20.0)  # noqa: E731
+    with open(path, "w") as f:
+        _header(f, [
+            "Sightline double integral R = I / (si sj) of Sect. 3 (lognormal form, sigma2 1,",
+            "outer scale 20 pc) by the band rule of oracle/band.py with 6 nodes per panel,",
+            "first width 1e-3 L0, ratio 3, first m-panel L0/(4c), truncation 40 L0, and by",
+            "the 64-node Gauss-Legendre rule.",
+            "Written by tests/golden/make_golden.py from oracle/.",
+            "columns: si sj chord2 | band R | evaluations | GL64 R",
+        ])
+        for si, sj, c2 in BAND_CASES:
+            R, ev = Bd.pair_R_band(si, sj, c2, g, 20.0, **BAND_RULE)
+            R64 = O.pair_R(np.array([si]), np.array([sj]), np.array([c2]), g, 64)[0]
+            f.write("%.17e %.17e %.17e %.17e %d %.17e\n" % (si, sj, c2, R[0], ev[0], R64))
+
+
+def hmc_chain():
+    path = os.path.join(HERE, "hmc_chain.txt")
+    mu = np.array([-1.0, -1.05, -0.98, -1.02])
+    S = 0.03 * np.exp(-np.abs(np.arange(4)[:, None] - np.arange(4)[None, :]) / 2.0) \
+        + 1e-4 * np.eye(4)
+    mom = np.random.default_rng(20170909).standard_normal((12, 4))
+    x = Mo.monotone_sightline(mu, S, 10, None, burn=2, momenta=mom)
+    with open(path, "w") as f:
+        _header(f, [
+            "Exact HMC for a Gaussian truncated to a non-decreasing sequence (the dA/ds >= 0",
+            "conditioning of Sect. 5; Pakman & Paninski 2014), oracle/monotone.py:",
+            "mu = (-1, -1.05, -0.98, -1.02), S_ij = 0.03 exp(-|i - j| / 2) + 1e-4 delta_ij,",
+            "momenta = numpy default_rng(20170909).standard_normal((12, 4)), 2 burn-in steps.",
+            "Written by tests/golden/make_golden.py from oracle/.",
+            "rows: the 10 samples (4 points each)",
+        ])
+        for row in x:
+            f.write(" ".join("%.17e" % v for v in row) + "\n")
+
+
 if __name__ == "__main__":
     ep_posterior()
     tilted_moments()
     density_moments()
+    band_rule()
+    hmc_chain()

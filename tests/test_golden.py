@@ -77,3 +77,33 @@ def test_density_moments_fixture():
         got = Dn.density_moments(np.array([m1, m2]), S, 10.0)
         assert got == pytest.approx((dm, dv), rel=1e-12)
         assert dm > 0 and dv > 0   # A2 > A1 makes the density positive
+
+
+def test_band_rule_fixture():
+    """The oracle's band rule keeps its stored values and node counts; on the
+    stored diagonals the 64-node rule differs from it as the 1-D reduction
+    says it must (more than 30 % at 1000 pc)."""
+    from oracle import band as Bd
+    t = _table("band_rule.txt")
+    g = lambda r: O.g_of_r(r, 1.0, 20.0)  # noqa: E731
+    rule = dict(n=6, h0=1e-3, q=3.0, m0=0.25, K=40.0)
+    for si, sj, c2, R, ev, R64 in t:
+        got, n = Bd.pair_R_band(si, sj, c2, g, 20.0, **rule)
+        assert got[0] == pytest.approx(R, rel=1e-12)
+        assert n[0] == int(ev)
+    diag1000 = t[(t[:, 0] == 1000.0) & (t[:, 1] == 1000.0)][0]
+    assert diag1000[5] / diag1000[3] - 1 > 0.3
+
+
+def test_hmc_chain_fixture():
+    """The oracle's exact-HMC chain for the stored input and momenta, and the
+    constraint on every stored sample."""
+    from oracle import monotone as Mo
+    t = _table("hmc_chain.txt")
+    assert np.all(np.diff(t, axis=1) >= 0)
+    mu = np.array([-1.0, -1.05, -0.98, -1.02])
+    S = 0.03 * np.exp(-np.abs(np.arange(4)[:, None] - np.arange(4)[None, :]) / 2.0) \
+        + 1e-4 * np.eye(4)
+    mom = np.random.default_rng(20170909).standard_normal((12, 4))
+    x = Mo.monotone_sightline(mu, S, 10, None, burn=2, momenta=mom)
+    np.testing.assert_allclose(x, t, rtol=0, atol=1e-12)
