@@ -466,3 +466,39 @@ def predict(cat, K, m, tau, nu, lq, bq, sq, form=FORM_LOGNORMAL,
     V = linalg.solve_triangular(L, sqt[:, None] * Ks.T, lower=True)
     var = kss - (V * V).sum(axis=0)
     return mean, var
+
+
+def posterior_sampled(K, m, tau, nu, idx, tol=1e-12):
+    """Posterior mean of every star and marginal variances of the stars idx
+    for prior N(m, K) (K a scipy sparse matrix) times the sites, through the
+    same regression form as `posterior` with B = I + S^1/2 K S^1/2 solved by
+    scipy's conjugate gradient (relative residual tol) instead of a dense
+    Cholesky factor: mu = m + K (b - S^1/2 B^-1 S^1/2 K b), b = nu - tau m, and
+    Sigma_ii = K_ii - v_i^T B^-1 v_i with v_i = S^1/2 K e_i.  For catalogues
+    whose dense covariance does not fit."""
+    from scipy.sparse import diags
+    from scipy.sparse.linalg import LinearOperator, cg
+    tau = np.asarray(tau, dtype=np.float64)
+    n = len(tau)
+    sq = np.sqrt(tau)
+    S = diags(sq)
+    Bop = LinearOperator((n, n), matvec=lambda v: v + sq * (K @ (sq * v)), dtype=np.float64)
+    dB = 1.0 + tau * K.diagonal()
+    M = LinearOperator((n, n), matvec=lambda v: v / dB, dtype=np.float64)
+
+    def solve(rhs):
+        x, info = cg(Bop, rhs, rtol=tol, atol=0.0, maxiter=20 * n, M=M)
+        if info != 0:
+            raise RuntimeError("CG did not converge")
+        return x
+
+    b = nu - tau * m
+    y = solve(sq * (K @ b))
+    mu = m + K @ (b - sq * y)
+    var = np.empty(len(idx))
+    for k, i in enumerate(idx):
+        e = np.zeros(n)
+        e[i] = 1.0
+        v = S @ (K @ e)
+        var[k] = K[i, i] - v @ solve(v)
+    return mu, var

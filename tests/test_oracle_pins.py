@@ -274,3 +274,17 @@ def test_ep_two_stars_against_exact_posterior():
     assert r["max_delta"] < 1e-12
     assert np.all(np.abs(r["mu"] - mu) < 0.01 * np.sqrt(var))
     assert np.all(np.abs(r["var"] / var - 1) < 0.02)
+
+
+def test_sampled_posterior_equals_dense_posterior(small_cat):
+    """The sparse-solve posterior (for catalogues whose dense K does not fit)
+    reproduces the dense-Cholesky posterior."""
+    cs = O.build_cov(small_cat, dense=False)
+    cd = O.build_cov(small_cat)
+    r = O.ep_run(cd["K"], cd["m"], small_cat["A_obs"], small_cat["A_sigma"], max_sweeps=3,
+                 tol=0.0)
+    idx = np.array([0, 5, 77, 149])
+    mu, var = O.posterior_sampled(cs["K"], cs["m"], r["tau"], r["nu"], idx)
+    mu0, v0, _ = O.posterior(cd["K"], cd["m"], r["tau"], r["nu"])
+    np.testing.assert_allclose(mu, mu0, rtol=1e-9, atol=1e-10)
+    np.testing.assert_allclose(var, v0[idx], rtol=1e-9)
