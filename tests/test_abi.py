@@ -86,3 +86,21 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
     blk = (C.c_int32 * 4)(0, 0, 1, 1)
     assert L.gm_pic_posterior(None, 2, blk, 2, x, x, x, x, x) == 1
     assert L.gm_pic_predict(None, 2, blk, x, x, x, x, x) == 1
+
+
+def test_header_is_plain_c99(tmp_path):
+    """include/gmead.h is a C header: it compiles as strict C99 (no C++ in the
+    declarations, fixed-width types only)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "gmead.h"\n'
+                   "int main(void) { gm_config c; gm_stats s;\n"
+                   "  gm_config_default(&c); s.nnz = 0;\n"
+                   "  return c.n_nodes < 0 || s.nnz != 0; }\n")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    f"-I{os.path.join(ROOT, 'include')}", "-c", str(src), "-o",
+                    str(tmp_path / "use.o")], check=True)
