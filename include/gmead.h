@@ -419,11 +419,13 @@ gm_status gm_surrogate_eval(gm_ctx* ctx, int64_t n, const double* si, const doub
  *   stream     : cudaStream_t to run on (NULL = legacy default stream)
  *   max_delta_out, skipped_out : host pointers (may be NULL) receiving the
  *                largest relative site change and the number of skipped stars
- * All arrays must be DEVICE pointers of length n (host pointers: GM_E_INVAL).
+ * All arrays must be DEVICE pointers of the current device (or managed
+ * memory), length n; host pointers and memory of another GPU: GM_E_INVAL.
  * The scratch is a file-scope device array of about 66 KB that every GPU
  * loading the library keeps until the process exits.  The first call on a
- * device resolves its address and uploads the Gauss-Hermite rule with
- * synchronous copies, so make that first call before any stream capture.
+ * device (and the first after a device reset) uploads the Gauss-Hermite rule
+ * with a synchronous copy and a device synchronisation, so make that first
+ * call before any stream capture.
  * All calls share the array: calls whose work overlaps on the GPU race with
  * one another, so serialise them.  The call synchronises `stream` and
  * returns GM_E_NONFINITE if a non-finite value appeared. */

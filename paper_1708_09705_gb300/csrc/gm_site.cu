@@ -191,6 +191,10 @@ static __device__ __align__(256) double g_na_scratch[kNaSlots];
 // Scratch layout (doubles): [0, kGH) nodes, [kGH, 2 kGH) weights * exp(x^2),
 // [2 kGH, 2 kGH + kNaMaxBlocks) per-block maxima, then the skip counter
 // (as an unsigned 64-bit word), the flags word and the reduced maximum.
+// Per device, the scratch address at which the rule was last uploaded.  The
+// address is resolved again on every call, so a module reloaded after a
+// device reset (new address) gets its rule uploaded again instead of a stale
+// pointer being used.
 static double* g_na_ptr[kNaMaxDevices] = {nullptr};
 
 __global__ void k_na_reduce_max(int nb, const double* __restrict__ part, double* __restrict__ out) {
@@ -207,38 +211,44 @@ __global__ void k_na_reduce_max(int nb, const double* __restrict__ part, double*
   }
 }
 
-static bool na_device_ptr(const void* p) {
+// Device memory of the current device `dev`, or managed memory.  Memory of
+// another GPU is refused: without peer access the kernel could not read it.
+static bool na_device_ptr(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
-// First call on a device: resolve the device address of the scratch array
-// (the host-side name is only a stand-in) and upload the Gauss-Hermite rule.
-// Serialised by a mutex; uses synchronous copies, so it must not run inside
-// a stream capture.
+// Resolves the device address of the scratch array on the current device
+// (the host-side name is only a stand-in) on every call, and uploads the
+// Gauss-Hermite rule when that address has not seen it yet (first call on a
+// device, or a module reloaded after a device reset).  The upload is a
+// synchronous copy followed by a device synchronisation, so the rule is on
+// the device before any kernel on any stream (a non-blocking one included)
+// can read it; that first call therefore must not run inside a stream
+// capture.  Serialised by a mutex.
 static gm_status na_setup(int dev, double** out) {
   static std::mutex mu;
   std::lock_guard<std::mutex> lock(mu);
-  if (g_na_ptr[dev]) {
-    *out = g_na_ptr[dev];
-    return GM_OK;
-  }
   double* p = nullptr;
   if (cudaGetSymbolAddress((void**)&p, g_na_scratch) != cudaSuccess || !p) {
     cudaGetLastError();
     return GM_E_CUDA;
   }
-  double rule[2 * kGH];
-  gauss_hermite(kGH, rule, rule + kGH);
-  if (cudaMemcpy(p, rule, sizeof(rule), cudaMemcpyHostToDevice) != cudaSuccess) {
-    cudaGetLastError();
-    return GM_E_CUDA;
+  if (g_na_ptr[dev] != p) {
+    double rule[2 * kGH];
+    gauss_hermite(kGH, rule, rule + kGH);
+    if (cudaMemcpy(p, rule, sizeof(rule), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+      cudaGetLastError();
+      return GM_E_CUDA;
+    }
+    g_na_ptr[dev] = p;
   }
-  g_na_ptr[dev] = p;
   *out = p;
   return GM_OK;
 }
@@ -255,14 +265,14 @@ extern "C" gm_status gm_site_update_noalloc(int64_t n, const double* mu, const d
   if (!mu || !var || !obs || !obs_sigma || !tau || !nu) return GM_E_INVAL;
   if (likelihood != GM_LIK_GAUSS_IN_A && likelihood != GM_LIK_GAUSS_IN_LNA) return GM_E_INVAL;
   if (!(damping > 0 && damping <= 1) || !(vc_floor >= 0)) return GM_E_INVAL;
-  for (const void* p : {(const void*)mu, (const void*)var, (const void*)obs,
-                        (const void*)obs_sigma, (const void*)tau, (const void*)nu})
-    if (!na_device_ptr(p)) return GM_E_INVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
     cudaGetLastError();
     return GM_E_CUDA;
   }
+  for (const void* p : {(const void*)mu, (const void*)var, (const void*)obs,
+                        (const void*)obs_sigma, (const void*)tau, (const void*)nu})
+    if (!na_device_ptr(p, dev)) return GM_E_INVAL;
   double* base = nullptr;
   gm_status st = na_setup(dev, &base);
   if (st != GM_OK) return st;

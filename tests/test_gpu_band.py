@@ -1,10 +1,5 @@
 """Band-rule covariance quadrature on the GPU (quad_rule = GM_QUAD_BAND)
-against the oracle's band rule (oracle/band.py) with the device constants.
-
-Not collected (the file name does not match test_*.py): the GPU parity
-tests of the band-rule covariance quadrature, whose device routines are so far checked against the
-oracle only through host builds.  The file becomes tests/test_gpu_band.py
-with its first run on a GPU."""
+against the oracle's band rule (oracle/band.py) with the device constants."""
 import numpy as np
 import pytest
 

@@ -1,10 +1,5 @@
 """The mixed form of the tensor-core panel product (tc_products = 3) on the
-GPU against the FP32-grade form and the FP64 path.
-
-Not collected (the file name does not match test_*.py): the kernels with
-three products per step are so far only compiled; a CPU emulation of the
-FP32 variance solves put the EP-level error of this form at 7.6e-7 in mean
-ln A.  The file becomes tests/test_gpu_mixed.py with its first run on a GPU."""
+GPU against the FP32-grade form and the FP64 path."""
 import numpy as np
 import pytest
 

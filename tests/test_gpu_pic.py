@@ -1,10 +1,5 @@
 """PITC / PIC posterior over inducing points on the GPU (gm_pic_posterior)
-against oracle/pic.py.
-
-Not collected (the file name does not match test_*.py): the GPU parity
-tests of the PIC posterior and predictive, whose device routines are so far checked against the
-oracle only through host builds.  The file becomes tests/test_gpu_pic.py
-with its first run on a GPU."""
+against oracle/pic.py."""
 import numpy as np
 import pytest
 

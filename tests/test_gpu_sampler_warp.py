@@ -1,10 +1,5 @@
 """The warp-per-sightline sampler (GM_HMC_WARP=1) on the GPU against the
-one-thread sampler and the oracle's chain.
-
-Not collected (the file name does not match test_*.py): the warp kernel's
-phases are so far checked only through a host build that runs its 32 lanes
-one after another (tests/test_sampler_host.py).  The file becomes
-tests/test_gpu_sampler_warp.py with its first run on a GPU."""
+one-thread sampler and the oracle's chain."""
 import numpy as np
 import pytest
 

@@ -1,11 +1,6 @@
 """The grouped path of gm_predict_sightlines (m = 4, 8, 16 or 32 points per
 sightline: the points of a sightline share one panel group and their cross
-terms come from the m solves) on the GPU against the oracle.
-
-Not collected (the file name does not match test_*.py): the grouped
-cross-term kernel's indexing is so far checked on the CPU against the
-oracle's joint predictive.  The file becomes
-tests/test_gpu_sightline_group.py with its first run on a GPU."""
+terms come from the m solves) on the GPU against the oracle."""
 import numpy as np
 import pytest
 

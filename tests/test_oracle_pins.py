@@ -288,3 +288,83 @@ def test_sampled_posterior_equals_dense_posterior(small_cat):
     mu0, v0, _ = O.posterior(cd["K"], cd["m"], r["tau"], r["nu"])
     np.testing.assert_allclose(mu, mu0, rtol=1e-9, atol=1e-10)
     np.testing.assert_allclose(var, v0[idx], rtol=1e-9)
+
+
+# ------------------------------------------------- prior moments of ln A
+def _normal_expect(fn, m, v):
+    """E[fn(a)] for a ~ N(m, v) by adaptive quadrature of the density."""
+    sd = math.sqrt(v)
+    val, _ = integrate.quad(lambda z: fn(m + sd * z) * math.exp(-0.5 * z * z),
+                            -40.0, 40.0, epsabs=0, epsrel=1e-13, limit=400)
+    return val / math.sqrt(2.0 * math.pi)
+
+
+@pytest.mark.parametrize("s", [40.0, 300.0, 3000.0])
+def test_prior_mean_and_variance_reproduce_extinction_moments(s):
+    """Sect. 3 model: rho = e^f with E rho = rho_bar, so A = int_0^s rho dt has
+    E[A] = rho_bar s and Var[A] = rho_bar^2 I_ss (I the double sightline
+    integral of expm1(sigma2 phi)).  The lognormal form's prior N(m, K_ss) of
+    a = ln A must reproduce both moments of A = e^a; the expectations are taken
+    by integrating the normal density, not from the lognormal formulae."""
+    rho_bar, sigma2, L0 = 1e-3, 1.0, 20.0
+    cat = dict(l=np.array([0.3]), b=np.array([0.01]), s=np.array([s]), sigma2=sigma2,
+               outer_scale_pc=L0, rho_bar=rho_bar, cutoff_pc=3 * L0, n_nodes=64)
+    cv = O.build_cov(cat)
+    m, Kss = float(cv["m"][0]), float(cv["diag"][0])
+    R = float(O.pair_R([s], [s], [0.0], lambda r: O.g_of_r(r, sigma2, L0), 64)[0])
+    EA = _normal_expect(math.exp, m, Kss)
+    EA2 = _normal_expect(lambda a: math.exp(2 * a), m, Kss)
+    assert EA == pytest.approx(rho_bar * s, rel=1e-10)
+    assert EA2 - EA * EA == pytest.approx((rho_bar * s) ** 2 * R, rel=1e-9)
+    assert Kss > 0.01   # large enough that a slip of K/2 in m would show
+
+
+def test_linear_form_prior_mean_is_mean_log_density():
+    """First-order form: a ~ ln s + (1/s) int f dt, so E[a] = ln s + E[f], with
+    E[f] fixed by E[e^f] = rho_bar for f ~ N(E f, sigma2) (root-found here)."""
+    from scipy import optimize
+    rho_bar, sigma2 = 1e-3, 0.7
+    mu_f = optimize.brentq(lambda mu: _normal_expect(math.exp, mu, sigma2) - rho_bar, -20, 0,
+                           xtol=1e-14)
+    s = np.array([100.0, 900.0])
+    cat = dict(l=np.array([0.3, 0.3001]), b=np.array([0.01, 0.02]), s=s, sigma2=sigma2,
+               outer_scale_pc=20.0, rho_bar=rho_bar, cutoff_pc=60.0, n_nodes=16)
+    m = O.build_cov(cat, form=O.FORM_LINEAR)["m"]
+    np.testing.assert_allclose(m, np.log(s) + mu_f, rtol=0, atol=1e-10)
+
+
+# ----------------------------------------------------------- the taper
+def test_wendland_values_at_tabulated_points():
+    """Wendland (1995) psi_{3,1}(h) = (1-h)_+^4 (4h+1); values worked by hand."""
+    h = np.array([0.0, 0.25, 0.5, 0.75, 0.9, 1.0, 1.5])
+    want = np.array([1.0, 0.6328125, 0.1875, 0.015625, 0.00046, 0.0, 0.0])
+    np.testing.assert_allclose(O.wendland(h), want, rtol=1e-14, atol=0)
+
+
+def test_wendland_polynomial_structure():
+    """psi_{3,1} is one quintic on [0, 1]: 1 - 10h^2 + 20h^3 - 15h^4 + 4h^5.
+    No linear term and a cubic one: as a radial function of R^3 it is C^2 but
+    not C^3 at the origin; at h = 1 it vanishes to fourth order.  The
+    coefficients are recovered by a least-squares fit on [0, 1]."""
+    h = np.linspace(0.0, 1.0, 41)
+    coef = np.polynomial.polynomial.polyfit(h, O.wendland(h), 7)
+    np.testing.assert_allclose(coef, [1, 0, -10, 20, -15, 4, 0, 0], rtol=0, atol=1e-8)
+    assert np.all(O.wendland(np.array([1.0, 1.0 + 1e-12, 2.0, 10.0])) == 0.0)
+
+
+def _radial_ft3(f, k):
+    """Isotropic 3-D Fourier transform of a radial function supported in
+    [0, 1]: (4 pi / k) int_0^1 r f(r) sin(k r) dr."""
+    v, _ = integrate.quad(lambda r: r * f(r), 0.0, 1.0, weight="sin", wvar=k, limit=200)
+    return 4.0 * math.pi / k * v
+
+
+def test_wendland_is_positive_definite_in_3d():
+    """The taper must be positive definite in R^3 (so K o W stays PD): its 3-D
+    Fourier transform is non-negative.  The same check rejects the R^1 member
+    psi_{2,1} = (1-h)^3 (3h+1), whose transform goes negative."""
+    ks = np.linspace(0.1, 120.0, 1200)
+    F = np.array([_radial_ft3(lambda r: float(O.wendland(np.array([r]))[0]), k) for k in ks])
+    assert F.min() > -1e-12
+    F21 = np.array([_radial_ft3(lambda r: (1 - r) ** 3 * (3 * r + 1), k) for k in ks])
+    assert F21.min() < -1e-4
