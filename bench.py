@@ -291,6 +291,8 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
              ("probed_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6, probe_factor=2.0)),
              ("probed_deflated_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
                                            probe_factor=2.0, deflate=64)),
+             ("mixed_probed_deflated", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
+                                            probe_factor=2.0, deflate=64, tc_products=3)),
              ("learned_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
                                    cov_source=gm.COV_SURROGATE))]
     for name, kw in forms:
@@ -331,8 +333,10 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
     return {"stars": n_sub, "sweeps": sweeps, "forms": out,
             "equal_error_bar": "1e-3 in mean ln A vs the FP64 plain form",
             "notes": "plain = exact variances (one solve per star); probed = colour classes "
-                     "2 cutoffs apart share a solve; learned = surrogate K with quadrature "
-                     "fallback at the gate"}
+                     "2 cutoffs apart share a solve; mixed = the variance panels' tensor-core "
+                     "product with three BF16 products per step (K1 PD1 + K1 PD2 + K2 PD1) "
+                     "instead of six; learned = surrogate K with quadrature fallback at the "
+                     "gate"}
 
 
 def run_fields(a):
@@ -351,8 +355,8 @@ def run_fields(a):
     fid = np.concatenate([np.full(len(f["s"]), i, dtype=np.int32) for i, f in enumerate(fields)])
     L0 = np.array([f["outer_scale_pc"] for f in fields])
     n = len(fid)
-    cfg = gm.default_config(sigma2=1.0, rho_bar=1e-3, n_nodes=64, precision=gm.PREC_FP32,
-                            cg_tol=1e-6, probe_factor=a.probe)
+    cfg = gm.default_config(sigma2=1.0, rho_bar=1e-3, n_nodes=64, quad_rule=gm.QUAD_GL,
+                            precision=gm.PREC_FP32, cg_tol=1e-6, probe_factor=a.probe)
     ctx = gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"],
                      field_id=fid, field_L0=L0, field_cutoff=3 * L0)
     for _ in range(a.warmup):

@@ -123,9 +123,11 @@ typedef struct {
                              error is the neglected cross terms, which decay
                              with the distance (measured 4e-8 relative at
                              2 x cutoff on a 20,000-star 5-degree field)      */
-  int32_t quad_rule;      /* GM_QUAD_GL (default; n_nodes per sightline) or
-                             GM_QUAD_BAND (n_nodes unused).  The band rule
-                             needs cov_source = GM_COV_QUADRATURE          */
+  int32_t quad_rule;      /* GM_QUAD_BAND (default: the converged band rule;
+                             n_nodes unused) or GM_QUAD_GL (n_nodes
+                             Gauss-Legendre nodes per sightline).  With
+                             cov_source = GM_COV_SURROGATE the rule is the
+                             surrogate's training target and its fallback  */
   int32_t tc_products;    /* BF16 products per step of the FP32 tensor-core
                              panel product: 6 (default; 0 reads as 6),
                              FP32-grade products from three-piece splits of
@@ -315,6 +317,49 @@ gm_status gm_pic_posterior(gm_ctx* ctx, int32_t n_blocks, const int32_t* block_o
  * queries (radians, pc); mean_out, var_out: nq.  All host or device. */
 gm_status gm_pic_predict(gm_ctx* ctx, int64_t nq, const int32_t* q_block, const double* l,
                          const double* b, const double* s, double* mean_out, double* var_out);
+
+/* Mean function of the extinction pseudo-density (Sect. 5 set-up): an
+ * exponential disc plus a Gaussian bump along the line of sight,
+ *   rho(x) = rho0 exp(-(R(x) - R_sun)/L - |z|/H) + A_b N(|x|; s_b, w^2),
+ * x heliocentric (pc, x_1 towards the Galactic centre, x_3 towards the north
+ * Galactic pole), R(x) = |(R_sun - x_1, x_2)|.  The prior mean of ln A_i
+ * becomes ln E[A_i] - K_ii/2 with E[A_i] the line integral of rho (disc by a
+ * 64-node Gauss-Legendre rule, bump in closed form); the covariance stays
+ * that of the stationary relative fluctuations.  Applied to the stars now
+ * (if the covariance is built) and by every later gm_build_cov and
+ * prediction.  theta = {L, H, rho0, s_b, A_b} (pc, pc, mag/pc, pc, mag), all
+ * > 0 (host); r_sun_pc, bump_width_pc > 0.  theta = NULL restores the
+ * constant mean density rho_bar.  One-field contexts only (GM_E_STATE). */
+gm_status gm_set_mean_fn(gm_ctx* ctx, const double* theta, double r_sun_pc,
+                         double bump_width_pc);
+
+/* Learning phase for the five mean-function hyperparameters (Sect. 2, eq.
+ * example_learning; Sect. 4.1 simplified case; Sect. 5 log-normal
+ * hyperpriors).  Needs likelihood GM_LIK_GAUSS_IN_LNA and the lognormal form
+ * (GM_E_INVAL otherwise) and a built covariance (GM_E_STATE).  The marginal
+ * likelihood is then exact, atilde ~ N(m(theta), K + Sigma), and the mode of
+ * ln p(theta | atilde) in phi = ln theta is found by Newton steps (gradient
+ * J^T (K + Sigma)^-1 (atilde - m) - (phi - mu)/s^2 from one posterior-mean
+ * solve; Hessian by central differences of the gradient, step 1e-4 in phi,
+ * shifted until positive definite; steps halved until the log posterior
+ * rises) until the largest step is below tol or max_iter steps.
+ *   theta0      : starting point (5 values > 0)
+ *   prior_mean, prior_sd : log-normal hyperprior of each parameter, given by
+ *                 its mean and standard deviation (natural units; the paper
+ *                 takes sd = mean)
+ *   theta_out   : the mode (5); cov_out (may be NULL): the Laplace
+ *                 covariance of phi = ln theta at the mode (5 x 5 row-major);
+ *   log_post_out (may be NULL): -1/2 r^T (K + Sigma)^-1 r + ln p(phi) there
+ *                 (the theta-dependent part of the log posterior);
+ *   iters_out (may be NULL): Newton steps taken.
+ * All host pointers.  On return the context holds the mean function at the
+ * mode (as after gm_set_mean_fn), the exact Gaussian sites tau = 1/sigma^2,
+ * nu = atilde/sigma^2, and the posterior mean for them; the variances are
+ * recomputed by the next call that needs them. */
+gm_status gm_learn_mean(gm_ctx* ctx, const double* theta0, const double* prior_mean,
+                        const double* prior_sd, double r_sun_pc, double bump_width_pc,
+                        int32_t max_iter, double tol, double* theta_out, double* cov_out,
+                        double* log_post_out, int32_t* iters_out);
 
 /* Marginal posterior mean and variance of ln A for every star under the
  * current sites (refreshed if the sites changed).  Length n each. */

@@ -459,7 +459,8 @@ static gm_status pack_setup(gm_ctx* c) {
 static void launch_spmm(gm_ctx* c, PackState& S, int wpb, cudaStream_t st, const float* dv) {
   if (S.n_tc_items > 0) {
     panel_spmm_tc_packed(c, S.n_tc_items, S.tc_items, S.tc_base, S.tc_width, dv,
-                         (const float*)S.Pp.p, (const float*)S.PD.p, (float*)S.Q.p, st, false);
+                         (const float*)S.Pp.p, (const float*)S.PD.p, (float*)S.Q.p,
+                         (int64_t)(S.PD.bytes / sizeof(float)), st, false);
     return;
   }
   const int sms = sm_count(c);
@@ -484,7 +485,7 @@ static gm_status autotune(gm_ctx* c, PackState& S, const float* dv) {
   if (S.n_tc_items > 0)
     return panel_spmm_tc_packed(c, S.n_tc_items, S.tc_items, S.tc_base, S.tc_width, dv,
                                 (const float*)S.Pp.p, (const float*)S.PD.p, (float*)S.Q.p,
-                                c->stream, true);
+                                (int64_t)(S.PD.bytes / sizeof(float)), c->stream, true);
   if (S.wpb) return GM_OK;
   if (const char* env = std::getenv("GM_PANEL_WARPS")) {
     const int w = std::atoi(env);

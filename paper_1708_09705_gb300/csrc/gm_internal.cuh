@@ -126,6 +126,7 @@ struct gm_ctx {
   // K-step prefix per block, padded union columns, BF16 operand images
   int64_t tc_nblk = 0, tc_nks = 0;
   gm::Buffer tc_kbase, tc_upad, tc_img;
+  gm::Buffer tc_planes;             // BF16 planes of the panel PD (async tile product)
   std::vector<int64_t> h_tc_boff;   // first tile block of each field (n_fields + 1)
   gm::Buffer tc_brow0, tc_boffd;    // first row of each block (+ end); device h_tc_boff
   int tc_pf = 0;                    // tuned prefetch depth of the tile product (0: untuned)
@@ -161,6 +162,13 @@ struct gm_ctx {
   int32_t* probe_colour = nullptr;
   std::vector<int32_t> h_probe_ncol;
   double probe_factor_done = 0;  // probe_factor the colouring was made for
+
+  // ---- mean function of the density (exponential disc + bump of Sect. 5),
+  // set by gm_set_mean_fn / gm_learn_mean; off: constant mean density rho_bar
+  bool mean_fn_on = false;
+  double mean_theta[5] = {0, 0, 0, 0, 0};  // L, H, rho0, s_bump, A_bump
+  double mean_rsun = 0, mean_w = 0;
+  gm::Buffer mf_J, mf_gl, mf_part;        // Jacobian, 64-node rule, partials
 
   // ---- status flags and pinned readback
   unsigned* d_flags = nullptr;
@@ -308,8 +316,8 @@ gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const floa
 // (on the context stream, outside any graph capture) instead of launching.
 gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
                                const int64_t* blk_base, const int32_t* blk_width, const float* dv,
-                               const float* P, const float* PD, float* Q, cudaStream_t st,
-                               bool tune);
+                               const float* P, const float* PD, float* Q, int64_t pd_elems,
+                               cudaStream_t st, bool tune);
 
 // Q = B P for an n x R FP32 panel with PD = d o P given (the variance panels'
 // product); part: max(tile blocks, ceil(n / 8)) x R doubles of scratch.
@@ -339,6 +347,15 @@ gm_status panel_spmm_tiled(gm_ctx* c, int64_t n, int R, int nbx, const float* dv
 
 // Posterior of the current sites: mu, var, alpha (gm_solve.cu).
 gm_status refresh_posterior(gm_ctx* c);
+// posterior mean only (alpha and mu) for the current sites and prior mean
+gm_status posterior_mean_only(gm_ctx* c);
+// device status flags -> status (and cleared)
+gm_status read_flags(gm_ctx* c);
+// prior mean from the mean function at n points: m = ln E[A] - kss/2;
+// J (5 columns of n, may be null) = dm / d ln theta  (gm_learn.cu)
+gm_status mean_fn_apply(gm_ctx* c, int64_t n, const double* s, const double* ux,
+                        const double* uy, const double* uz, const double* kss, double* m,
+                        double* J);
 // Variances k_rr - v_r^T B^-1 v_r for rows of an arbitrary CSR over stars
 // (v_r = S^1/2 k_r); used for the stars themselves and for queries.  With
 // pair_cross, the cross terms v_b^T B^-1 v_a of consecutive rows: pairs

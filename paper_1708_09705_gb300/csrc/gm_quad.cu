@@ -130,6 +130,31 @@ __device__ __forceinline__ float g_lookup(const float4* __restrict__ tab, const 
   return fmaf(v, fmaf(v, fmaf(v, c.w, c.z), c.y), c.x);
 }
 
+// The FP32 pair kernel keeps a window of the table, from the segment of
+// 2^kWinEmin up, in shared memory with every segment stored kRep = 8 times in
+// a row (one 128-byte bank row per segment); lane l reads copy l % 8.  The 8
+// lanes of a quarter-warp, which share one pass of a 16-byte shared load,
+// then always fall in 8 distinct bank groups: the lookups of a warp cost
+// four passes whatever segments the lanes hit (a single copy averaged 1.9
+// passes per quarter-warp on the 20,000-star field's pairs).  Below 2^kWinEmin
+// the argument is clamped: g(x) - g(0) scales as x^(1/3), 2.4e-8 of g(0) there.
+constexpr int kWinEmin = -76;
+constexpr int kRep = 8;
+constexpr int kWinK0 = (kWinEmin - kTabF32.emin) << kTabF32.m;  // first segment kept
+constexpr int kWinSegs =  // incl. the zero segment
+    ((kTabF32.emax - kTabF32.emin) << kTabF32.m) + 1 - kWinK0;
+
+// tab8 points at copy (lane % 8) of window segment 0; t describes the window.
+__device__ __forceinline__ float g_lookup_rep(const float4* __restrict__ tab8, const TabF32& t,
+                                              float x) {
+  x = fmaxf(x, t.xmin);
+  int bits = __float_as_int(x);
+  int k = min((bits - t.base) >> t.shift, t.last);
+  float v = __int_as_float(((bits << (23 - t.shift)) & 0x007fffff) | 0x3f800000) - 1.0f;
+  float4 c = tab8[k * kRep];
+  return fmaf(v, fmaf(v, fmaf(v, c.w, c.z), c.y), c.x);
+}
+
 __device__ __forceinline__ double g_lookup(const D4* __restrict__ tab, const TabF64& t,
                                            double x) {
   x = fmax(x, t.xmin);
@@ -162,8 +187,13 @@ struct QuadParams {
 // One warp per CSR entry (i, j): lanes own the nodes q' of sightline j,
 // loop over the nodes q of sightline i, and the warp sums the products.
 // In symmetric mode entries with j < i are left for k_mirror.
+// Threads per block of the pair kernel: the FP32 form runs one block of 32
+// warps per SM around its replicated table (at most 64 registers a thread).
 template <typename T, int KPL>
-__global__ void __launch_bounds__(256) k_pair_quad(
+constexpr int pair_threads() { return sizeof(T) == 4 ? (KPL <= 2 ? 1024 : 512) : 256; }
+
+template <typename T, int KPL>
+__global__ void __launch_bounds__(pair_threads<T, KPL>()) k_pair_quad(
     QuadParams P, int64_t n_rows, const double* __restrict__ rs, const double* __restrict__ rux,
     const double* __restrict__ ruy, const double* __restrict__ ruz, const double* __restrict__ s,
     const double* __restrict__ ux, const double* __restrict__ uy, const double* __restrict__ uz,
@@ -177,12 +207,17 @@ __global__ void __launch_bounds__(256) k_pair_quad(
   T* zq = reinterpret_cast<T*>(smem);
   T* wq = zq + kMaxNodes;
   const T4* tab;
+  const int lane = threadIdx.x & 31;
+  TabF32 tw = tf;  // the shared-memory window of the FP32 table
   if (sizeof(T) == 4) {
-    // the FP32 table lives in shared memory
+    // the FP32 table window lives in shared memory, kRep copies per segment
     float4* st = reinterpret_cast<float4*>(smem + 2 * kMaxNodes * sizeof(T));
-    const float4* gt = reinterpret_cast<const float4*>(gtab);
-    for (int k = threadIdx.x; k <= tf.last; k += blockDim.x) st[k] = gt[k];
-    tab = reinterpret_cast<const T4*>(st);
+    const float4* gt = reinterpret_cast<const float4*>(gtab) + kWinK0;
+    for (int k = threadIdx.x; k < kWinSegs * kRep; k += blockDim.x) st[k] = gt[k / kRep];
+    tab = reinterpret_cast<const T4*>(st + (lane & (kRep - 1)));
+    tw.base = tf.base + (kWinK0 << tf.shift);
+    tw.last = tf.last - kWinK0;
+    tw.xmin = __int_as_float(tw.base);
   } else {
     tab = reinterpret_cast<const T4*>(gtab);
   }
@@ -192,7 +227,6 @@ __global__ void __launch_bounds__(256) k_pair_quad(
   }
   __syncthreads();
 
-  const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t e = warp; e < nnz; e += nwarps) {
@@ -231,7 +265,7 @@ __global__ void __launch_bounds__(256) k_pair_quad(
         T x = d * d + t * ctp[k];
         T gv;
         if (sizeof(T) == 4)
-          gv = (T)g_lookup(reinterpret_cast<const float4*>(tab), tf, (float)x);
+          gv = (T)g_lookup_rep(reinterpret_cast<const float4*>(tab), tw, (float)x);
         else
           gv = (T)g_lookup(reinterpret_cast<const D4*>(tab), td, (double)x);
         inner += wp[k] * gv;
@@ -527,15 +561,16 @@ static void launch_pair(gm_ctx* c, const QuadParams& P, int64_t n_rows, const do
                         const int32_t* row_field, const int64_t* row_ptr, const int32_t* col,
                         int64_t nnz, void* val) {
   size_t smem = 2 * kMaxNodes * sizeof(T);
-  if (sizeof(T) == 4) smem += (size_t)(kTabF32.n_real() + 1) * sizeof(float4);
+  if (sizeof(T) == 4) smem += (size_t)kWinSegs * kRep * sizeof(float4);
+  constexpr int nt = pair_threads<T, KPL>();
   auto kern = k_pair_quad<T, KPL>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
   int blocks = std::max(1, per_sm) * sm_count(c);
-  blocks = (int)std::min<int64_t>(blocks, std::max<int64_t>(1, ceil_div(nnz * 32, 256)));
+  blocks = (int)std::min<int64_t>(blocks, std::max<int64_t>(1, ceil_div(nnz * 32, nt)));
   GM_PROF(c, "k_pair_quad");
-  kern<<<blocks, 256, smem, c->stream>>>(P, n_rows, rs, rux, ruy, ruz, c->s, c->ux, c->uy, c->uz,
+  kern<<<blocks, nt, smem, c->stream>>>(P, n_rows, rs, rux, ruy, ruz, c->s, c->ux, c->uy, c->uz,
                                          row_ptr, col, nnz, (T*)val, c->gl_zeta, c->gl_w, c->gtab,
                                          tab_f32(), tab_f64(), c->kdiag, c->prior_m, c->d_flags,
                                          c->fgrid, row_field);

@@ -77,7 +77,57 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ part, 
 }
 
 // ---------------------------------------------------------------- SpMV
+// Row dot products of the CSR of K are HBM-bound: per stored entry a 4-byte
+// column index and a 4- or 8-byte value are streamed once, and the gathered
+// x[col] hits L1/L2.  A warp owns a row; each lane loads 16-byte vectors of
+// values and column indices (float4 + int4, or double2 + int2) over the
+// 16-byte-aligned body of the row, two vectors in flight per iteration, with
+// the ragged head and tail of the row loaded as scalars.  The value and index
+// streams are read with the evict-first hint so that x stays in L1.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using V = float4; using C = int4; };
+template <> struct Vec16<double> { using V = double2; using C = int2; };
+
+template <typename TAcc, typename TX>
+__device__ __forceinline__ TAcc vdot(const float4 v, const int4 c, const TX* __restrict__ x) {
+  return (TAcc)v.x * (TAcc)x[c.x] + (TAcc)v.y * (TAcc)x[c.y] + (TAcc)v.z * (TAcc)x[c.z] +
+         (TAcc)v.w * (TAcc)x[c.w];
+}
+template <typename TAcc, typename TX>
+__device__ __forceinline__ TAcc vdot(const double2 v, const int2 c, const TX* __restrict__ x) {
+  return (TAcc)v.x * (TAcc)x[c.x] + (TAcc)v.y * (TAcc)x[c.y];
+}
+
+// This lane's share of sum_{e in [b, e1)} val[e] x[col[e]].
+template <typename TAcc, typename TA, typename TX>
+__device__ __forceinline__ TAcc row_dot_lane(int64_t b, int64_t e1, const int32_t* __restrict__ col,
+                                             const TA* __restrict__ val,
+                                             const TX* __restrict__ x, int lane) {
+  constexpr int V = 16 / sizeof(TA);
+  using VA = typename Vec16<TA>::V;
+  using VC = typename Vec16<TA>::C;
+  TAcc acc = 0;
+  int64_t a = (b + V - 1) / V * V;  // first vector-aligned entry of the row
+  if (a > e1) a = e1;
+  if (b + lane < a) acc += (TAcc)__ldcs(val + b + lane) * (TAcc)x[__ldcs(col + b + lane)];
+  const int64_t ng = (e1 - a) / V;
+  const VA* va = reinterpret_cast<const VA*>(val + a);
+  const VC* vc = reinterpret_cast<const VC*>(col + a);
+  int64_t k = lane;
+  for (; k + 32 < ng; k += 64) {
+    const VA v0 = __ldcs(va + k), v1 = __ldcs(va + k + 32);
+    const VC c0 = __ldcs(vc + k), c1 = __ldcs(vc + k + 32);
+    acc += vdot<TAcc>(v0, c0, x);
+    acc += vdot<TAcc>(v1, c1, x);
+  }
+  if (k < ng) acc += vdot<TAcc>(__ldcs(va + k), __ldcs(vc + k), x);
+  const int64_t t = a + ng * V;
+  if (t + lane < e1) acc += (TAcc)__ldcs(val + t + lane) * (TAcc)x[__ldcs(col + t + lane)];
+  return acc;
+}
+
 // y = K x (FP64 accumulate), optionally y = base + K x.  Warp per row.
+// val and col must be 16-byte aligned (every device buffer of the library is).
 template <typename TA, typename TX>
 __global__ void k_spmv(int64_t n_rows, const int64_t* __restrict__ row_ptr,
                        const int32_t* __restrict__ col, const TA* __restrict__ val,
@@ -87,32 +137,31 @@ __global__ void k_spmv(int64_t n_rows, const int64_t* __restrict__ row_ptr,
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < n_rows; i += nw) {
-    double acc = 0;
-    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32)
-      acc += (double)val[e] * (double)x[col[e]];
+    double acc = row_dot_lane<double>(row_ptr[i], row_ptr[i + 1], col, val, x, lane);
     acc = warp_sum(acc);
     if (lane == 0) y[i] = (base ? base[i] : 0.0) + acc;
   }
 }
 
-// q = p + d o (K pd), pq partial.  Warp per row.
+// q = p + d o (K pd), pq partial.  Warp per row; kBTB threads per block so
+// that the grid of the CG vector kernels (2 blocks per SM) keeps 32 warps of
+// loads in flight on every SM.
+constexpr int kBTB = 512;
 template <typename TA, typename TV>
-__global__ void __launch_bounds__(kBT) k_apply_B(int64_t n, const int64_t* __restrict__ row_ptr,
-                                                 const int32_t* __restrict__ col,
-                                                 const TA* __restrict__ val,
-                                                 const TV* __restrict__ dv,
-                                                 const TV* __restrict__ p,
-                                                 const TV* __restrict__ pd, TV* __restrict__ q,
-                                                 double* __restrict__ pq_part) {
+__global__ void __launch_bounds__(kBTB) k_apply_B(int64_t n, const int64_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const TA* __restrict__ val,
+                                                  const TV* __restrict__ dv,
+                                                  const TV* __restrict__ p,
+                                                  const TV* __restrict__ pd, TV* __restrict__ q,
+                                                  double* __restrict__ pq_part) {
   __shared__ double sh[40];
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double pq = 0;
   for (int64_t i = warp; i < n; i += nw) {
-    TV acc = 0;
-    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32)
-      acc += (TV)val[e] * pd[col[e]];
+    TV acc = row_dot_lane<TV>(row_ptr[i], row_ptr[i + 1], col, val, pd, lane);
     acc = warp_sum(acc);
     if (lane == 0) {
       TV qi = p[i] + dv[i] * acc;
@@ -797,6 +846,8 @@ static gm_status cg_single(gm_ctx* c, const TV* rhs, TV* x, double tol, int max_
   const TV *dv = (const TV*)ws.dv.p, *minv = (const TV*)ws.minv.p;
   double* part = (double*)ws.part.p;
   double* hp = (double*)c->h_pinned;
+  if (((uintptr_t)c->col | (uintptr_t)c->val) & 15)
+    return set_error(c, GM_E_INVAL, "CSR arrays must be 16-byte aligned");
   GM_PROF(c, "k_cg_init");
   k_cg_init<TV><<<G, kBT, 0, st>>>(n, rhs, minv, dv, x, r, p, pd, part);
   GM_LAUNCH_CHECK(c);
@@ -821,7 +872,7 @@ static gm_status cg_single(gm_ctx* c, const TV* rhs, TV* x, double tol, int max_
   int it = 1;
   for (; it <= max_it; ++it) {
     GM_PROF(c, "k_apply_B");
-    k_apply_B<TA, TV><<<G, kBT, 0, st>>>(n, c->row_ptr, c->col, (const TA*)c->val, dv, p, pd, q, part);
+    k_apply_B<TA, TV><<<G, kBTB, 0, st>>>(n, c->row_ptr, c->col, (const TA*)c->val, dv, p, pd, q, part);
     GM_LAUNCH_CHECK(c);
     GM_PROF(c, "k_cg_update1");
     k_cg_update1<TV><<<G, kBT, 0, st>>>(n, it, minv, x, r, p, q, part, c->d_flags);
@@ -877,6 +928,8 @@ static gm_status posterior_mean(gm_ctx* c, int64_t* iters, double* resid) {
   const int wb = (int)std::min<int64_t>(ceil_div(n * 32, 256), 16 * sms);
   double *b64 = (double*)ws.b64.p, *w64 = (double*)ws.w64.p, *x64 = (double*)ws.x64.p,
          *r64 = (double*)ws.r64.p, *d64 = (double*)ws.d64.p;
+  if (((uintptr_t)c->col | (uintptr_t)c->val) & 15)
+    return set_error(c, GM_E_INVAL, "CSR arrays must be 16-byte aligned");
   // b = nu - tau m ; w = K b ; rhs = d o w
   GM_PROF(c, "k_site_rhs");
   k_site_rhs<<<eb, 256, 0, st>>>(n, c->nu, c->tau, c->prior_m, b64);
@@ -1232,6 +1285,26 @@ gm_status refresh_posterior(gm_ctx* c) {
   return GM_OK;
 }
 
+gm_status posterior_mean_only(gm_ctx* c) {
+  gm_status s = prepare_precond(c);
+  if (s != GM_OK) return s;
+  int64_t it = 0;
+  double res = 0;
+  if (c->cfg.precision == GM_PREC_FP32) {
+    if (c->cfg.deflate > 0 && c->n_fields == 1) {
+      s = deflate_prepare(c, (const float*)W(c).dv.p, (const float*)W(c).minv.p);
+      if (s != GM_OK) return s;
+    }
+    s = posterior_mean<float, float>(c, &it, &res);
+  } else {
+    s = posterior_mean<double, double>(c, &it, &res);
+  }
+  if (s != GM_OK) return s;
+  c->stats.cg_iters_mean = it;
+  c->stats.cg_resid_mean = res;
+  return GM_OK;
+}
+
 gm_status panel_variances(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const int32_t* col,
                           const void* val, const double* kdiag_rows, double* var_out,
                           int64_t* iters_out, double* resid_out, double* pair_cross,
@@ -1249,6 +1322,8 @@ gm_status csr_dot_alpha(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
                         const void* val, const double* alpha, const double* base, double* out) {
   const int wb = (int)std::min<int64_t>(ceil_div(n_rows * 32, 256), 16 * sm_count(c));
   if (n_rows == 0) return GM_OK;
+  if (((uintptr_t)col | (uintptr_t)val) & 15)
+    return set_error(c, GM_E_INVAL, "CSR arrays must be 16-byte aligned");
   GM_PROF(c, "k_spmv");
   if (c->cfg.precision == GM_PREC_FP32)
     k_spmv<float, double><<<wb, 256, 0, c->stream>>>(n_rows, row_ptr, col, (const float*)val, alpha, base, out);

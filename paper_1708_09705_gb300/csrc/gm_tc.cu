@@ -75,6 +75,15 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t da, uint64_t db
       "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
 }
 
+// The same MMA with B in the MN-major layout.
+__device__ __forceinline__ void tc_mma_mn(uint32_t tmem_d, uint64_t da, uint64_t db,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kTcIdesc | (1u << 16)), "r"(acc));
+}
+
 // Bounded wait on an mbarrier phase; false if it gave up.
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
   for (uint32_t it = 0; it < (1u << 26); ++it) {
@@ -665,6 +674,297 @@ __global__ void __launch_bounds__(288, 2) k_panel_spmm_tc_ws(
   }
 }
 
+// ---------------------------------------------------------------- async variant
+// The B operand straight from memory.  Once per product the panel PD is split
+// into three BF16 planes (k_split3_planes, the same rounding as split3), so
+// that a K-step's B tile is a plain copy of 16 gathered plane rows x 256
+// columns: no register staging and no split on the MMA's critical path.  The
+// tile is kept MN-major in shared memory (the panel's columns contiguous, as
+// in the planes): no-swizzle core matrices of 8 k-rows x 16 B (8 columns),
+// column-adjacent ones 128 B apart, the two 8-row k-groups 4 KB apart, and
+// the MMA's instruction descriptor marks B as MN-major.
+//
+// Warp roles (160 threads, two CTAs per SM): warps 0-3 are producers -- per
+// K-step thread 0 starts one bulk copy of the tile's A pieces (cp.async.bulk,
+// completing on the stage's A barrier with its byte count) and all 128
+// threads copy the B pieces in 16-byte chunks (cp.async, each thread's
+// completion arriving on the stage's B barrier without blocking the thread),
+// kTaRing stages ahead of the tensor cores; warp 4's lane 0 waits for both
+// barriers, orders the copies before the tensor core's reads
+// (fence.proxy.async), issues the MMAs and commits to the stage's empty
+// barrier.  Warps 0-3 then run the epilogue.  Every wait is bounded and gives
+// up when another thread has; a CTA that gives up waits (bounded) for its
+// bulk copies and MMAs in flight before it releases tensor memory.
+constexpr int kTaRing = 3;
+constexpr int kTaProd = 128;
+constexpr int kTaThreads = kTaProd + 32;
+constexpr int kTaPiece = kTcCols * kTcK * 2;              // 8 KB: one plane's B tile
+constexpr int kTaStage = 3 * kTcA + 3 * kTaPiece;         // 36 KB
+constexpr int kTaSmem = kTaRing * kTaStage;               // 108 KB (partials reuse stage 0)
+
+// byte offset of B element (k, n) in the MN-major image of one plane
+__host__ __device__ __forceinline__ int tcb_off(int k, int n) {
+  return (k >> 3) * 4096 + (n >> 3) * 128 + (k & 7) * 16 + (n & 7) * 2;
+}
+
+// MN-major no-swizzle descriptor: LBO = stride of the k-groups (4 KB), SBO =
+// stride of the 8-column chunks (128 B)
+__device__ __forceinline__ uint64_t tc_desc_mn(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((4096u >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// PD (elements [0, ne)) -> three BF16 planes, plane p at planes + p * ne
+__global__ void k_split3_planes(int64_t ne, const float* __restrict__ PD,
+                                uint16_t* __restrict__ planes) {
+  const int64_t n4 = ne >> 2;
+  const float4* src = reinterpret_cast<const float4*>(PD);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = __ldcs(src + q);
+    uint32_t a[4], b[4], c[4];
+    split3(v.x, a[0], b[0], c[0]);
+    split3(v.y, a[1], b[1], c[1]);
+    split3(v.z, a[2], b[2], c[2]);
+    split3(v.w, a[3], b[3], c[3]);
+    reinterpret_cast<uint2*>(planes)[q] = make_uint2(pack2(a[0], a[1]), pack2(a[2], a[3]));
+    reinterpret_cast<uint2*>(planes + ne)[q] = make_uint2(pack2(b[0], b[1]), pack2(b[2], b[3]));
+    reinterpret_cast<uint2*>(planes + 2 * ne)[q] = make_uint2(pack2(c[0], c[1]), pack2(c[2], c[3]));
+  }
+  for (int64_t e = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t a, b, c;
+    split3(PD[e], a, b, c);
+    planes[e] = (uint16_t)(a >> 16);
+    planes[ne + e] = (uint16_t)(b >> 16);
+    planes[2 * ne + e] = (uint16_t)(c >> 16);
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTaThreads, 2) k_panel_spmm_tc_async(
+    int64_t n, int R, const int64_t* __restrict__ kbase, const int32_t* __restrict__ upad,
+    const unsigned char* __restrict__ img, const float* __restrict__ dv,
+    const float* __restrict__ P, const uint16_t* __restrict__ planes, int64_t plane_elems,
+    float* __restrict__ Q, double* __restrict__ part_pq, TcPanels pk,
+    unsigned* __restrict__ flags) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t fullA[kTaRing], fullB[kTaRing], empty[kTaRing];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  volatile int* abort_v = &abort_flag;
+  double* sh_pq = reinterpret_cast<double*>(smem);  // [4][256], after the last MMA
+  constexpr int npl = NP == 3 ? 2 : 3;              // BF16 pieces used per side
+  constexpr uint32_t abytes = npl * kTcA;
+
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const bool packed = pk.items != nullptr;
+  int64_t b, base, brow0, bend;
+  int c0, W;
+  if (packed) {
+    const int2 it = pk.items[blockIdx.x];
+    b = it.x;
+    c0 = it.y * kTcCols;
+    W = pk.width[b];
+    base = pk.base[b];
+    brow0 = pk.row0[b];
+    bend = pk.row0[b + 1];
+  } else {
+    b = blockIdx.y;
+    c0 = blockIdx.x * kTcCols;
+    W = R;
+    base = 0;
+    brow0 = b * kTcRows;
+    bend = min(brow0 + kTcRows, n);
+  }
+  const int64_t ks0 = kbase[b], nks = kbase[b + 1] - ks0;
+
+  if (t == 0) {
+    abort_flag = 0;
+    for (int q = 0; q < kTaRing; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&fullA[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&fullB[q])),
+                   "r"(kTaProd));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&empty[q])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+        tc_smem(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  int64_t issued_a = 0;  // bulk copies started by thread 0
+
+  if (warp < 4) {
+    // ---- producers.  Thread t copies, per plane, the chunks (k, j) with
+    // k in {t % 8, 8 + t % 8} and j in {t / 8, 16 + t / 8} (16-byte chunk j =
+    // columns 8j .. 8j + 7): a quarter-warp fills one 128-byte core matrix.
+    const int klo = t & 7, j0 = t >> 3;
+    for (int64_t ks = 0; ks < nks; ++ks) {
+      const int s = (int)(ks % kTaRing);
+      const int64_t use = ks / kTaRing;
+      if (use > 0 && !tc_wait_or_abort(tc_smem(&empty[s]), (uint32_t)((use - 1) & 1), abort_v)) {
+        abort_flag = 1;
+        break;
+      }
+      unsigned char* sA = smem + s * kTaStage;
+      unsigned char* sB = sA + 3 * kTcA;
+      if (t == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                         tc_smem(&fullA[s])),
+                     "r"(abytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];" ::"r"(tc_smem(sA)),
+            "l"(__cvta_generic_to_global(img + (ks0 + ks) * (int64_t)(3 * kTcA))), "r"(abytes),
+            "r"(tc_smem(&fullA[s]))
+            : "memory");
+        ++issued_a;
+      }
+      const int32_t* up = upad + (ks0 + ks) * kTcK;
+      const int64_t u0 = __ldg(up + klo), u1 = __ldg(up + 8 + klo);
+#pragma unroll
+      for (int p = 0; p < npl; ++p) {
+        const uint16_t* pl = planes + p * plane_elems + base;
+        const uint32_t db = tc_smem(sB + p * kTaPiece);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = klo + 8 * h;
+          const int64_t row = h ? u1 : u0;
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            const int j = j0 + 16 * g;
+            const int colg = c0 + 8 * j;
+            const bool in = colg < W;
+            const uint16_t* src = in ? pl + row * W + colg : planes;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             db + (uint32_t)tcb_off(k, 8 * j)),
+                         "l"(__cvta_generic_to_global(src)), "r"(in ? 16 : 0)
+                         : "memory");
+          }
+        }
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
+                       tc_smem(&fullB[s]))
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp == 4 && lane == 0) {
+    // ---- MMA issuer
+    for (int64_t ks = 0; ks < nks; ++ks) {
+      const int s = (int)(ks % kTaRing);
+      const uint32_t par = (uint32_t)((ks / kTaRing) & 1);
+      if (!tc_wait_or_abort(tc_smem(&fullA[s]), par, abort_v) ||
+          !tc_wait_or_abort(tc_smem(&fullB[s]), par, abort_v)) {
+        abort_flag = 1;
+        break;
+      }
+      // the B pieces were written through the generic proxy (cp.async)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a = tc_smem(smem + s * kTaStage), bb = a + 3 * kTcA;
+      const uint64_t A1 = tc_desc(a), A2 = tc_desc(a + kTcA);
+      const uint64_t B1 = tc_desc_mn(bb), B2 = tc_desc_mn(bb + kTaPiece);
+      if constexpr (NP == 3) {
+        tc_mma_mn(tmem, A2, B1, ks > 0 ? 1u : 0u);
+        tc_mma_mn(tmem, A1, B2, 1u);
+        tc_mma_mn(tmem, A1, B1, 1u);
+      } else {
+        const uint64_t A3 = tc_desc(a + 2 * kTcA), B3 = tc_desc_mn(bb + 2 * kTaPiece);
+        tc_mma_mn(tmem, A3, B1, ks > 0 ? 1u : 0u);
+        tc_mma_mn(tmem, A2, B2, 1u);
+        tc_mma_mn(tmem, A1, B3, 1u);
+        tc_mma_mn(tmem, A2, B1, 1u);
+        tc_mma_mn(tmem, A1, B2, 1u);
+        tc_mma_mn(tmem, A1, B1, 1u);
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              tc_smem(&empty[s])));
+    }
+  }
+  // all MMAs done: the last step's commit tracks every earlier one
+  if (nks > 0 && !*abort_v && warp < 4) {
+    const int64_t last = nks - 1;
+    if (!tc_wait_or_abort(tc_smem(&empty[last % kTaRing]), (uint32_t)((last / kTaRing) & 1),
+                          abort_v))
+      abort_flag = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool ok = !abort_flag;
+  if (ok && warp < 4) {
+    // epilogue: warp w holds accumulator rows 32 w .. 32 w + 31, all 256 columns
+    const int r = 32 * warp + lane;
+    const int64_t row = brow0 + r;
+    const bool vrow = row < bend;
+    const float dr = vrow ? dv[row] : 0.f;
+#pragma unroll 1
+    for (int ch = 0; ch < 16; ++ch) {
+      const int cl = 16 * ch;
+      uint32_t u[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+            "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]),
+            "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+          : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cl));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int cg = c0 + cl + k;
+        double pq = 0.0;
+        if (vrow && cg < W) {
+          const int64_t at = base + row * W + cg;
+          const float pv = P[at];
+          const float qv = pv + dr * __uint_as_float(u[k]);
+          Q[at] = qv;
+          pq = (double)pv * (double)qv;
+        }
+        if (!packed) {  // uniform over the CTA
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
+          if (lane == 0) sh_pq[warp * kTcCols + cl + k] = pq;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (ok) {
+    if (!packed)
+      for (int cl = t; cl < kTcCols; cl += kTaThreads)
+        if (c0 + cl < W)
+          part_pq[b * R + c0 + cl] = ((sh_pq[cl] + sh_pq[kTcCols + cl]) +
+                                      sh_pq[2 * kTcCols + cl]) + sh_pq[3 * kTcCols + cl];
+  } else if (t == 0) {
+    atomicOr(flags, kFlagTimeout);
+    // bounded waits for the bulk copies and MMAs still in flight
+    for (int q = 0; q < kTaRing; ++q) {
+      const int64_t na = issued_a > q ? (issued_a - 1 - q) / kTaRing + 1 : 0;
+      if (na > 0) tc_wait(tc_smem(&fullA[q]), (uint32_t)((na - 1) & 1));
+      const int64_t uses = nks > q ? (nks - 1 - q) / kTaRing + 1 : 0;
+      if (uses > 0) tc_wait(tc_smem(&empty[q]), (uint32_t)((uses - 1) & 1));
+    }
+  }
+  __syncthreads();
+  if (warp == 4) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  }
+}
+
 // ---------------------------------------------------------------- host
 // The tensor-core path serves FP32 contexts unless GM_SPMM=simt.
 bool tc_wanted(gm_ctx* c) {
@@ -767,10 +1067,29 @@ gm_status tc_tiles_build(gm_ctx* c) {
 
 static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const float* dv,
                            const float* P, const float* PD, float* Q, double* part_pq,
-                           TcPanels pk, cudaStream_t st) {
+                           TcPanels pk, int64_t pd_elems, cudaStream_t st) {
   const int64_t* kb = (const int64_t*)c->tc_kbase.p;
   const int32_t* up = (const int32_t*)c->tc_upad.p;
   const uint4* im = (const uint4*)c->tc_img.p;
+  if (pf == 4) {
+    // BF16 planes of PD, then the product with B copied straight from them
+    if (!ensure(c, c->tc_planes, (size_t)std::max<int64_t>(pd_elems, 1) * 3 * sizeof(uint16_t)))
+      return set_error(c, GM_E_NOMEM, "BF16 planes of the panel");
+    uint16_t* pl = (uint16_t*)c->tc_planes.p;
+    const int sb = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(pd_elems, 4 * 256), 1),
+                                          8 * sm_count(c));
+    GM_PROF(c, "k_split3_planes");
+    k_split3_planes<<<sb, 256, 0, st>>>(pd_elems, PD, pl);
+    GM_PROF(c, "k_panel_spmm_tc");
+    const unsigned char* ib = (const unsigned char*)c->tc_img.p;
+    if (c->cfg.tc_products == 3)
+      k_panel_spmm_tc_async<3><<<grid, kTaThreads, kTaSmem, st>>>(
+          n, R, kb, up, ib, dv, P, pl, pd_elems, Q, part_pq, pk, c->d_flags);
+    else
+      k_panel_spmm_tc_async<6><<<grid, kTaThreads, kTaSmem, st>>>(
+          n, R, kb, up, ib, dv, P, pl, pd_elems, Q, part_pq, pk, c->d_flags);
+    return GM_OK;
+  }
   if (c->cfg.tc_products == 3) {
     if (pf == 3)
       k_panel_spmm_tc_ws<3><<<grid, 288, kTcSmemWs, st>>>(n, R, kb, up, im, dv, P, PD, Q,
@@ -796,12 +1115,21 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
 }
 
 // Variant of the tile product: 1, 2 = CTA-synchronous with gathers one or two
-// steps ahead, 3 = warp-specialised ring.  GM_TC_PREFETCH=1|2|3 pins it, else
-// the fastest on the context's first panel product (one timed launch each;
+// steps ahead, 3 = warp-specialised ring, 4 = B copied asynchronously from
+// BF16 planes of PD (opt-in).  GM_TC_PREFETCH=1|2|3|4 pins it, else the
+// fastest of 1-3 on the context's first panel product (one timed launch each;
 // the product is idempotent: Q is overwritten).
 static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv, const float* P,
-                         const float* PD, float* Q, double* part_pq, TcPanels pk) {
+                         const float* PD, float* Q, double* part_pq, TcPanels pk,
+                         int64_t pd_elems) {
   if (c->tc_pf) return GM_OK;
+  // the planes are allocated here, before any graph capture of the products
+  if (!ensure(c, c->tc_planes, (size_t)std::max<int64_t>(pd_elems, 1) * 3 * sizeof(uint16_t)))
+    return set_error(c, GM_E_NOMEM, "BF16 planes of the panel");
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc_async<6>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTaSmem));
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc_async<3>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kTaSmem));
   GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<1, 6>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
   GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_panel_spmm_tc<2, 6>,
@@ -816,7 +1144,7 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemWs));
   if (const char* e = std::getenv("GM_TC_PREFETCH")) {
     const int v = std::atoi(e);
-    if (v >= 1 && v <= 3) {
+    if (v >= 1 && v <= 4) {
       c->tc_pf = v;
       return GM_OK;
     }
@@ -828,7 +1156,8 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
   for (int pf : {1, 2, 3}) {
     float ms = 0;
     GM_CUDA_CHECK(c, cudaEventRecord(a, c->stream));
-    launch_tc(c, pf, grid, n, R, dv, P, PD, Q, part_pq, pk, c->stream);
+    gm_status ls = launch_tc(c, pf, grid, n, R, dv, P, PD, Q, part_pq, pk, pd_elems, c->stream);
+    if (ls != GM_OK) return ls;
     GM_CUDA_CHECK(c, cudaEventRecord(b, c->stream));
     GM_CUDA_CHECK(c, cudaEventSynchronize(b));
     GM_LAUNCH_CHECK(c);
@@ -849,10 +1178,11 @@ gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const floa
   // blocks' tile images (read from DRAM once instead of once per group)
   dim3 grid((unsigned)ceil_div(R, kTcCols), (unsigned)c->tc_nblk);
   const TcPanels pk{nullptr, nullptr, nullptr, nullptr};
-  gm_status s = tc_tune(c, grid, n, R, dv, P, PD, Q, part_pq, pk);
+  gm_status s = tc_tune(c, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R);
   if (s != GM_OK) return s;
   GM_PROF(c, "k_panel_spmm_tc");
-  launch_tc(c, c->tc_pf, grid, n, R, dv, P, PD, Q, part_pq, pk, c->stream);
+  s = launch_tc(c, c->tc_pf, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R, c->stream);
+  if (s != GM_OK) return s;
   GM_LAUNCH_CHECK(c);
   return GM_OK;
 }
@@ -860,12 +1190,12 @@ gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const floa
 // Packed multi-field panels: one CTA per (tile block, column group) item.
 gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
                                const int64_t* blk_base, const int32_t* blk_width, const float* dv,
-                               const float* P, const float* PD, float* Q, cudaStream_t st,
-                               bool tune) {
+                               const float* P, const float* PD, float* Q, int64_t pd_elems,
+                               cudaStream_t st, bool tune) {
   const TcPanels pk{blk_base, blk_width, (const int64_t*)c->tc_brow0.p, items};
   dim3 grid((unsigned)n_items);
-  if (tune) return tc_tune(c, grid, c->n, 0, dv, P, PD, Q, nullptr, pk);
-  return launch_tc(c, c->tc_pf, grid, c->n, 0, dv, P, PD, Q, nullptr, pk, st);
+  if (tune) return tc_tune(c, grid, c->n, 0, dv, P, PD, Q, nullptr, pk, pd_elems);
+  return launch_tc(c, c->tc_pf, grid, c->n, 0, dv, P, PD, Q, nullptr, pk, pd_elems, st);
 }
 
 }  // namespace gm

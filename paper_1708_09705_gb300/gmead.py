@@ -38,7 +38,7 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
            "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries", "gm_predict_pairs",
            "gm_predict_sightlines", "gm_monotone_sample", "gm_pic_posterior",
-           "gm_pic_predict"]
+           "gm_pic_predict", "gm_set_mean_fn", "gm_learn_mean"]
 
 
 class GmError(RuntimeError):
@@ -109,6 +109,9 @@ def lib():
         L.gm_pic_posterior.argtypes = [vp, i32, vp, i64, vp, vp, vp, vp, vp]
         L.gm_pic_predict.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
+        L.gm_set_mean_fn.argtypes = [vp, vp, dbl, dbl]
+        L.gm_learn_mean.argtypes = [vp, vp, vp, vp, dbl, dbl, i32, dbl, vp, vp,
+                                    C.POINTER(dbl), C.POINTER(i32)]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
         L.gm_stream.argtypes = [vp]
         L.gm_stream.restype = vp
@@ -138,7 +141,7 @@ def lib():
                   "gm_get_stats", "gm_profile", "gm_kernel_time", "gm_surrogate_set_params",
                   "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
                   "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries",
-                  "gm_predict_pairs"):
+                  "gm_predict_pairs", "gm_set_mean_fn", "gm_learn_mean"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -287,6 +290,29 @@ class Context:
                                          b.ctypes.data, s.ctypes.data, mean.ctypes.data,
                                          var.ctypes.data))
         return mean, var
+
+    # ---- mean function of the density and its hyperparameters (Sect. 5)
+    def set_mean_fn(self, theta, r_sun_pc=8000.0, bump_width_pc=400.0):
+        """Disc + bump mean density theta = (L, H, rho0, s_bump, A_bump), or
+        None for the constant mean density."""
+        t = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(lib().gm_set_mean_fn(self._h, None if t is None else t.ctypes.data,
+                                         float(r_sun_pc), float(bump_width_pc)))
+
+    def learn_mean(self, theta0, prior_mean, prior_sd=None, r_sun_pc=8000.0,
+                   bump_width_pc=400.0, max_iter=50, tol=1e-10):
+        """Mode and Laplace covariance (of ln theta) of the five mean-function
+        hyperparameters; returns dict(theta, cov_phi, log_post, iters)."""
+        t0 = np.ascontiguousarray(theta0, dtype=np.float64)
+        pm = np.ascontiguousarray(prior_mean, dtype=np.float64)
+        ps = pm.copy() if prior_sd is None else np.ascontiguousarray(prior_sd, dtype=np.float64)
+        th, cov = np.empty(5), np.empty((5, 5))
+        lp, it = C.c_double(0.0), C.c_int32(0)
+        self._check(lib().gm_learn_mean(self._h, t0.ctypes.data, pm.ctypes.data, ps.ctypes.data,
+                                        float(r_sun_pc), float(bump_width_pc), int(max_iter),
+                                        float(tol), th.ctypes.data, cov.ctypes.data,
+                                        C.byref(lp), C.byref(it)))
+        return dict(theta=th, cov_phi=cov, log_post=lp.value, iters=it.value)
 
     # ---- state
     def _pair_out(self, fn, out):
@@ -490,9 +516,10 @@ def get_posterior(ctx: Context, out=None):
 
 
 def config_from_catalogue(cat, **kw) -> Config:
-    """Config with the hyperparameters of a synthetic catalogue dict."""
+    """Config with the hyperparameters of a synthetic catalogue dict; the
+    node rule is the workload's: n_nodes Gauss-Legendre nodes per sightline."""
     base = dict(sigma2=float(cat["sigma2"]), outer_scale_pc=float(cat["outer_scale_pc"]),
                 rho_bar=float(cat["rho_bar"]), cutoff_pc=float(cat["cutoff_pc"]),
-                n_nodes=int(cat["n_nodes"]))
+                n_nodes=int(cat["n_nodes"]), quad_rule=QUAD_GL)
     base.update(kw)
     return default_config(**base)

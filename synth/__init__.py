@@ -6,7 +6,7 @@ computes (no covariance quadrature, no EP), so both the CPU oracle and the
 CUDA path can take their inputs from here without sharing arithmetic.
 """
 from .catalogue import (Workload, WORKLOADS, make_catalogue, make_fields,
-                        catalogue_subset)
+                        catalogue_subset, make_disc_catalogue, DISC_TRUTH)
 
 __all__ = ["Workload", "WORKLOADS", "make_catalogue", "make_fields",
-           "catalogue_subset"]
+           "catalogue_subset", "make_disc_catalogue", "DISC_TRUTH"]

@@ -77,7 +77,8 @@ def _unit(l, b):
     return np.stack([cb * np.cos(l), cb * np.sin(l), np.sin(b)], axis=-1)
 
 
-def _truth_fft(rng, l, b, s, sigma2, L0, rho_bar, h=2.0, pad_factor=3.0, order=1):
+def _truth_fft(rng, l, b, s, sigma2, L0, rho_bar, h=2.0, pad_factor=3.0, order=1,
+               rho_fn=None):
     """Line integrals of exp(f) for a spectrally synthesised log-density f.
 
     order: how f is read at the integration points, 1 = trilinear
@@ -85,7 +86,10 @@ def _truth_fft(rng, l, b, s, sigma2, L0, rho_bar, h=2.0, pad_factor=3.0, order=1
     interpolation averages cells whose correlation is well below 1 (the
     Kolmogorov correlation has a cusp at zero separation: phi(0.1) = 0.8), so
     it lowers the variance of the sampled log-density and E[exp f] with it;
-    nearest-cell values keep the variance sigma2."""
+    nearest-cell values keep the variance sigma2.
+
+    rho_fn: optional mean density (mag/pc) at heliocentric positions (..., 3);
+    the density is then rho_fn(x) exp(f - ln rho_bar) (so E rho = rho_fn)."""
     from scipy import fft as sfft
     from scipy.ndimage import map_coordinates
 
@@ -142,11 +146,13 @@ def _truth_fft(rng, l, b, s, sigma2, L0, rho_bar, h=2.0, pad_factor=3.0, order=1
         t0 = k * h
         t1 = np.minimum(t0 + h, s[idx][star])
         tm = 0.5 * (t0 + t1)
-        p = (u[idx][star] * tm[:, None]) @ R.T
+        ph = u[idx][star] * tm[:, None]
+        p = ph @ R.T
         g = ((p - lo) / h).T
         fv = map_coordinates(f, g, order=order, mode="nearest")
-        A[idx] = np.bincount(star, weights=np.exp(mu_f + fv) * (t1 - t0),
-                             minlength=len(idx))
+        rho = np.exp(mu_f + fv) if rho_fn is None else \
+            rho_fn(ph) * np.exp(mu_f - math.log(rho_bar) + fv)
+        A[idx] = np.bincount(star, weights=rho * (t1 - t0), minlength=len(idx))
     return A
 
 
@@ -183,6 +189,60 @@ def make_catalogue(wl: Workload | str, n: int | None = None, seed: int | None = 
                 sigma2=wl.sigma2, outer_scale_pc=wl.outer_scale_pc,
                 rho_bar=wl.rho_bar, cutoff_pc=wl.cutoff_pc, n_nodes=wl.n_nodes,
                 name=wl.name, seed=seed)
+
+
+# Sect. 5 set-up: an exponential disc of dust plus a Gaussian bump (a spiral
+# arm) along the line of sight.  Parameters of the truth (L, H, rho0, s_bump,
+# A_bump in pc, pc, mag/pc, pc, mag); Sun at 8 kpc from the Galactic centre;
+# bump width 400 pc.
+DISC_TRUTH = (2500.0, 150.0, 0.9e-3, 2200.0, 0.15)
+R_SUN_PC, BUMP_WIDTH_PC = 8000.0, 400.0
+
+
+def disc_density(x, theta=DISC_TRUTH):
+    """Mean pseudo-density of the Sect. 5 truth at heliocentric positions x
+    (pc, x-axis towards the Galactic centre)."""
+    L, H, rho0, sb, Ab = theta
+    R = np.hypot(R_SUN_PC - x[..., 0], x[..., 1])
+    d = np.linalg.norm(x, axis=-1)
+    return (rho0 * np.exp(-(R - R_SUN_PC) / L - np.abs(x[..., 2]) / H)
+            + Ab / (BUMP_WIDTH_PC * math.sqrt(2 * math.pi))
+            * np.exp(-0.5 * ((d - sb) / BUMP_WIDTH_PC) ** 2))
+
+
+def make_disc_catalogue(n=6000, seed=0, theta=DISC_TRUTH, sigma_lnA=0.05, truth="fft",
+                        l_deg=(174.0, 186.0), b_deg=(-2.5 / 60, 2.5 / 60),
+                        s_pc=(100.0, 5000.0), outer_scale_pc=20.0, sigma2=1.0):
+    """The Sect. 5 letter-box field towards the anticentre (174 <= l < 186
+    deg, |b| < 2.5 arcmin, distances to 5 kpc) with the disc-plus-bump mean
+    density `theta` and a log-density GP on top; observations of the
+    log-extinction with Gaussian noise sigma_lnA (the simplified case of
+    Sect. 4.1).  truth='fft' synthesises the fluctuations (nearest-cell
+    reading), truth='mean' uses the mean extinction only (a numerical line
+    integral of the mean density, 1 pc steps)."""
+    wl = Workload("sect5_disc", n, l_deg, b_deg, s_pc=s_pc, sigma2=sigma2,
+                  outer_scale_pc=outer_scale_pc, n_nodes=64, seed=seed)
+    ss = np.random.SeedSequence([seed, n, 5])
+    r_pos, r_truth, r_noise = [np.random.default_rng(c) for c in ss.spawn(3)]
+    l, b, s = _field_positions(r_pos, n, wl.l_deg, wl.b_deg, wl.s_pc)
+    rho_fn = lambda x: disc_density(x, theta)
+    if truth == "fft":
+        A_true = _truth_fft(r_truth, l, b, s, sigma2, outer_scale_pc, wl.rho_bar, order=0,
+                            rho_fn=rho_fn)
+    elif truth == "mean":
+        u = _unit(l, b)
+        A_true = np.empty(n)
+        for i in range(n):
+            t = (np.arange(int(math.ceil(s[i]))) + 0.5) * (s[i] / math.ceil(s[i]))
+            A_true[i] = rho_fn(u[i] * t[:, None]).sum() * (s[i] / math.ceil(s[i]))
+    else:
+        raise ValueError(truth)
+    sig = np.full(n, float(sigma_lnA))
+    a_obs = np.log(A_true) + sig * r_noise.standard_normal(n)
+    return dict(l=l, b=b, s=s, A_obs=a_obs, A_sigma=sig, A_true=A_true, sigma2=sigma2,
+                outer_scale_pc=outer_scale_pc, rho_bar=wl.rho_bar, cutoff_pc=wl.cutoff_pc,
+                n_nodes=wl.n_nodes, name=wl.name, seed=seed, theta_true=np.array(theta),
+                r_sun_pc=R_SUN_PC, bump_width_pc=BUMP_WIDTH_PC)
 
 
 def catalogue_subset(cat, idx):

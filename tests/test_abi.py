@@ -44,7 +44,7 @@ def test_status_strings_and_defaults(L):
     assert cfg.cov_source == gm.COV_QUADRATURE and cfg.surrogate_gate == 1e-4
     assert cfg.probe_factor == 0.0        # exact variances unless asked
     assert cfg.deflate == 0
-    assert cfg.quad_rule == gm.QUAD_GL and cfg.tc_products == 6
+    assert cfg.quad_rule == gm.QUAD_BAND and cfg.tc_products == 6   # the converged rule
 
 
 def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
@@ -63,9 +63,6 @@ def test_init_rejects_bad_arguments_before_touching_a_gpu(L):
                        ("tc_products", 4)):
         c2 = gm.default_config(**{field: bad})
         assert L.gm_ep_init(C.byref(h), C.byref(c2), 4, x, x, x, x, x, None, None) == 1, field
-    # the band rule with the surrogate source is not offered
-    c3 = gm.default_config(quad_rule=gm.QUAD_BAND, cov_source=gm.COV_SURROGATE)
-    assert L.gm_ep_init(C.byref(h), C.byref(c3), 4, x, x, x, x, x, None, None) == 1
     assert not h.value
     # several fields: field ids required, FP32 form only, positive field scales
     fid = (C.c_int32 * 4)(0, 1, 0, 1)

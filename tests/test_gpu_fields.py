@@ -37,7 +37,7 @@ def test_fields_match_oracle_and_single_contexts(gm):
     cat = {k: v[order] for k, v in cat.items()}
     fid = fid[order]
     base = dict(sigma2=1.0, outer_scale_pc=20.0, rho_bar=1e-3, cutoff_pc=60.0, n_nodes=32,
-                precision=gm.PREC_FP32, cg_tol=1e-7)
+                quad_rule=gm.QUAD_GL, precision=gm.PREC_FP32, cg_tol=1e-7)
     cfg = gm.default_config(**base)
     with gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"],
                     field_id=fid, field_L0=L0, field_cutoff=3 * L0) as ctx:

@@ -1,0 +1,107 @@
+"""Mean function of the density and the learning of its five hyperparameters
+(gm_set_mean_fn, gm_learn_mean) on the GPU against oracle/learn.py."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import learn as Lr
+from synth import make_disc_catalogue
+
+pytestmark = pytest.mark.gpu
+THETA = np.array([2500.0, 150.0, 0.9e-3, 2200.0, 0.15])
+
+
+@pytest.fixture(scope="module")
+def gm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_09705_gb300 import _build
+    _build.build()
+    import paper_1708_09705_gb300 as pkg
+    return pkg
+
+
+def _ctx(gm, cat, prec):
+    cfg = gm.config_from_catalogue(cat, precision=prec, likelihood=gm.LIK_GAUSS_IN_LNA,
+                                   cg_tol=1e-12 if prec == gm.PREC_FP64 else 1e-6)
+    return gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"])
+
+
+def test_mean_function_prior_mean_matches_oracle(gm):
+    cat = make_disc_catalogue(300, seed=1, truth="mean")
+    u = O.unit_vectors(cat["l"], cat["b"])
+    with _ctx(gm, cat, gm.PREC_FP64) as ctx:
+        ctx.build_cov()
+        m0, kd = ctx.get_prior()
+        ctx.set_mean_fn(THETA)
+        m1, _ = ctx.get_prior()
+        ctx.build_cov()          # a rebuild keeps the mean function
+        m2, _ = ctx.get_prior()
+        ctx.set_mean_fn(None)    # back to the constant density
+        m3, _ = ctx.get_prior()
+    ref = Lr.prior_mean(u, cat["s"], THETA, kd)
+    np.testing.assert_allclose(m1, ref, rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(m2, m1)
+    np.testing.assert_array_equal(m3, m0)
+
+
+def test_learned_hyperparameters_match_oracle(gm):
+    """MAP and Laplace covariance of ln theta (FP64) against the oracle's
+    Newton iteration on the same data and covariance; then the posterior mean
+    and a prediction with the learned mean function."""
+    cat = make_disc_catalogue(300, seed=2, truth="fft")
+    u = O.unit_vectors(cat["l"], cat["b"])
+    cv = O.build_cov(cat)
+    K = cv["K"]
+    ref = Lr.learn_mean(u, cat["s"], cat["A_obs"], cat["A_sigma"], K, Lr.PRIOR_MEAN,
+                        max_iter=50, tol=1e-10)
+    rng = np.random.default_rng(4)
+    jq = rng.choice(300, 8, replace=False)
+    lq, bq, sq = cat["l"][jq] + 1e-4, cat["b"][jq], cat["s"][jq] * 0.9
+    with _ctx(gm, cat, gm.PREC_FP64) as ctx:
+        ctx.build_cov()
+        res = ctx.learn_mean(Lr.PRIOR_MEAN, Lr.PRIOR_MEAN, max_iter=50, tol=1e-10)
+        mu, var = ctx.get_posterior()
+        tau, nu = ctx.get_sites()
+        m, _ = ctx.get_prior()
+        pm, pv = ctx.predict(lq, bq, sq)
+    np.testing.assert_allclose(res["theta"], ref["theta"], rtol=1e-6)
+    np.testing.assert_allclose(res["cov_phi"], ref["cov_phi"], rtol=1e-4, atol=1e-8)
+    # the theta-dependent part of the log posterior at the mode
+    C = K + np.diag(cat["A_sigma"] ** 2)
+    r = cat["A_obs"] - Lr.prior_mean(u, cat["s"], ref["theta"], np.diag(K))
+    mu_p, s2 = Lr.prior_lognormal()
+    ph = np.log(ref["theta"])
+    lp = -0.5 * r @ np.linalg.solve(C, r) - 0.5 * np.sum((ph - mu_p) ** 2 / s2
+                                                        + np.log(2 * np.pi * s2))
+    assert res["log_post"] == pytest.approx(lp, rel=1e-8)
+    # exact Gaussian sites; posterior = GP regression with the learned mean
+    np.testing.assert_allclose(tau, 1.0 / cat["A_sigma"] ** 2, rtol=1e-14)
+    p_mu, p_var, _ = O.posterior(K, m, tau, nu)
+    np.testing.assert_allclose(mu, p_mu, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(var, p_var, rtol=1e-7)
+    # prediction: the oracle's GP conditional with the mean function at the queries
+    qm_c, qv = O.predict(cat, K, m, tau, nu, lq, bq, sq)
+    uq = O.unit_vectors(lq, bq)
+    shift = np.log(Lr.mean_extinction(uq, sq, res["theta"]) / (cat["rho_bar"] * sq))
+    np.testing.assert_allclose(pm, qm_c + shift, rtol=0, atol=1e-8)
+    np.testing.assert_allclose(pv, qv, rtol=1e-7)
+
+
+def test_learning_on_the_letterbox_field(gm):
+    """6,000 stars of the Sect. 5 letter-box field (FP32 form): the mode is
+    found, it raises the log posterior above the hyperprior means, and the
+    well-constrained parameters lie within 5 Laplace sigma of the truth."""
+    cat = make_disc_catalogue(6000, seed=0, truth="fft")
+    with _ctx(gm, cat, gm.PREC_FP32) as ctx:
+        ctx.build_cov()
+        first = ctx.learn_mean(Lr.PRIOR_MEAN, Lr.PRIOR_MEAN, max_iter=1, tol=1e-8)
+        ctx.set_mean_fn(None)
+        res = ctx.learn_mean(Lr.PRIOR_MEAN, Lr.PRIOR_MEAN, max_iter=50, tol=1e-8)
+    assert res["iters"] < 50
+    assert res["log_post"] >= first["log_post"]
+    z = (np.log(res["theta"]) - np.log(cat["theta_true"])) / np.sqrt(np.diag(res["cov_phi"]))
+    print("letter-box MAP", res["theta"], "truth", cat["theta_true"], "z", z)
+    assert np.all(np.isfinite(z))
+    assert np.all(np.abs(z[[2, 3, 4]]) < 5.0), z

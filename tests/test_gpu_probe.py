@@ -126,7 +126,8 @@ def test_probed_fields_match_exact_fields(gm):
     out = {}
     for pf in (0.0, 3.0):
         cfg = gm.default_config(sigma2=1.0, outer_scale_pc=20.0, rho_bar=1e-3, cutoff_pc=60.0,
-                                n_nodes=32, precision=gm.PREC_FP32, cg_tol=1e-7, probe_factor=pf)
+                                n_nodes=32, quad_rule=gm.QUAD_GL, precision=gm.PREC_FP32,
+                                cg_tol=1e-7, probe_factor=pf)
         with gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"],
                         field_id=fid, field_L0=L0, field_cutoff=3 * L0) as ctx:
             ctx.build_cov()
