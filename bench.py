@@ -467,7 +467,9 @@ def run_gpu(a):
     # dominant kernel and its roofline
     dom = max(kt.items(), key=lambda kv: kv[1][1])
     cols = st["probe_colours"] if a.probe > 0 else n
-    panel = cfg.rhs_panel or (math.ceil(cols / 32) * 32)
+    # right-hand sides per product launch (the panel may hold fewer columns
+    # than there are solves when memory caps it)
+    panel = st.get("variance_panel_width") or cfg.rhs_panel or (math.ceil(cols / 32) * 32)
     roof = roofline_for(dom[0], dom[1][0], dom[1][1], st, a.precision, panel)
     launches = int(sum(v[0] for v in kt.values()))
     total_ms = sum(v[1] for v in kt.values())

@@ -167,6 +167,9 @@ typedef struct {
                               summed over fields (last gm_build_cov)          */
   int64_t tile_ksteps;     /* tensor-core tiles: K-steps of 16 union columns
                               summed over 128-row blocks (0: CUDA-core path)  */
+  int64_t variance_panel_width; /* right-hand sides per panel of the last
+                              multi-RHS solve (each product launch covers
+                              this many columns)                             */
 } gm_stats;
 
 /* Fills *cfg with defaults: sigma2 1, L0 20 pc, rho_bar 1e-3 mag/pc, cutoff

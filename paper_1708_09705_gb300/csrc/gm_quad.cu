@@ -144,14 +144,17 @@ constexpr int kWinK0 = (kWinEmin - kTabF32.emin) << kTabF32.m;  // first segment
 constexpr int kWinSegs =  // incl. the zero segment
     ((kTabF32.emax - kTabF32.emin) << kTabF32.m) + 1 - kWinK0;
 
-// tab8 points at copy (lane % 8) of window segment 0; t describes the window.
-__device__ __forceinline__ float g_lookup_rep(const float4* __restrict__ tab8, const TabF32& t,
-                                              float x) {
-  x = fmaxf(x, t.xmin);
-  int bits = __float_as_int(x);
-  int k = min((bits - t.base) >> t.shift, t.last);
-  float v = __int_as_float(((bits << (23 - t.shift)) & 0x007fffff) | 0x3f800000) - 1.0f;
-  float4 c = tab8[k * kRep];
+// tab8 points at copy (lane % 8) of window segment 0.  The window's geometry
+// is compile-time, so the segment offset folds into the load's address.
+// x must be >= 2^kWinEmin (callers add it to the separation).
+constexpr int kWinShift = 23 - kTabF32.m;
+constexpr int kWinBaseSeg = (127 + kWinEmin) << kTabF32.m;  // (float bits of 2^kWinEmin) >> shift
+constexpr int kWinLast = kWinSegs - 1;
+__device__ __forceinline__ float g_lookup_rep(const float4* __restrict__ tab8, float x) {
+  const int bits = __float_as_int(x);
+  const int k = min((bits >> kWinShift) - kWinBaseSeg, kWinLast);
+  const float v = __int_as_float(((bits << (23 - kWinShift)) & 0x007fffff) | 0x3f800000) - 1.0f;
+  const float4 c = tab8[k * kRep];
   return fmaf(v, fmaf(v, fmaf(v, c.w, c.z), c.y), c.x);
 }
 
@@ -208,16 +211,12 @@ __global__ void __launch_bounds__(pair_threads<T, KPL>()) k_pair_quad(
   T* wq = zq + kMaxNodes;
   const T4* tab;
   const int lane = threadIdx.x & 31;
-  TabF32 tw = tf;  // the shared-memory window of the FP32 table
   if (sizeof(T) == 4) {
     // the FP32 table window lives in shared memory, kRep copies per segment
     float4* st = reinterpret_cast<float4*>(smem + 2 * kMaxNodes * sizeof(T));
     const float4* gt = reinterpret_cast<const float4*>(gtab) + kWinK0;
     for (int k = threadIdx.x; k < kWinSegs * kRep; k += blockDim.x) st[k] = gt[k / kRep];
     tab = reinterpret_cast<const T4*>(st + (lane & (kRep - 1)));
-    tw.base = tf.base + (kWinK0 << tf.shift);
-    tw.last = tf.last - kWinK0;
-    tw.xmin = __int_as_float(tw.base);
   } else {
     tab = reinterpret_cast<const T4*>(gtab);
   }
@@ -262,12 +261,16 @@ __global__ void __launch_bounds__(pair_threads<T, KPL>()) k_pair_quad(
 #pragma unroll
       for (int k = 0; k < KPL; ++k) {
         T d = t - tp[k];
-        T x = d * d + t * ctp[k];
         T gv;
-        if (sizeof(T) == 4)
-          gv = (T)g_lookup_rep(reinterpret_cast<const float4*>(tab), tw, (float)x);
-        else
+        if (sizeof(T) == 4) {
+          // x >= 2^kWinEmin by construction: the window's floor is added
+          const float x = fmaf((float)d, (float)d,
+                               fmaf((float)t, (float)ctp[k], __int_as_float((127 + kWinEmin) << 23)));
+          gv = (T)g_lookup_rep(reinterpret_cast<const float4*>(tab), x);
+        } else {
+          const T x = d * d + t * ctp[k];
           gv = (T)g_lookup(reinterpret_cast<const D4*>(tab), td, (double)x);
+        }
         inner += wp[k] * gv;
       }
       acc += wq[q] * inner;

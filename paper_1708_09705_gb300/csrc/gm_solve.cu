@@ -1064,11 +1064,15 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   if (R == 0) {
     size_t free_b = 0, tot_b = 0;
     cudaMemGetInfo(&free_b, &tot_b);
-    double budget = std::min<double>(0.4 * (double)free_b, 48e9);
-    R = (int64_t)(budget / (5.0 * (double)n * sizeof(TV)));
+    // five panel arrays (+ three BF16 planes of PD for the tensor-core
+    // product) within half the free memory, at most 160 GB
+    double budget = std::min<double>(0.5 * (double)free_b, 160e9);
+    const double per = 5.0 * sizeof(TV) + (sizeof(TV) == 4 && c->tc_nblk > 0 ? 6.0 : 0.0);
+    R = (int64_t)(budget / (per * (double)n));
   }
   R = std::max<int64_t>(32, std::min<int64_t>(R, ceil_div(n_cols_all, 32) * 32));
   R = (R / 32) * 32;
+  c->stats.variance_panel_width = R;
   const int nbx = std::max(1, (int)std::min<int64_t>(ceil_div(n, 8), (int64_t)(4 * sms * 32 / (R / 32 + 1)) + 1));
   const size_t pbytes = (size_t)n * R * sizeof(TV);
   // partial rows: the panel product may write more rows (one per 128-row tile)
