@@ -72,18 +72,30 @@ def density(x, theta, r_sun=R_SUN, w=BUMP_W):
     return disc + bump
 
 
-def mean_extinction(u, s, theta, r_sun=R_SUN, w=BUMP_W):
-    """E[A] = int_0^s rho(t u) dt per star: the disc by adaptive quadrature,
-    the bump in closed form (the integral of a normal density)."""
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(200)
+
+
+def _disc_terms(u, s, theta, r_sun):
+    """The disc integrand and its two shape derivatives at the 200 nodes."""
     L, H, rho0, sb, Ab = theta
-    out = np.empty(len(s))
-    for i, (ui, si) in enumerate(zip(u, s)):
-        f = lambda t: rho0 * math.exp(-(math.hypot(r_sun - t * ui[0], t * ui[1]) - r_sun) / L
-                                      - abs(t * ui[2]) / H)
-        disc, _ = integrate.quad(f, 0.0, si, epsabs=0.0, epsrel=1e-13, limit=200)
-        bump = Ab * (special.ndtr((si - sb) / w) - special.ndtr(-sb / w))
-        out[i] = disc + bump
-    return out
+    u = np.asarray(u, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    t = 0.5 * s[:, None] * (1.0 + _GL_X[None, :])          # (n, 200)
+    dR = np.hypot(r_sun - t * u[:, 0:1], t * u[:, 1:2]) - r_sun
+    az = np.abs(t * u[:, 2:3])
+    f = rho0 * np.exp(-dR / L - az / H)
+    return s, f, dR / L, az / H
+
+
+def mean_extinction(u, s, theta, r_sun=R_SUN, w=BUMP_W):
+    """E[A] = int_0^s rho(t u) dt per star: the disc by a 200-node
+    Gauss-Legendre rule on [0, s] (the integrand is smooth in t), the bump in
+    closed form (the integral of a normal density)."""
+    L, H, rho0, sb, Ab = theta
+    s, f, _, _ = _disc_terms(u, s, theta, r_sun)
+    disc = 0.5 * s * (f @ _GL_W)
+    bump = Ab * (special.ndtr((s - sb) / w) - special.ndtr(-sb / w))
+    return disc + bump
 
 
 def prior_mean(u, s, theta, Kdiag, **kw):
@@ -91,17 +103,20 @@ def prior_mean(u, s, theta, Kdiag, **kw):
     return np.log(mean_extinction(u, s, theta, **kw)) - 0.5 * np.asarray(Kdiag)
 
 
-def jacobian(u, s, theta, Kdiag, h=1e-6, **kw):
-    """d m / d phi (n x 5), phi = ln theta, by central differences in phi."""
-    phi = np.log(np.asarray(theta, dtype=np.float64))
-    J = np.empty((len(s), 5))
-    for k in range(5):
-        e = np.zeros(5)
-        e[k] = h
-        mp = prior_mean(u, s, np.exp(phi + e), Kdiag, **kw)
-        mm = prior_mean(u, s, np.exp(phi - e), Kdiag, **kw)
-        J[:, k] = (mp - mm) / (2 * h)
-    return J
+def jacobian(u, s, theta, Kdiag, r_sun=R_SUN, w=BUMP_W):
+    """d m / d phi (n x 5), phi = ln theta: d ln E / d ln theta_k, each the
+    derivative of the line integral taken under the integral sign (disc:
+    rho (R - R_sun)/L, rho |z|/H and rho for L, H, rho0) or of the bump's
+    closed form (s_b, A_b).  K_ii does not depend on theta."""
+    L, H, rho0, sb, Ab = theta
+    s, f, xl, xh = _disc_terms(u, s, theta, r_sun)
+    E = mean_extinction(u, s, theta, r_sun, w)
+    a, a0 = (s - sb) / w, -sb / w
+    pdf = lambda z: np.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+    cols = [0.5 * s * ((f * xl) @ _GL_W), 0.5 * s * ((f * xh) @ _GL_W), 0.5 * s * (f @ _GL_W),
+            sb * Ab * (pdf(a0) - pdf(a)) / w,
+            Ab * (special.ndtr(a) - special.ndtr(a0))]
+    return np.stack(cols, axis=1) / E[:, None]
 
 
 def log_posterior(atil, sig, K, m, phi, mu, s2):

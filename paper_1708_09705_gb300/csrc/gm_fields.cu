@@ -142,7 +142,7 @@ __global__ void k_pk_elem(int64_t n_items, const int4* __restrict__ items,
     const int64_t c = (int64_t)w.y * 32 + lane;
     const int64_t gid = F.Wptr + c;
     const int64_t i0 = (int64_t)w.z * kSeg, i1 = min(i0 + kSeg, F.nrows);
-    double s1 = 0, s2 = 0;
+    PartialSum<float> s1, s2;
     if (MODE == kPkUpd2 && !active[gid]) continue;
     const float alpha = MODE == kPkUpd1 ? (float)scal[gid] : 0.f;
     const float beta = MODE == kPkUpd2 ? (float)scal[tcols + gid] : 0.f;
@@ -154,16 +154,16 @@ __global__ void k_pk_elem(int64_t n_items, const int4* __restrict__ items,
         X[k] = 0.f;
         P[k] = zi;
         PD[k] = dv[r] * zi;
-        s1 += (double)ri * (double)zi;
-        s2 += (double)ri * (double)ri;
+        s1.add(ri * zi);
+        s2.add(ri * ri);
       } else if (MODE == kPkPQ) {
-        s1 += (double)P[k] * (double)Q[k];
+        s1.add(P[k] * Q[k]);
       } else if (MODE == kPkUpd1) {
         X[k] += alpha * P[k];
         const float ri = Rr[k] - alpha * Q[k];
         Rr[k] = ri;
-        s1 += (double)ri * (double)(minv[r] * ri);
-        s2 += (double)ri * (double)ri;
+        s1.add(ri * (minv[r] * ri));
+        s2.add(ri * ri);
       } else {
         const float pi = minv[r] * Rr[k] + beta * P[k];
         P[k] = pi;
@@ -172,8 +172,8 @@ __global__ void k_pk_elem(int64_t n_items, const int4* __restrict__ items,
     }
     if (MODE != kPkUpd2) {
       const int64_t po = F.PO + (int64_t)w.z * F.W + c;
-      pa[po] = s1;
-      if (MODE != kPkPQ) pb[po] = s2;
+      pa[po] = s1.value();
+      if (MODE != kPkPQ) pb[po] = s2.value();
     }
   }
 }

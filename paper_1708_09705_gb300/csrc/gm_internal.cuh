@@ -200,6 +200,33 @@ struct gm_ctx {
 
 namespace gm {
 
+// Running sum for per-element dot-product partials.  FP32 panels use a
+// compensated (Kahan) FP32 sum: GB300's FP64 pipe is a small fraction of its
+// FP32 rate, so one FP64 add per panel element bounded the element-wise
+// passes; the compensation keeps the total within a few FP32 ulps whatever
+// the number of terms.  FP64 panels keep a plain FP64 sum.
+template <typename TV>
+struct PartialSum {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct PartialSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+}  // namespace gm
+
+namespace gm {
+
 // ---------------------------------------------------------------- helpers
 gm_status set_error(gm_ctx* c, gm_status st, const std::string& msg);
 gm_status cuda_fail(gm_ctx* c, cudaError_t e, const char* what);

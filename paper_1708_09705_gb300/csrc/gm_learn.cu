@@ -348,6 +348,15 @@ extern "C" gm_status gm_learn_mean(gm_ctx* c, const double* theta0, const double
   gm_status st = gm_set_mean_fn(c, theta0, r_sun_pc, bump_width_pc);
   if (st != GM_OK) return st;
   c->launches = 0;
+  // The Hessian comes from differences of gradients 1e-4 apart in phi, so the
+  // gradients' solves run to 1e-12 (FP32 contexts: by the FP64-residual
+  // refinement of the mean solve); the context's tolerance is restored after.
+  struct TolGuard {
+    gm_ctx* c;
+    double tol;
+    ~TolGuard() { c->cfg.cg_tol = tol; }
+  } guard{c, c->cfg.cg_tol};
+  c->cfg.cg_tol = std::min(c->cfg.cg_tol, 1e-12);
   const int G = 2 * sm_count(c);
   if (!ensure(c, c->mf_J, (size_t)5 * c->n * sizeof(double)) ||
       !ensure(c, c->mf_part, (size_t)6 * G * sizeof(double)))

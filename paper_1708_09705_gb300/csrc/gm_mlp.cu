@@ -13,7 +13,15 @@
 // Operands live in shared memory in the no-swizzle K-major layout of 8 x 16 B
 // core matrices; one thread issues tcgen05.mma, tcgen05.commit signals an
 // mbarrier, and the four warps read the accumulator rows with tcgen05.ld,
-// add the bias, apply SiLU and write the next layer's BF16 operand.
+// add the bias, apply SiLU and write the next layer's operand.
+//
+// Precision: every operand (features, activations, weights) is held as two
+// BF16 pieces x = x_hi + x_lo (x_hi = x rounded to BF16, x_lo = the rounded
+// remainder) and each product is x_hi y_hi + x_hi y_lo + x_lo y_hi (three
+// MMAs, FP32 accumulation): about 2^-16 relative, so the network's output is
+// that of its FP32 weights to ~1e-4 in ln K.  A single BF16 piece (2^-8 per
+// operand) limited the served entries to ~1 % in K, the scale of the
+// network's own fit.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -38,6 +46,7 @@ constexpr int kSW = 64 * 64 * 2;     // B of layers 2, 3
 constexpr int kSW4 = 16 * 64 * 2;    // B of layer 4: 16 rows x 64
 constexpr int kSA1 = 128 * 16 * 2;   // A of layer 1
 constexpr int kSA = 128 * 64 * 2;    // A of layers 2-4
+constexpr int kSWimg = kSW1 + 2 * kSW + kSW4;  // one piece of all weight images (20 KB)
 
 // byte offset of element (row, k) in a K-major no-swizzle image with K_total
 // columns: core matrices of 8 rows x 8 elements (16 B rows), k-adjacent
@@ -131,21 +140,33 @@ __device__ __forceinline__ void pair_features(double si, double sj, double chord
   f[4] = (float)log(L0 / 20.0);
 }
 
-// Writes one thread's 64 activations (row `row`) into a K = 64 operand image.
+// Two BF16 pieces of x, packed in pairs: hi = x rounded to BF16 (nearest
+// even), lo = the remainder x - hi rounded the same way.
+__device__ __forceinline__ void split2_pack(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Writes 8 consecutive values of one row (k = 8 g ..) of a K-major operand,
+// both pieces (the lo image `lo_off` bytes after the hi image).
+__device__ __forceinline__ void store8_split(unsigned char* img, int lo_off, int off, const float* v) {
+  uint4 uh, ul;
+  split2_pack(v[0], v[1], uh.x, ul.x);
+  split2_pack(v[2], v[3], uh.y, ul.y);
+  split2_pack(v[4], v[5], uh.z, ul.z);
+  split2_pack(v[6], v[7], uh.w, ul.w);
+  *reinterpret_cast<uint4*>(img + off) = uh;
+  *reinterpret_cast<uint4*>(img + lo_off + off) = ul;
+}
+
+// Writes one thread's 64 activations (row `row`) into a K = 64 operand image
+// (hi piece at sA, lo piece at sA + kSA).
 __device__ __forceinline__ void store_row64(unsigned char* sA, int row, const float* h) {
 #pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    __nv_bfloat162 p0 = __floats2bfloat162_rn(h[8 * g + 0], h[8 * g + 1]);
-    __nv_bfloat162 p1 = __floats2bfloat162_rn(h[8 * g + 2], h[8 * g + 3]);
-    __nv_bfloat162 p2 = __floats2bfloat162_rn(h[8 * g + 4], h[8 * g + 5]);
-    __nv_bfloat162 p3 = __floats2bfloat162_rn(h[8 * g + 6], h[8 * g + 7]);
-    uint4 u;
-    u.x = *reinterpret_cast<uint32_t*>(&p0);
-    u.y = *reinterpret_cast<uint32_t*>(&p1);
-    u.z = *reinterpret_cast<uint32_t*>(&p2);
-    u.w = *reinterpret_cast<uint32_t*>(&p3);
-    *reinterpret_cast<uint4*>(sA + kmaj_off(row, 8 * g, 64)) = u;
-  }
+  for (int g = 0; g < 8; ++g) store8_split(sA, kSA, kmaj_off(row, 8 * g, 64), h + 8 * g);
 }
 
 // Forward pass over a list of pairs; writes y and e.  Block = 128 threads.
@@ -156,20 +177,21 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpIn in, const unsigned ch
                                                      float* __restrict__ e_out,
                                                      unsigned* __restrict__ flags) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  // weight images: hi pieces (20 KB) then lo pieces (20 KB)
   unsigned char* sW1 = smem;                 // 2 KB
   unsigned char* sW2 = sW1 + kSW1;           // 8 KB
   unsigned char* sW3 = sW2 + kSW;            // 8 KB
   unsigned char* sW4 = sW3 + kSW;            // 2 KB
-  unsigned char* sA1 = sW4 + kSW4;           // 4 KB
-  unsigned char* sA = sA1 + kSA1;            // 16 KB
-  float* sBias = reinterpret_cast<float*>(sA + kSA);  // 64*3 + 2
+  unsigned char* sA1 = smem + 2 * kSWimg;    // 4 KB hi + 4 KB lo
+  unsigned char* sA = sA1 + 2 * kSA1;        // 16 KB hi + 16 KB lo
+  float* sBias = reinterpret_cast<float*>(sA + 2 * kSA);  // 64*3 + 2
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
   const int tid = threadIdx.x, warp = tid >> 5;
   // weights and biases into shared memory
-  for (int k = tid; k < (kSW1 + 2 * kSW + kSW4) / 16; k += blockDim.x)
+  for (int k = tid; k < 2 * kSWimg / 16; k += blockDim.x)
     reinterpret_cast<uint4*>(smem)[k] = reinterpret_cast<const uint4*>(wimg)[k];
   for (int k = tid; k < kMlpHid; k += blockDim.x) {
     sBias[k] = params[kB1 + k];
@@ -210,18 +232,7 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpIn in, const unsigned ch
       for (int k = 0; k < 16; ++k) f[k] = 0.f;
       if (p < in.n) pair_features(in.si[p], in.sj[p], in.chord[p], in.sigma2, in.L0, f);
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        __nv_bfloat162 q0 = __floats2bfloat162_rn(f[8 * g + 0], f[8 * g + 1]);
-        __nv_bfloat162 q1 = __floats2bfloat162_rn(f[8 * g + 2], f[8 * g + 3]);
-        __nv_bfloat162 q2 = __floats2bfloat162_rn(f[8 * g + 4], f[8 * g + 5]);
-        __nv_bfloat162 q3 = __floats2bfloat162_rn(f[8 * g + 6], f[8 * g + 7]);
-        uint4 u;
-        u.x = *reinterpret_cast<uint32_t*>(&q0);
-        u.y = *reinterpret_cast<uint32_t*>(&q1);
-        u.z = *reinterpret_cast<uint32_t*>(&q2);
-        u.w = *reinterpret_cast<uint32_t*>(&q3);
-        *reinterpret_cast<uint4*>(sA1 + kmaj_off(tid, 8 * g, 16)) = u;
-      }
+      for (int g = 0; g < 2; ++g) store8_split(sA1, kSA1, kmaj_off(tid, 8 * g, 16), f + 8 * g);
     }
     for (int layer = 0; layer < 4; ++layer) {
       asm volatile("fence.proxy.async.shared::cta;");
@@ -229,15 +240,24 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpIn in, const unsigned ch
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;");
       if (tid == 0) {
+        // per K-step: the two small cross terms, then hi x hi
         if (layer == 0) {
-          mma_bf16(tmem, mdesc(dA1, 128, 256), mdesc(dW1, 128, 256), id64, 0);
+          mma_bf16(tmem, mdesc(dA1 + kSA1, 128, 256), mdesc(dW1, 128, 256), id64, 0);
+          mma_bf16(tmem, mdesc(dA1, 128, 256), mdesc(dW1 + kSWimg, 128, 256), id64, 1);
+          mma_bf16(tmem, mdesc(dA1, 128, 256), mdesc(dW1, 128, 256), id64, 1);
         } else {
           const uint32_t dw = layer == 1 ? dW2 : (layer == 2 ? dW3 : dW4);
           const uint32_t idd = layer == 3 ? id16 : id64;
 #pragma unroll
-          for (int s = 0; s < 4; ++s)
-            mma_bf16(tmem, mdesc(dA + 256 * s, 128, 1024), mdesc(dw + 256 * s, 128, 1024), idd,
-                     s > 0 ? 1u : 0u);
+          for (int s = 0; s < 4; ++s) {
+            const uint64_t ah = mdesc(dA + 256 * s, 128, 1024),
+                           al = mdesc(dA + kSA + 256 * s, 128, 1024),
+                           wh = mdesc(dw + 256 * s, 128, 1024),
+                           wl = mdesc(dw + kSWimg + 256 * s, 128, 1024);
+            mma_bf16(tmem, al, wh, idd, s > 0 ? 1u : 0u);
+            mma_bf16(tmem, ah, wl, idd, 1u);
+            mma_bf16(tmem, ah, wh, idd, 1u);
+          }
         }
         mma_commit(mb);
       }
@@ -275,33 +295,29 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpIn in, const unsigned ch
   }
 }
 
-// BF16 operand images of the weights (B operands are W^T, K-major):
+// BF16 operand images of the weights (B operands are W^T, K-major), two
+// pieces (hi image, then lo image kSWimg bytes later):
 //   layer 1: rows n < 64, k < 16 (k >= 5 zero); layers 2, 3: 64 x 64;
 //   layer 4: rows n < 16 (n >= 2 zero), k < 64.
+__device__ __forceinline__ void put_split(unsigned char* img, int off, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  *reinterpret_cast<__nv_bfloat16*>(img + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(img + kSWimg + off) = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 __global__ void k_mlp_pack(const float* __restrict__ params, unsigned char* __restrict__ img) {
-  __nv_bfloat16* w1 = reinterpret_cast<__nv_bfloat16*>(img);
-  unsigned char* b2 = img + kSW1;
-  unsigned char* b3 = b2 + kSW;
-  unsigned char* b4 = b3 + kSW;
   for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < 64 * 64; idx += blockDim.x * gridDim.x) {
     const int n = idx / 64, k = idx % 64;
-    if (k < 16) {
-      float v = k < kMlpIn ? params[kW1 + k * kMlpHid + n] : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(w1) + kmaj_off(n, k, 16)) =
-          __float2bfloat16_rn(v);
-    }
-    *reinterpret_cast<__nv_bfloat16*>(b2 + kmaj_off(n, k, 64)) =
-        __float2bfloat16_rn(params[kW2 + k * kMlpHid + n]);
-    *reinterpret_cast<__nv_bfloat16*>(b3 + kmaj_off(n, k, 64)) =
-        __float2bfloat16_rn(params[kW3 + k * kMlpHid + n]);
-    if (n < 16) {
-      float v = n < kMlpOut ? params[kW4 + k * kMlpOut + n] : 0.f;
-      *reinterpret_cast<__nv_bfloat16*>(b4 + kmaj_off(n, k, 64)) = __float2bfloat16_rn(v);
-    }
+    if (k < 16) put_split(img, kmaj_off(n, k, 16), k < kMlpIn ? params[kW1 + k * kMlpHid + n] : 0.f);
+    put_split(img, kSW1 + kmaj_off(n, k, 64), params[kW2 + k * kMlpHid + n]);
+    put_split(img, kSW1 + kSW + kmaj_off(n, k, 64), params[kW3 + k * kMlpHid + n]);
+    if (n < 16)
+      put_split(img, kSW1 + 2 * kSW + kmaj_off(n, k, 64),
+                n < kMlpOut ? params[kW4 + k * kMlpOut + n] : 0.f);
   }
 }
 
-constexpr size_t kMlpSmem = kSW1 + 2 * kSW + kSW4 + kSA1 + kSA + 256 * sizeof(float);
+constexpr size_t kMlpSmem = 2 * kSWimg + 2 * kSA1 + 2 * kSA + 256 * sizeof(float);
 
 gm_status mlp_forward(gm_ctx* c, const MlpIn& in, float* y, float* e) {
   if (!c->mlp_params || !c->mlp_trained) return set_error(c, GM_E_STATE, "surrogate has no weights");
@@ -334,7 +350,7 @@ static bool mlp_is_dev(const void* p) {
 gm_status mlp_ensure(gm_ctx* c) {
   if (c->mlp_params) return GM_OK;
   c->mlp_params = (float*)dev_alloc(c, kMlpParams * sizeof(float));
-  c->mlp_img = (unsigned char*)dev_alloc(c, kSW1 + 2 * kSW + kSW4);
+  c->mlp_img = (unsigned char*)dev_alloc(c, 2 * kSWimg);
   if (!c->mlp_params || !c->mlp_img) return set_error(c, GM_E_NOMEM, "surrogate weights");
   return GM_OK;
 }

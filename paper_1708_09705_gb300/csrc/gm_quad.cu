@@ -175,6 +175,11 @@ __device__ __forceinline__ double wendland(double h) {
   double u = 1.0 - h, u2 = u * u;
   return u2 * u2 * (4.0 * h + 1.0);
 }
+__device__ __forceinline__ float wendland_f(float h) {
+  if (h >= 1.0f) return 0.0f;
+  const float u = 1.0f - h, u2 = u * u;
+  return u2 * u2 * fmaf(4.0f, h, 1.0f);
+}
 
 struct QuadParams {
   double inv_L0;
@@ -278,19 +283,37 @@ __global__ void __launch_bounds__(pair_threads<T, KPL>()) k_pair_quad(
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane == 0) {
-      double R = (double)acc;
-      double K = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
-      if (P.taper == GM_TAPER_WENDLAND) {
-        double ds = si - sj;
-        double d = sqrt(fma(ds, ds, si * sj * chord2));
-        K *= wendland(d * inv_cut);
+      T K;
+      if (sizeof(T) == 4) {
+        // FP32 form: the entry's own arithmetic in FP32 too (GB300's FP64
+        // pipe is narrow; per-pair FP64 work, not the node sum, bounded this
+        // kernel): log1p and the taper to ~1e-7 relative
+        const float R = (float)acc;
+        float Kf = P.form == GM_FORM_LOGNORMAL ? log1pf(R) : R;
+        if (P.taper == GM_TAPER_WENDLAND) {
+          // the difference of the distances in FP64: it cancels, and the
+          // taper near the cutoff amplifies its error
+          const float ds = (float)(si - sj);
+          const float d = sqrtf(fmaf(ds, ds, (float)si * (float)sj * (float)c2));
+          Kf *= wendland_f(d * (float)inv_cut);
+        }
+        K = (T)Kf;
+      } else {
+        const double R = (double)acc;
+        double Kd = P.form == GM_FORM_LOGNORMAL ? log1p(R) : R;
+        if (P.taper == GM_TAPER_WENDLAND) {
+          const double ds = si - sj;
+          const double d = sqrt(fma(ds, ds, si * sj * chord2));
+          Kd *= wendland(d * inv_cut);
+        }
+        K = (T)Kd;
       }
-      if (!isfinite(K)) atomicOr(flags, kFlagNonFinite);
-      val[e] = (T)K;
+      if (!isfinite((double)K)) atomicOr(flags, kFlagNonFinite);
+      val[e] = K;
       if (P.symmetric && j == i) {
-        kdiag[i] = (double)(T)K;
+        kdiag[i] = (double)K;
         prior_m[i] = P.log_rho_bar + log(si) -
-                     (P.form == GM_FORM_LOGNORMAL ? 0.5 * (double)(T)K : 0.5 * P.sigma2);
+                     (P.form == GM_FORM_LOGNORMAL ? 0.5 * (double)K : 0.5 * P.sigma2);
       }
     }
   }

@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kBT) k_panel_init(int64_t n, int R, const TV* 
   const int c = blockIdx.y * 32 + lane;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  double rz = 0, bb = 0;
+  PartialSum<TV> rz, bb;
   for (int64_t i = w; i < n; i += nw) {
     int64_t k = i * R + c;
     TV ri = Rr[k];
@@ -426,11 +426,11 @@ __global__ void __launch_bounds__(kBT) k_panel_init(int64_t n, int R, const TV* 
     X[k] = 0;
     P[k] = zi;
     PD[k] = dv[i] * zi;
-    rz += (double)ri * (double)zi;
-    bb += (double)ri * (double)ri;
+    rz.add(ri * zi);
+    bb.add(ri * ri);
   }
-  sh_rz[wib][lane] = rz;
-  sh_bb[wib][lane] = bb;
+  sh_rz[wib][lane] = rz.value();
+  sh_bb[wib][lane] = bb.value();
   __syncthreads();
   if (wib == 0) {
     double a = 0, b = 0;
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(kBT) k_panel_init_warm(int64_t n, int R, const
   const int c = blockIdx.y * 32 + lane;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  double rz = 0, bb = 0;
+  PartialSum<TV> rz, bb;
   for (int64_t i = w; i < n; i += nw) {
     int64_t k = i * R + c;
     TV v = Rr[k];
@@ -480,11 +480,11 @@ __global__ void __launch_bounds__(kBT) k_panel_init_warm(int64_t n, int R, const
     Rr[k] = ri;
     P[k] = zi;
     PD[k] = dv[i] * zi;
-    rz += (double)ri * (double)zi;
-    bb += (double)v * (double)v;
+    rz.add(ri * zi);
+    bb.add(v * v);
   }
-  sh_rz[wib][lane] = rz;
-  sh_bb[wib][lane] = bb;
+  sh_rz[wib][lane] = rz.value();
+  sh_bb[wib][lane] = bb.value();
   __syncthreads();
   if (wib == 0) {
     double a = 0, b = 0;
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kBT) k_panel_spmm(int64_t n, int R,
   const int c = blockIdx.y * 32 + lane;
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  double pq = 0;
+  PartialSum<TV> pq;
   for (int64_t i = w; i < n; i += nw) {
     const int64_t e0 = row_ptr[i], e1 = row_ptr[i + 1];
     TV acc = 0;
@@ -535,9 +535,9 @@ __global__ void __launch_bounds__(kBT) k_panel_spmm(int64_t n, int R,
     TV pi = P[k];
     TV qi = pi + dv[i] * acc;
     Q[k] = qi;
-    pq += (double)pi * (double)qi;
+    pq.add(pi * qi);
   }
-  sh[wib][lane] = pq;
+  sh[wib][lane] = pq.value();
   __syncthreads();
   if (wib == 0) {
     double a = 0;
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(kBT) k_panel_update1(int64_t n, int R, const T
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const TV a = (TV)scal[c];
-  double rz = 0, rr = 0;
+  PartialSum<TV> rz, rr;
   // four rows per pass with all loads issued first (memory-level parallelism)
   int64_t i = w;
   for (; i + 3 * nw < n; i += 4 * nw) {
@@ -639,8 +639,8 @@ __global__ void __launch_bounds__(kBT) k_panel_update1(int64_t n, int R, const T
       X[k] = x[u] + a * p[u];
       const TV ri = r[u] - a * q[u];
       Rr[k] = ri;
-      rz += (double)ri * (double)(m[u] * ri);
-      rr += (double)ri * (double)ri;
+      rz.add(ri * (m[u] * ri));
+      rr.add(ri * ri);
     }
   }
   for (; i < n; i += nw) {
@@ -648,11 +648,11 @@ __global__ void __launch_bounds__(kBT) k_panel_update1(int64_t n, int R, const T
     X[k] += a * P[k];
     TV ri = Rr[k] - a * Q[k];
     Rr[k] = ri;
-    rz += (double)ri * (double)(minv[i] * ri);
-    rr += (double)ri * (double)ri;
+    rz.add(ri * (minv[i] * ri));
+    rr.add(ri * ri);
   }
-  sh_a[wib][lane] = rz;
-  sh_b[wib][lane] = rr;
+  sh_a[wib][lane] = rz.value();
+  sh_b[wib][lane] = rr.value();
   __syncthreads();
   if (wib == 0) {
     double s1 = 0, s2 = 0;

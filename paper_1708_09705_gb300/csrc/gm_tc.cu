@@ -255,18 +255,18 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, i
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const int cg = c0 + cl + k;
-        double pq = 0.0;
+        float pq = 0.f;
         if (vrow && cg < W) {
           const int64_t at = base + row * W + cg;
           const float p = P[at];
           const float q = p + dr * __uint_as_float(u[k]);
           Q[at] = q;
-          pq = (double)p * (double)q;
+          pq = p * q;
         }
-        if (!packed) {  // uniform over the CTA
+        if (!packed) {  // uniform over the CTA; FP32 tree over the warp's 32 rows
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
-          if (lane == 0) sh_pq[quad * kTcCols + cl + k] = pq;
+          if (lane == 0) sh_pq[quad * kTcCols + cl + k] = (double)pq;
         }
       }
     }
@@ -680,9 +680,12 @@ __global__ void __launch_bounds__(288, 2) k_panel_spmm_tc_ws(
 // that a K-step's B tile is a plain copy of 16 gathered plane rows x 256
 // columns: no register staging and no split on the MMA's critical path.  The
 // tile is kept MN-major in shared memory (the panel's columns contiguous, as
-// in the planes): no-swizzle core matrices of 8 k-rows x 16 B (8 columns),
-// column-adjacent ones 128 B apart, the two 8-row k-groups 4 KB apart, and
-// the MMA's instruction descriptor marks B as MN-major.
+// in the planes) in the 128-byte-swizzled layout: 1 KB atoms of 8 k-rows x
+// 64 columns (a 128-byte row per k) in which the 16-byte chunk c of row r
+// sits at chunk c ^ r, the atoms of consecutive 64-column blocks 1 KB apart
+// and the two 8-row k-groups 4 KB apart; the MMA's instruction descriptor
+// marks B as MN-major.  (Without the swizzle the chunks of one k-row lie
+// 128 B apart, in one bank group, and the tensor core's reads serialise.)
 //
 // Warp roles (160 threads, two CTAs per SM): warps 0-3 are producers -- per
 // K-step thread 0 starts one bulk copy of the tile's A pieces (cp.async.bulk,
@@ -700,21 +703,24 @@ constexpr int kTaProd = 128;
 constexpr int kTaThreads = kTaProd + 32;
 constexpr int kTaPiece = kTcCols * kTcK * 2;              // 8 KB: one plane's B tile
 constexpr int kTaStage = 3 * kTcA + 3 * kTaPiece;         // 36 KB
-constexpr int kTaSmem = kTaRing * kTaStage;               // 108 KB (partials reuse stage 0)
+// 108 KB of stages (the partials reuse stage 0) + 1 KB to align the swizzled atoms
+constexpr int kTaSmem = kTaRing * kTaStage + 1024;
 
-// byte offset of B element (k, n) in the MN-major image of one plane
+// byte offset of B element (k, n) in the swizzled MN-major image of one plane
 __host__ __device__ __forceinline__ int tcb_off(int k, int n) {
-  return (k >> 3) * 4096 + (n >> 3) * 128 + (k & 7) * 16 + (n & 7) * 2;
+  return (n >> 6) * 1024 + (k >> 3) * 4096 + (k & 7) * 128 + ((((n >> 3) & 7) ^ (k & 7)) << 4) +
+         (n & 7) * 2;
 }
 
-// MN-major no-swizzle descriptor: LBO = stride of the k-groups (4 KB), SBO =
-// stride of the 8-column chunks (128 B)
+// MN-major 128-byte-swizzle descriptor: LBO = stride of the 64-column atoms
+// (1 KB), SBO = stride of the 8-row k-groups (4 KB), layout type 2
 __device__ __forceinline__ uint64_t tc_desc_mn(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((4096u >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((4096u >> 4) & 0x3FFF) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -752,11 +758,13 @@ __global__ void __launch_bounds__(kTaThreads, 2) k_panel_spmm_tc_async(
     const float* __restrict__ P, const uint16_t* __restrict__ planes, int64_t plane_elems,
     float* __restrict__ Q, double* __restrict__ part_pq, TcPanels pk,
     unsigned* __restrict__ flags) {
-  extern __shared__ __align__(1024) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t fullA[kTaRing], fullB[kTaRing], empty[kTaRing];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   volatile int* abort_v = &abort_flag;
+  // the swizzle pattern follows the address bits: stages start on 1 KB
+  unsigned char* smem = smem_raw + ((1024u - (tc_smem(smem_raw) & 1023u)) & 1023u);
   double* sh_pq = reinterpret_cast<double*>(smem);  // [4][256], after the last MMA
   constexpr int npl = NP == 3 ? 2 : 3;              // BF16 pieces used per side
   constexpr uint32_t abytes = npl * kTcA;
@@ -805,10 +813,10 @@ __global__ void __launch_bounds__(kTaThreads, 2) k_panel_spmm_tc_async(
   int64_t issued_a = 0;  // bulk copies started by thread 0
 
   if (warp < 4) {
-    // ---- producers.  Thread t copies, per plane, the chunks (k, j) with
-    // k in {t % 8, 8 + t % 8} and j in {t / 8, 16 + t / 8} (16-byte chunk j =
-    // columns 8j .. 8j + 7): a quarter-warp fills one 128-byte core matrix.
-    const int klo = t & 7, j0 = t >> 3;
+    // ---- producers.  Thread t copies, per plane, 16-byte chunk t % 8 of
+    // k-row t / 8 in each of the four 64-column blocks: a quarter-warp fills
+    // one 128-byte row of an atom from 128 contiguous bytes of a plane row.
+    const int clo = t & 7, kr = t >> 3;
     for (int64_t ks = 0; ks < nks; ++ks) {
       const int s = (int)(ks % kTaRing);
       const int64_t use = ks / kTaRing;
@@ -831,27 +839,21 @@ __global__ void __launch_bounds__(kTaThreads, 2) k_panel_spmm_tc_async(
             : "memory");
         ++issued_a;
       }
-      const int32_t* up = upad + (ks0 + ks) * kTcK;
-      const int64_t u0 = __ldg(up + klo), u1 = __ldg(up + 8 + klo);
+      const int64_t row = __ldg(upad + (ks0 + ks) * kTcK + kr);
 #pragma unroll
       for (int p = 0; p < npl; ++p) {
-        const uint16_t* pl = planes + p * plane_elems + base;
+        const uint16_t* pl = planes + p * plane_elems + base + row * W;
         const uint32_t db = tc_smem(sB + p * kTaPiece);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int k = klo + 8 * h;
-          const int64_t row = h ? u1 : u0;
-#pragma unroll
-          for (int g = 0; g < 2; ++g) {
-            const int j = j0 + 16 * g;
-            const int colg = c0 + 8 * j;
-            const bool in = colg < W;
-            const uint16_t* src = in ? pl + row * W + colg : planes;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
-                             db + (uint32_t)tcb_off(k, 8 * j)),
-                         "l"(__cvta_generic_to_global(src)), "r"(in ? 16 : 0)
-                         : "memory");
-          }
+        for (int nb = 0; nb < 4; ++nb) {
+          const int n = 64 * nb + 8 * clo;
+          const int colg = c0 + n;
+          const bool in = colg < W;
+          const uint16_t* src = in ? pl + colg : planes;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                           db + (uint32_t)tcb_off(kr, n)),
+                       "l"(__cvta_generic_to_global(src)), "r"(in ? 16 : 0)
+                       : "memory");
         }
       }
       asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(
@@ -924,18 +926,18 @@ __global__ void __launch_bounds__(kTaThreads, 2) k_panel_spmm_tc_async(
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const int cg = c0 + cl + k;
-        double pq = 0.0;
+        float pq = 0.f;
         if (vrow && cg < W) {
           const int64_t at = base + row * W + cg;
           const float pv = P[at];
           const float qv = pv + dr * __uint_as_float(u[k]);
           Q[at] = qv;
-          pq = (double)pv * (double)qv;
+          pq = pv * qv;
         }
-        if (!packed) {  // uniform over the CTA
+        if (!packed) {  // uniform over the CTA; FP32 tree over the warp's 32 rows
 #pragma unroll
           for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
-          if (lane == 0) sh_pq[warp * kTcCols + cl + k] = pq;
+          if (lane == 0) sh_pq[warp * kTcCols + cl + k] = (double)pq;
         }
       }
     }
@@ -1078,9 +1080,11 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
     uint16_t* pl = (uint16_t*)c->tc_planes.p;
     const int sb = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(pd_elems, 4 * 256), 1),
                                           8 * sm_count(c));
-    GM_PROF(c, "k_split3_planes");
+    // per-kernel timing only for the single-panel path (the packed path may
+    // run inside a graph capture)
+    if (!pk.items) GM_PROF(c, "k_split3_planes");
     k_split3_planes<<<sb, 256, 0, st>>>(pd_elems, PD, pl);
-    GM_PROF(c, "k_panel_spmm_tc");
+    if (!pk.items) GM_PROF(c, "k_panel_spmm_tc");
     const unsigned char* ib = (const unsigned char*)c->tc_img.p;
     if (c->cfg.tc_products == 3)
       k_panel_spmm_tc_async<3><<<grid, kTaThreads, kTaSmem, st>>>(
@@ -1116,9 +1120,9 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
 
 // Variant of the tile product: 1, 2 = CTA-synchronous with gathers one or two
 // steps ahead, 3 = warp-specialised ring, 4 = B copied asynchronously from
-// BF16 planes of PD (opt-in).  GM_TC_PREFETCH=1|2|3|4 pins it, else the
-// fastest of 1-3 on the context's first panel product (one timed launch each;
-// the product is idempotent: Q is overwritten).
+// BF16 planes of PD.  GM_TC_PREFETCH=1|2|3|4 pins it, else the fastest on the
+// context's first panel product (one timed launch each; the product is
+// idempotent: Q is overwritten).
 static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv, const float* P,
                          const float* PD, float* Q, double* part_pq, TcPanels pk,
                          int64_t pd_elems) {
@@ -1153,7 +1157,7 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
   GM_CUDA_CHECK(c, cudaEventCreate(&a));
   GM_CUDA_CHECK(c, cudaEventCreate(&b));
   float best = 1e30f;
-  for (int pf : {1, 2, 3}) {
+  for (int pf : {1, 2, 3, 4}) {
     float ms = 0;
     GM_CUDA_CHECK(c, cudaEventRecord(a, c->stream));
     gm_status ls = launch_tc(c, pf, grid, n, R, dv, P, PD, Q, part_pq, pk, pd_elems, c->stream);
@@ -1180,7 +1184,7 @@ gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const floa
   const TcPanels pk{nullptr, nullptr, nullptr, nullptr};
   gm_status s = tc_tune(c, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R);
   if (s != GM_OK) return s;
-  GM_PROF(c, "k_panel_spmm_tc");
+  if (c->tc_pf != 4) GM_PROF(c, "k_panel_spmm_tc");  // variant 4 times its two kernels itself
   s = launch_tc(c, c->tc_pf, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R, c->stream);
   if (s != GM_OK) return s;
   GM_LAUNCH_CHECK(c);

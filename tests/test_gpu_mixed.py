@@ -19,7 +19,7 @@ def gm():
     return pkg
 
 
-@pytest.mark.parametrize("variant", ["1", "2", "3"])
+@pytest.mark.parametrize("variant", ["1", "2", "3", "4"])
 def test_mixed_form_within_the_equal_error_bar(gm, monkeypatch, variant):
     cat = catalogue_subset(make_catalogue("c2_plain_20k", truth="mean"), np.arange(2500))
     monkeypatch.setenv("GM_TC_PREFETCH", variant)

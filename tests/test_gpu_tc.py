@@ -24,11 +24,12 @@ def gm():
 def test_tensor_core_panel_product_matches_simt_and_fp64(gm, monkeypatch, probe):
     """The tensor-core FP32 errors against the FP64 path must be those of the
     CUDA-core FP32 kernel (same tolerance class), for every variant of the
-    tile product (gathers one or two steps ahead, warp-specialised ring)."""
+    tile product (gathers one or two steps ahead, warp-specialised ring, B
+    copied asynchronously from BF16 planes of PD)."""
     cat = catalogue_subset(make_catalogue("c2_plain_20k", truth="mean"), np.arange(2500))
     res = {}
     runs = [("fp64", gm.PREC_FP64, None, None), ("simt", gm.PREC_FP32, "simt", None)]
-    runs += [("tc%d" % v, gm.PREC_FP32, None, str(v)) for v in (1, 2, 3)]
+    runs += [("tc%d" % v, gm.PREC_FP32, None, str(v)) for v in (1, 2, 3, 4)]
     for name, prec, env, variant in runs:
         if env:
             monkeypatch.setenv("GM_SPMM", env)
@@ -51,8 +52,8 @@ def test_tensor_core_panel_product_matches_simt_and_fp64(gm, monkeypatch, probe)
     assert "k_panel_spmm_tiled" in res["simt"][2]
     mu64, v64 = res["fp64"][0], res["fp64"][1]
     err = {k: (np.abs(res[k][0] - mu64).max(), np.max(np.abs(res[k][1] - v64) / v64))
-           for k in ("tc1", "tc2", "tc3", "simt")}
-    for v in ("tc1", "tc2", "tc3"):
+           for k in ("tc1", "tc2", "tc3", "tc4", "simt")}
+    for v in ("tc1", "tc2", "tc3", "tc4"):
         assert "k_panel_spmm_tc" in res[v][2] and "k_panel_spmm_tiled" not in res[v][2]
         print("FP32 vs FP64 after 3 sweeps (mean, var rel): tensor cores (%s) %.2e %.2e, "
               "CUDA cores %.2e %.2e" % ((v,) + err[v] + err["simt"]))
@@ -62,3 +63,8 @@ def test_tensor_core_panel_product_matches_simt_and_fp64(gm, monkeypatch, probe)
     # the variants compute the same products in the same order: equal results
     for v in ("tc2", "tc3"):
         assert np.array_equal(res[v][0], res["tc1"][0]) and np.array_equal(res[v][1], res["tc1"][1])
+    # the same BF16 pieces with B read MN-major: equal up to the tensor core's
+    # internal summation order
+    assert "k_split3_planes" in res["tc4"][2]
+    np.testing.assert_allclose(res["tc4"][0], res["tc1"][0], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(res["tc4"][1], res["tc1"][1], rtol=1e-5, atol=0)

@@ -95,6 +95,21 @@ def test_jacobian_matches_closed_form_derivatives():
     np.testing.assert_allclose(J, want, rtol=1e-7, atol=1e-9)
 
 
+def test_jacobian_is_the_derivative_of_the_prior_mean():
+    """Off the anticentre, disc and bump together: against central
+    differences of m in ln theta."""
+    u = O.unit_vectors(np.radians([176.0, 183.0, 185.5]), np.radians([0.04, -0.02, 0.01]))
+    s = np.array([600.0, 2100.0, 4600.0])
+    J = Lr.jacobian(u, s, THETA, np.zeros(3))
+    phi = np.log(THETA)
+    for k in range(5):
+        e = np.zeros(5)
+        e[k] = 1e-5
+        fd = (Lr.prior_mean(u, s, np.exp(phi + e), np.zeros(3))
+              - Lr.prior_mean(u, s, np.exp(phi - e), np.zeros(3))) / 2e-5
+        np.testing.assert_allclose(J[:, k], fd, rtol=1e-6, atol=1e-10)
+
+
 def test_map_recovers_hyperparameters_of_model_draws():
     """Data drawn from the model itself, atil ~ N(m(theta), K + Sigma): over
     several draws the MAP lies within the Laplace errors of the truth (z
