@@ -923,22 +923,64 @@ __global__ void __launch_bounds__(kTaThreads, 2) k_panel_spmm_tc_async(
             "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
           : "r"(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cl));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      // the panel width is a multiple of 32: a 16-column chunk is all in or out
+      float pq[16];
+      if (vrow && c0 + cl < W) {
+        const int64_t at = base + row * W + c0 + cl;  // 16-byte aligned
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int cg = c0 + cl + k;
-        float pq = 0.f;
-        if (vrow && cg < W) {
-          const int64_t at = base + row * W + cg;
-          const float pv = P[at];
-          const float qv = pv + dr * __uint_as_float(u[k]);
-          Q[at] = qv;
-          pq = pv * qv;
+        for (int v = 0; v < 4; ++v) {
+          const float4 p4 = *reinterpret_cast<const float4*>(P + at + 4 * v);
+          float4 q4;
+          q4.x = p4.x + dr * __uint_as_float(u[4 * v + 0]);
+          q4.y = p4.y + dr * __uint_as_float(u[4 * v + 1]);
+          q4.z = p4.z + dr * __uint_as_float(u[4 * v + 2]);
+          q4.w = p4.w + dr * __uint_as_float(u[4 * v + 3]);
+          *reinterpret_cast<float4*>(Q + at + 4 * v) = q4;
+          pq[4 * v + 0] = p4.x * q4.x;
+          pq[4 * v + 1] = p4.y * q4.y;
+          pq[4 * v + 2] = p4.z * q4.z;
+          pq[4 * v + 3] = p4.w * q4.w;
         }
-        if (!packed) {  // uniform over the CTA; FP32 tree over the warp's 32 rows
+      } else {
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) pq += __shfl_xor_sync(0xffffffffu, pq, off);
-          if (lane == 0) sh_pq[warp * kTcCols + cl + k] = (double)pq;
+        for (int k = 0; k < 16; ++k) pq[k] = 0.f;
+      }
+      if (!packed) {  // uniform over the CTA
+        // column sums over the warp's 32 rows by a reduce-scatter of
+        // shuffles (16 instead of 80): each step halves the columns a lane
+        // holds; at the end lanes 2c' and 2c' + 1 hold the sum of column
+        // c' = bits 4..1 of the lane index (FP32 tree, fixed order)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const bool up = lane & 16;
+          const float send = up ? pq[j] : pq[j + 8];
+          const float keep = up ? pq[j + 8] : pq[j];
+          pq[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool up = lane & 8;
+          const float send = up ? pq[j] : pq[j + 4];
+          const float keep = up ? pq[j + 4] : pq[j];
+          pq[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const bool up = lane & 4;
+          const float send = up ? pq[j] : pq[j + 2];
+          const float keep = up ? pq[j + 2] : pq[j];
+          pq[j] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        {
+          const bool up = lane & 2;
+          const float send = up ? pq[0] : pq[1];
+          const float keep = up ? pq[1] : pq[0];
+          pq[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        }
+        pq[0] += __shfl_xor_sync(0xffffffffu, pq[0], 1);
+        const int colw = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                         ((lane >> 1) & 1);
+        if ((lane & 1) == 0) sh_pq[warp * kTcCols + cl + colw] = (double)pq[0];
       }
     }
   }
@@ -1157,17 +1199,23 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
   GM_CUDA_CHECK(c, cudaEventCreate(&a));
   GM_CUDA_CHECK(c, cudaEventCreate(&b));
   float best = 1e30f;
+  // two timed launches per variant, the faster kept: a single launch is
+  // cold (instruction cache, first touch of the planes) and misranks them
   for (int pf : {1, 2, 3, 4}) {
-    float ms = 0;
-    GM_CUDA_CHECK(c, cudaEventRecord(a, c->stream));
-    gm_status ls = launch_tc(c, pf, grid, n, R, dv, P, PD, Q, part_pq, pk, pd_elems, c->stream);
-    if (ls != GM_OK) return ls;
-    GM_CUDA_CHECK(c, cudaEventRecord(b, c->stream));
-    GM_CUDA_CHECK(c, cudaEventSynchronize(b));
-    GM_LAUNCH_CHECK(c);
-    GM_CUDA_CHECK(c, cudaEventElapsedTime(&ms, a, b));
-    if (ms < best) {
-      best = ms;
+    float fastest = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      float ms = 0;
+      GM_CUDA_CHECK(c, cudaEventRecord(a, c->stream));
+      gm_status ls = launch_tc(c, pf, grid, n, R, dv, P, PD, Q, part_pq, pk, pd_elems, c->stream);
+      if (ls != GM_OK) return ls;
+      GM_CUDA_CHECK(c, cudaEventRecord(b, c->stream));
+      GM_CUDA_CHECK(c, cudaEventSynchronize(b));
+      GM_LAUNCH_CHECK(c);
+      GM_CUDA_CHECK(c, cudaEventElapsedTime(&ms, a, b));
+      fastest = std::min(fastest, ms);
+    }
+    if (fastest < best) {
+      best = fastest;
       c->tc_pf = pf;
     }
   }
