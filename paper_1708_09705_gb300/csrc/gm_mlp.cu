@@ -457,6 +457,54 @@ __global__ void k_mlp_sample(int64_t n, uint64_t seed, double s_min, double s_ma
   }
 }
 
+// Training pairs drawn from the catalogue's own neighbour pairs: the CSR of
+// nq query stars (their s, u in qs, qux, ...) against all stars; pair p is
+// entry e = uniform in [0, qnnz) (self pairs, at zero separation, are always
+// computed by the quadrature and are redrawn).
+__global__ void k_mlp_sample_cat(int64_t n, uint64_t seed, int64_t nq, int64_t qnnz,
+                                 const int64_t* __restrict__ qptr, const int32_t* __restrict__ qcol,
+                                 const double* __restrict__ qs, const double* __restrict__ qux,
+                                 const double* __restrict__ quy, const double* __restrict__ quz,
+                                 const double* __restrict__ s, const double* __restrict__ ux,
+                                 const double* __restrict__ uy, const double* __restrict__ uz,
+                                 double* __restrict__ si, double* __restrict__ sj,
+                                 double* __restrict__ chord) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    double a = 0, b = 0, ch = 0;
+    for (int tries = 0; tries < 8; ++tries) {
+      const int64_t e = (int64_t)(splitmix64(seed ^ splitmix64(p * 16 + tries)) % (uint64_t)qnnz);
+      int64_t lo = 0, hi = nq;  // row of entry e
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (qptr[mid] <= e) lo = mid; else hi = mid;
+      }
+      const int32_t j = qcol[e];
+      const double dx = qux[lo] - ux[j], dy = quy[lo] - uy[j], dz = quz[lo] - uz[j];
+      a = qs[lo];
+      b = s[j];
+      ch = sqrt(fma(dx, dx, fma(dy, dy, dz * dz)));
+      if (ch > 0.0 || a != b) break;
+    }
+    si[p] = a;
+    sj[p] = b;
+    chord[p] = ch;
+  }
+}
+
+__global__ void k_gather_rows(int64_t nq, int64_t n, const double* __restrict__ s,
+                              const double* __restrict__ ux, const double* __restrict__ uy,
+                              const double* __restrict__ uz, double* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nq;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = (k * n) / nq;  // evenly spread over the spatially sorted stars
+    out[k] = s[i];
+    out[nq + k] = ux[i];
+    out[2 * nq + k] = uy[i];
+    out[3 * nq + k] = uz[i];
+  }
+}
+
 __global__ void k_mlp_features(int64_t n, const double* __restrict__ si,
                                const double* __restrict__ sj, const double* __restrict__ chord,
                                const double* __restrict__ K, double sigma2, double L0,
@@ -770,9 +818,38 @@ extern "C" gm_status gm_surrogate_train(gm_ctx* c, int64_t n_pairs, int32_t step
   GM_CUDA_CHECK(c, cudaStreamSynchronize(s));
   const double s_min = mm[0] * 0.9, s_max = mm[1] * 1.1;
   const int gb = 8 * sm_count(c);
-  GM_PROF(c, "k_mlp_sample");
-  k_mlp_sample<<<gb, 256, 0, s>>>(n + nv, seed, s_min, s_max, c->cfg.cutoff_pc, si, sj, ch);
-  GM_LAUNCH_CHECK(c);
+  // pairs like those the surrogate will serve: drawn from the neighbour pairs
+  // of up to 16,384 stars spread over the catalogue; synthetic geometry only
+  // if the catalogue has too few pairs
+  {
+    const int64_t nq = std::min<int64_t>(c->n, 16384);
+    double* qbuf = (double*)dev_alloc(c, (size_t)4 * nq * sizeof(double));
+    int64_t* qptr = (int64_t*)dev_alloc(c, (size_t)(nq + 1) * sizeof(int64_t));
+    if (!qbuf || !qptr) return set_error(c, GM_E_NOMEM, "training pair queries");
+    GM_PROF(c, "k_gather_rows");
+    k_gather_rows<<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nq, 256), 8 * sm_count(c))),
+                    256, 0, s>>>(nq, c->n, c->s, c->ux, c->uy, c->uz, qbuf);
+    GM_LAUNCH_CHECK(c);
+    Buffer qcol;
+    int64_t qnnz = 0;
+    st = neighbour_csr(c, nq, qbuf, qbuf + nq, qbuf + 2 * nq, qbuf + 3 * nq, nullptr, false, qptr,
+                       qcol, &qnnz, nullptr);
+    if (st != GM_OK) return st;
+    if (qnnz >= 4 * nq && qnnz >= 1024) {
+      GM_PROF(c, "k_mlp_sample_cat");
+      k_mlp_sample_cat<<<gb, 256, 0, s>>>(n + nv, seed, nq, qnnz, qptr, (const int32_t*)qcol.p,
+                                          qbuf, qbuf + nq, qbuf + 2 * nq, qbuf + 3 * nq, c->s,
+                                          c->ux, c->uy, c->uz, si, sj, ch);
+    } else {
+      GM_PROF(c, "k_mlp_sample");
+      k_mlp_sample<<<gb, 256, 0, s>>>(n + nv, seed, s_min, s_max, c->cfg.cutoff_pc, si, sj, ch);
+    }
+    GM_LAUNCH_CHECK(c);
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(s));
+    if (qcol.p) dev_free_now(c, qcol.p, qcol.bytes);
+    dev_free_now(c, qptr, (size_t)(nq + 1) * sizeof(int64_t));
+    dev_free_now(c, qbuf, (size_t)4 * nq * sizeof(double));
+  }
   st = pairlist_quadrature(c, n + nv, si, sj, ch, K);
   if (st != GM_OK) return st;
   GM_PROF(c, "k_mlp_features");
