@@ -451,6 +451,29 @@ gm_status gm_surrogate_eval(gm_ctx* ctx, int64_t n, const double* si, const doub
                             const double* chord, double sigma2, double L0, float* y_out,
                             float* e_out);
 
+/* Streamed assembly of a block of covariance rows: for a catalogue whose
+ * sparse covariance does not fit in device memory (a million stars within
+ * the cutoff of each other by the ten thousand: ~3.7e10 entries), rows are
+ * assembled block by block and handed to the caller.  Rows row0 .. row0 +
+ * nrows - 1 in the context's internal order (gm_get_perm maps internal to
+ * caller indices); each row lists every star within the cutoff (the row's
+ * own star included), columns as internal indices in increasing order,
+ * values the covariance entries of Sect. 3 with the taper, computed as
+ * gm_build_cov would (source GM_COV_QUADRATURE: the context's node rule;
+ * GM_COV_SURROGATE: the trained network, with the node rule where the
+ * estimated error exceeds the gate and on the diagonal).  No gm_build_cov is
+ * needed; one-field contexts only (GM_E_STATE).
+ *   capacity     : entries col_out / val_out can hold; if the block has more,
+ *                  GM_E_INVAL with *nnz_out set (call again with room)
+ *   row_ptr_out  : nrows + 1 offsets (int64), from 0
+ *   col_out      : int32 columns; val_out: float (FP32 contexts) or double
+ *   nnz_out      : entries of the block; fallback_out (may be NULL): entries
+ *                  recomputed by the node rule (diagonal included)
+ * Host or device pointers. */
+gm_status gm_cov_rows(gm_ctx* ctx, int64_t row0, int64_t nrows, int32_t source,
+                      int64_t capacity, int64_t* row_ptr_out, int32_t* col_out, void* val_out,
+                      int64_t* nnz_out, int64_t* fallback_out);
+
 /* Allocation-free EP site update.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory while they run --
  * frameworks that own every device allocation through their own pool,

@@ -146,6 +146,7 @@ struct gm_ctx {
   // ---- covariance surrogate (FP32 parameters, BF16 operand images)
   float* mlp_params = nullptr;
   unsigned char* mlp_img = nullptr;
+  unsigned char* mlp_bimg = nullptr;  // transposed weight images of the backward pass
   bool mlp_trained = false;   // parameters set (by training or by the caller)
 
   // ---- EP state

@@ -47,6 +47,10 @@ constexpr int kSW4 = 16 * 64 * 2;    // B of layer 4: 16 rows x 64
 constexpr int kSA1 = 128 * 16 * 2;   // A of layer 1
 constexpr int kSA = 128 * 64 * 2;    // A of layers 2-4
 constexpr int kSWimg = kSW1 + 2 * kSW + kSW4;  // one piece of all weight images (20 KB)
+// training: transposed weight images of the backward pass, and the dOut image
+constexpr int kSWb4 = 64 * 16 * 2, kSWb = 64 * 64 * 2;
+constexpr int kSWbimg = kSWb4 + 2 * kSWb;  // 18 KB per piece
+constexpr int kSD = 128 * 16 * 2;          // dOut image (128 samples x 16)
 
 // byte offset of element (row, k) in a K-major no-swizzle image with K_total
 // columns: core matrices of 8 rows x 8 elements (16 B rows), k-adjacent
@@ -351,7 +355,9 @@ gm_status mlp_ensure(gm_ctx* c) {
   if (c->mlp_params) return GM_OK;
   c->mlp_params = (float*)dev_alloc(c, kMlpParams * sizeof(float));
   c->mlp_img = (unsigned char*)dev_alloc(c, 2 * kSWimg);
-  if (!c->mlp_params || !c->mlp_img) return set_error(c, GM_E_NOMEM, "surrogate weights");
+  c->mlp_bimg = (unsigned char*)dev_alloc(c, 2 * kSWbimg);
+  if (!c->mlp_params || !c->mlp_img || !c->mlp_bimg)
+    return set_error(c, GM_E_NOMEM, "surrogate weights");
   return GM_OK;
 }
 }  // namespace gm
@@ -697,6 +703,334 @@ __global__ void k_minmax_s(int64_t n, const double* __restrict__ s, double* __re
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Training on the tensor cores: one CTA per batch tile of 128 samples.
+// Forward as in k_mlp_forward (the pre-activations Z1..Z3 stay in tensor
+// memory); backward dH_l = dZ_{l+1} W_{l+1}^T as M = 128 (samples) products
+// with the transposed weight images of k_mlp_pack_bwd; weight gradients
+// dW_l = H_{l-1}^T dZ_l as products over the 128 samples, reading the same
+// activation images as MN-major operands (M = the layer's inputs, zero-
+// padded rows of the M = 128 product are not read back); bias gradients are
+// column sums of dZ_l (FP32 shuffle reduce-scatter, then per warp in smem).
+// Every operand is held as two BF16 pieces (three MMAs per step, as in the
+// forward).  The tile's gradient goes to its own partial row; a second kernel
+// sums the rows in a fixed order.
+// Backward weight images (B operands, K-major, two pieces each):
+//   W4b: rows n = hidden (64), k = outputs (16, 2 used): element W4[n][k]
+//   W3b, W2b: rows n = layer input (64), k = layer output (64): W[n][k]
+
+__global__ void k_mlp_pack_bwd(const float* __restrict__ params, unsigned char* __restrict__ img) {
+  for (int idx = threadIdx.x + blockIdx.x * blockDim.x; idx < 64 * 64; idx += blockDim.x * gridDim.x) {
+    const int n = idx / 64, k = idx % 64;
+    auto put = [&](int off, float v) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16*>(img + off) = h;
+      *reinterpret_cast<__nv_bfloat16*>(img + kSWbimg + off) =
+          __float2bfloat16_rn(v - __bfloat162float(h));
+    };
+    if (k < 16) put(kmaj_off(n, k, 16), k < kMlpOut ? params[kW4 + n * kMlpOut + k] : 0.f);
+    put(kSWb4 + kmaj_off(n, k, 64), params[kW3 + n * kMlpHid + k]);
+    put(kSWb4 + kSWb + kmaj_off(n, k, 64), params[kW2 + n * kMlpHid + k]);
+  }
+}
+
+// three-MMA product of two-piece operands: lo x hi, hi x lo, hi x hi
+__device__ __forceinline__ void mma3(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh,
+                                     uint64_t bl, uint32_t idesc, uint32_t acc) {
+  mma_bf16(d, al, bh, idesc, acc);
+  mma_bf16(d, ah, bl, idesc, 1u);
+  mma_bf16(d, ah, bh, idesc, 1u);
+}
+
+constexpr size_t kTrainSmem = 2 * kSWimg + 2 * kSWbimg + 2 * kSA1 + 3 * 2 * kSA + 2 * kSD +
+                              (256 + 4 * 200) * sizeof(float);
+
+__global__ void __launch_bounds__(128) k_mlp_train_tc(
+    int64_t n_data, int B, int direct, uint64_t seed, uint64_t step, const float* __restrict__ X,
+    const float* __restrict__ Y, const float* __restrict__ params,
+    const unsigned char* __restrict__ wimg, const unsigned char* __restrict__ wbimg, float lam,
+    float* __restrict__ grad_part, double* __restrict__ loss_part, unsigned* __restrict__ flags) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sWf = smem;                         // forward weights, hi then lo
+  unsigned char* sWb = sWf + 2 * kSWimg;             // backward weights, hi then lo
+  unsigned char* sX = sWb + 2 * kSWbimg;             // X (hi, lo)
+  unsigned char* sH1 = sX + 2 * kSA1;                // H1 then dZ1 (hi, lo)
+  unsigned char* sH2 = sH1 + 2 * kSA;                // H2 then dZ2
+  unsigned char* sH3 = sH2 + 2 * kSA;                // H3 then dZ3
+  unsigned char* sD = sH3 + 2 * kSA;                 // dOut (hi, lo)
+  float* sBias = reinterpret_cast<float*>(sD + 2 * kSD);  // 194
+  float* sDb = sBias + 256;                          // [4 warps][194] bias-gradient partials
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ double sh_loss[2][4];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int k = tid; k < 2 * kSWimg / 16; k += blockDim.x)
+    reinterpret_cast<uint4*>(sWf)[k] = reinterpret_cast<const uint4*>(wimg)[k];
+  for (int k = tid; k < 2 * kSWbimg / 16; k += blockDim.x)
+    reinterpret_cast<uint4*>(sWb)[k] = reinterpret_cast<const uint4*>(wbimg)[k];
+  for (int k = tid; k < kMlpHid; k += blockDim.x) {
+    sBias[k] = params[kB1 + k];
+    sBias[64 + k] = params[kB2 + k];
+    sBias[128 + k] = params[kB3 + k];
+  }
+  if (tid < kMlpOut) sBias[192 + tid] = params[kB4 + tid];
+  for (int k = tid; k < 4 * 200; k += blockDim.x) sDb[k] = 0.f;
+  if (tid == 0) {
+    abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // the sample of this thread (row tid of the tile)
+  const int sidx = blockIdx.x * 128 + tid;
+  const bool live = sidx < B;
+  const int64_t p = !live ? 0
+                  : direct ? (int64_t)sidx
+                           : (int64_t)(splitmix64(seed ^ splitmix64(step * 1000003ull + sidx)) %
+                                       (uint64_t)n_data);
+  {
+    float f[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) f[k] = 0.f;
+    if (live)
+      for (int k = 0; k < kMlpIn; ++k) f[k] = X[p * kMlpIn + k];
+#pragma unroll
+    for (int g = 0; g < 2; ++g) store8_split(sX, kSA1, kmaj_off(tid, 8 * g, 16), f + 8 * g);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  constexpr uint32_t cZ1 = 0, cZ2 = 64, cZ3 = 128, cOut = 192, cDH = 208, cW1 = 272, cW2 = 336,
+                     cW3 = 400, cW4 = 464;
+  const uint32_t mb = smem_u32(&mbar);
+  uint32_t phase = 0;
+  // MMAs issued by thread 0, then all threads wait; smem written by the
+  // threads before is published to the tensor core first
+  auto run = [&](auto&& issue) -> bool {
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      issue();
+      mma_commit(mb);
+    }
+    const bool ok = mbar_wait(mb, phase);
+    phase ^= 1;
+    if (!ok) abort_flag = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    return !abort_flag;
+  };
+  const uint32_t id64 = idesc_bf16(128, 64), id16 = idesc_bf16(128, 16);
+  const uint32_t idT64 = id64 | (1u << 15) | (1u << 16), idT16 = id16 | (1u << 15) | (1u << 16);
+  const uint32_t aX = smem_u32(sX), aH1 = smem_u32(sH1), aH2 = smem_u32(sH2), aH3 = smem_u32(sH3),
+                 aD = smem_u32(sD), aWf = smem_u32(sWf), aWb = smem_u32(sWb);
+  // K-major operand of K = 64 (activation rows or weights), K-step s
+  auto km64 = [](uint32_t a, int s) { return mdesc(a + 256 * s, 128, 1024); };
+  // the same activation image as an MN-major operand over the samples:
+  // K-step s of 16 samples, 8-column chunks 128 B apart, 8-sample groups 1 KB apart
+  auto mn64 = [](uint32_t a, int s) { return mdesc(a + 2048 * s, 1024, 128); };
+  auto mn16 = [](uint32_t a, int s) { return mdesc(a + 512 * s, 256, 128); };
+  bool ok = true;
+  float z[64];
+  // ---- forward
+  ok = ok && run([&] {
+    mma3(tmem + cZ1, mdesc(aX, 128, 256), mdesc(aX + kSA1, 128, 256), mdesc(aWf, 128, 256),
+         mdesc(aWf + kSWimg, 128, 256), id64, 0u);
+  });
+  const uint32_t wf[3] = {aWf + kSW1, aWf + kSW1 + kSW, aWf + kSW1 + 2 * kSW};  // W2, W3, W4
+  unsigned char* sH[3] = {sH1, sH2, sH3};
+  const uint32_t aH[3] = {aH1, aH2, aH3};
+  for (int layer = 0; layer < 3 && ok; ++layer) {
+    // H_layer = silu(Z_layer + b) into its image, then Z_{layer+1}
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tmem_ld16(tmem + lane_off + 64 * layer + 16 * q, z + 16 * q);
+#pragma unroll
+    for (int k = 0; k < 64; ++k) z[k] = silu_f(z[k] + sBias[64 * layer + k]);
+    store_row64(sH[layer], tid, z);
+    const uint32_t dcol = layer < 2 ? 64 * (layer + 1) : cOut;
+    const uint32_t idd = layer < 2 ? id64 : id16;
+    const uint32_t aa = aH[layer], ww = wf[layer];
+    ok = run([&] {
+      for (int s = 0; s < 4; ++s)
+        mma3(tmem + dcol, km64(aa, s), km64(aa + kSA, s), km64(ww, s), km64(ww + kSWimg, s), idd,
+             s > 0 ? 1u : 0u);
+    });
+  }
+  // ---- loss and dOut
+  double l1 = 0, l2 = 0;
+  if (ok) {
+    float o[16];
+    tmem_ld16(tmem + lane_off + cOut, o);
+    float d[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) d[k] = 0.f;
+    if (live) {
+      const float out0 = o[0] + sBias[192], out1 = o[1] + sBias[193];
+      const float r = out0 - Y[p];
+      const float et = logf(fabsf(r) + 1e-5f);
+      const float u = et - out1;
+      const float wq = u > 0.f ? kErrQuantile : kErrQuantile - 1.f;
+      l1 = (double)r * r;
+      l2 = (double)(u * wq);
+      d[0] = 2.0f * r / (float)B;
+      d[1] = -lam * wq / (float)B;
+    }
+#pragma unroll
+    for (int g = 0; g < 2; ++g) store8_split(sD, kSD, kmaj_off(tid, 8 * g, 16), d + 8 * g);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {  // output bias gradients
+      float v = d[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) sDb[warp * 200 + 192 + k] = v;
+    }
+  }
+  // ---- backward: dH3 = dOut W4^T and dW4 = H3^T dOut
+  ok = ok && run([&] {
+    mma3(tmem + cDH, mdesc(aD, 128, 256), mdesc(aD + kSD, 128, 256), mdesc(aWb, 128, 256),
+         mdesc(aWb + kSWbimg, 128, 256), id64, 0u);
+    for (int s = 0; s < 8; ++s)
+      mma3(tmem + cW4, mn64(aH3, s), mn64(aH3 + kSA, s), mn16(aD, s), mn16(aD + kSD, s), idT16,
+           s > 0 ? 1u : 0u);
+  });
+  // dZ_l = dH_l o silu'(Z_l + b_l) over the activation image of H_l, then
+  // dH_{l-1} = dZ_l W_l^T and dW_l = H_{l-1}^T dZ_l
+  const uint32_t wb[2] = {aWb + kSWb4, aWb + kSWb4 + kSWb};  // W3b, W2b
+  const uint32_t cW[3] = {cW1, cW2, cW3};
+  for (int layer = 2; layer >= 0 && ok; --layer) {
+    float dh[64];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tmem_ld16(tmem + lane_off + cDH + 16 * q, dh + 16 * q);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tmem_ld16(tmem + lane_off + 64 * layer + 16 * q, z + 16 * q);
+#pragma unroll
+    for (int k = 0; k < 64; ++k) dh[k] *= dsilu_f(z[k] + sBias[64 * layer + k]);
+    store_row64(sH[layer], tid, dh);
+    // bias gradients: column sums over the warp's rows (reduce-scatter of 16
+    // columns at a time), accumulated per warp
+#pragma unroll
+    for (int c16 = 0; c16 < 4; ++c16) {
+      float v[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = dh[16 * c16 + k];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const bool up = lane & 16;
+        const float send = up ? v[j] : v[j + 8];
+        v[j] = (up ? v[j + 8] : v[j]) + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool up = lane & 8;
+        const float send = up ? v[j] : v[j + 4];
+        v[j] = (up ? v[j + 4] : v[j]) + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const bool up = lane & 4;
+        const float send = up ? v[j] : v[j + 2];
+        v[j] = (up ? v[j + 2] : v[j]) + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      {
+        const bool up = lane & 2;
+        const float send = up ? v[0] : v[1];
+        v[0] = (up ? v[1] : v[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
+      }
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+      const int colw = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                       ((lane >> 1) & 1);
+      if ((lane & 1) == 0) sDb[warp * 200 + 64 * layer + 16 * c16 + colw] = v[0];
+    }
+    const uint32_t az = aH[layer];  // now dZ_layer
+    const uint32_t ain = layer > 0 ? aH[layer - 1] : aX;
+    const uint32_t cw = cW[layer];
+    const int lyr = layer;
+    ok = run([&] {
+      if (lyr > 0) {  // dH_{layer-1} = dZ_layer W_layer^T
+        const uint32_t bw = wb[2 - lyr];
+        for (int s = 0; s < 4; ++s)
+          mma3(tmem + cDH, km64(az, s), km64(az + kSA, s), km64(bw, s), km64(bw + kSWbimg, s),
+               id64, s > 0 ? 1u : 0u);
+      }
+      for (int s = 0; s < 8; ++s) {  // dW_layer = H_{layer-1}^T dZ_layer
+        const uint64_t ah = lyr > 0 ? mn64(ain, s) : mn16(ain, s);
+        const uint64_t al = lyr > 0 ? mn64(ain + kSA, s) : mn16(ain + kSA1, s);
+        mma3(tmem + cw, ah, al, mn64(az, s), mn64(az + kSA, s), idT64, s > 0 ? 1u : 0u);
+      }
+    });
+  }
+  // ---- this tile's gradient row: dW from tensor memory (rows = the layer's
+  // inputs: warps 0-1 hold rows 0-63), biases from the warp partials
+  float* gp = grad_part + (int64_t)blockIdx.x * kMlpParams;
+  if (ok) {
+    if (warp < 2) {
+      const int k = tid;  // layer input index
+      float v[64];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tmem_ld16(tmem + lane_off + cW2 + 16 * q, v + 16 * q);
+      for (int n = 0; n < 64; ++n) gp[kW2 + k * kMlpHid + n] = v[n];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tmem_ld16(tmem + lane_off + cW3 + 16 * q, v + 16 * q);
+      for (int n = 0; n < 64; ++n) gp[kW3 + k * kMlpHid + n] = v[n];
+      tmem_ld16(tmem + lane_off + cW4, v);
+      for (int n = 0; n < kMlpOut; ++n) gp[kW4 + k * kMlpOut + n] = v[n];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) tmem_ld16(tmem + lane_off + cW1 + 16 * q, v + 16 * q);
+      if (k < kMlpIn)
+        for (int n = 0; n < 64; ++n) gp[kW1 + k * kMlpHid + n] = v[n];
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+    l2 += __shfl_xor_sync(0xffffffffu, l2, off);
+  }
+  if (lane == 0) {
+    sh_loss[0][warp] = l1;
+    sh_loss[1][warp] = l2;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (ok) {
+    for (int k = tid; k < 194; k += blockDim.x) {
+      const float v = ((sDb[k] + sDb[200 + k]) + sDb[400 + k]) + sDb[600 + k];
+      const int at = k < 64 ? kB1 + k : k < 128 ? kB2 + k - 64 : k < 192 ? kB3 + k - 128
+                                                                        : kB4 + k - 192;
+      gp[at] = v;
+    }
+    if (tid == 0) {
+      loss_part[2 * blockIdx.x] = sh_loss[0][0] + sh_loss[0][1] + sh_loss[0][2] + sh_loss[0][3];
+      loss_part[2 * blockIdx.x + 1] = sh_loss[1][0] + sh_loss[1][1] + sh_loss[1][2] + sh_loss[1][3];
+    }
+  } else if (tid == 0) {
+    atomicOr(flags, kFlagTimeout);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// grad = sum over tiles of grad_part (fixed order)
+__global__ void k_mlp_grad_reduce(int tiles, const float* __restrict__ grad_part,
+                                  float* __restrict__ grad) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kMlpParams; k += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int t = 0; t < tiles; ++t) s += grad_part[(int64_t)t * kMlpParams + k];
+    grad[k] = s;
+  }
+}
+
 // One Adam-trained batch step: fwd/bwd, weight gradients, update.
 struct TrainBufs {
   float* save;
@@ -710,6 +1044,27 @@ static gm_status grad_step(gm_ctx* c, int64_t n_data, int B, uint64_t seed, uint
                            const float* X, const float* Y, float lam, TrainBufs& tb,
                            bool direct) {
   const int blocks = (B + 127) / 128;
+  const char* env = std::getenv("GM_MLP_TRAIN");
+  if (env && env[0] == 't') {
+    // tensor cores: one CTA per tile of 128 samples, then the fixed-order sum
+    GM_PROF(c, "k_mlp_pack");
+    k_mlp_pack<<<16, 256, 0, c->stream>>>(c->mlp_params, c->mlp_img);
+    GM_LAUNCH_CHECK(c);
+    GM_PROF(c, "k_mlp_pack_bwd");
+    k_mlp_pack_bwd<<<16, 256, 0, c->stream>>>(c->mlp_params, c->mlp_bimg);
+    GM_LAUNCH_CHECK(c);
+    cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTrainSmem);
+    GM_PROF(c, "k_mlp_train_tc");
+    k_mlp_train_tc<<<blocks, 128, kTrainSmem, c->stream>>>(
+        n_data, B, direct ? 1 : 0, seed, step, X, Y, c->mlp_params, c->mlp_img, c->mlp_bimg, lam,
+        tb.save, tb.loss_part, c->d_flags);
+    GM_LAUNCH_CHECK(c);
+    GM_PROF(c, "k_mlp_grad_reduce");
+    k_mlp_grad_reduce<<<(kMlpParams + 255) / 256, 256, 0, c->stream>>>(blocks, tb.save, tb.grad);
+    GM_LAUNCH_CHECK(c);
+    return GM_OK;
+  }
   const size_t smem = kMlpParams * sizeof(float);
   cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   GM_PROF(c, "k_mlp_fwd_bwd");
@@ -1132,3 +1487,186 @@ gm_status surrogate_values(gm_ctx* c) {
 }
 
 }  // namespace gm
+
+// ---------------------------------------------------------------------------
+// Streamed assembly of a block of rows (gm_cov_rows).  A catalogue whose
+// covariance does not fit in memory (the 1,000,000-star field: ~3.7e10
+// stored entries) is assembled block by block: the neighbour rows of stars
+// row0 .. row0 + nrows - 1 (internal order) against all stars, with values by
+// the quadrature or by the surrogate with the quadrature at the gate, as
+// gm_build_cov computes them (the taper applied; the diagonal always by the
+// quadrature).
+// ---------------------------------------------------------------------------
+namespace gm {
+
+__global__ void k_chunk_pairs(int64_t nrows, int64_t row0, const int64_t* __restrict__ qptr,
+                              const int32_t* __restrict__ qcol, const double* __restrict__ s,
+                              const double* __restrict__ ux, const double* __restrict__ uy,
+                              const double* __restrict__ uz, double* __restrict__ psi,
+                              double* __restrict__ psj, double* __restrict__ pch,
+                              double* __restrict__ pdist, int32_t* __restrict__ pdiag) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < nrows; r += nw) {
+    const int64_t i = row0 + r;
+    for (int64_t e = qptr[r] + lane; e < qptr[r + 1]; e += 32) {
+      const int32_t j = qcol[e];
+      const double dx = ux[i] - ux[j], dy = uy[i] - uy[j], dz = uz[i] - uz[j];
+      const double c2 = fma(dx, dx, fma(dy, dy, dz * dz));
+      const double ds = s[i] - s[j];
+      psi[e] = s[i];
+      psj[e] = s[j];
+      pch[e] = sqrt(c2);
+      pdist[e] = sqrt(fma(ds, ds, s[i] * s[j] * c2));
+      pdiag[e] = j == i;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_chunk_apply(int64_t np, const int32_t* __restrict__ pdiag,
+                              const double* __restrict__ pdist, const float* __restrict__ y,
+                              const float* __restrict__ e, double gate, double inv_cut, int taper,
+                              T* __restrict__ val, int64_t* __restrict__ flag) {
+  const double loggate = log(gate);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float yp = y[p], ep = e[p];
+    const double w = taper == GM_TAPER_WENDLAND ? taper_w(pdist[p] * inv_cut) : 1.0;
+    const bool fb = pdiag[p] || !isfinite(yp) || !isfinite(ep) ||
+                    !((double)yp + (double)ep + log(w) <= loggate);
+    flag[p] = fb ? 1 : 0;
+    if (!fb) val[p] = (T)(w * exp((double)yp));
+  }
+}
+
+template <typename T>
+__global__ void k_chunk_fallback(int64_t nf, const int64_t* __restrict__ fl,
+                                 const int32_t* __restrict__ pdiag,
+                                 const double* __restrict__ pdist, const double* __restrict__ K,
+                                 double inv_cut, int taper, T* __restrict__ val,
+                                 unsigned* __restrict__ flags) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nf;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = fl[q];
+    double Kv = K[q];
+    if (!isfinite(Kv)) atomicOr(flags, kFlagNonFinite);
+    if (!pdiag[p] && taper == GM_TAPER_WENDLAND) Kv *= taper_w(pdist[p] * inv_cut);
+    val[p] = (T)Kv;
+  }
+}
+
+template <typename T>
+static gm_status cov_rows_t(gm_ctx* c, int64_t row0, int64_t nrows, int32_t source,
+                            int64_t* rp_out, int32_t* col_out, void* val_out, int64_t cap,
+                            int64_t* nnz_out, int64_t* fallback_out) {
+  cudaStream_t st = c->stream;
+  const int sms = sm_count(c);
+  ScopedDev bqp(c, (size_t)(nrows + 1) * sizeof(int64_t));
+  int64_t* qptr = (int64_t*)bqp.p;
+  if (!qptr) return set_error(c, GM_E_NOMEM, "row-block pointers");
+  Buffer qcol;
+  int64_t nnz = 0;
+  gm_status s = neighbour_csr(c, nrows, c->s + row0, c->ux + row0, c->uy + row0, c->uz + row0,
+                              nullptr, false, qptr, qcol, &nnz, nullptr);
+  if (s != GM_OK) return s;
+  ScopedDev bqc(c, qcol.p, qcol.bytes, ScopedDev::Adopt{});
+  *nnz_out = nnz;
+  if (fallback_out) *fallback_out = 0;
+  if (nnz > cap) return set_error(c, GM_E_INVAL, "row block: more entries than the capacity");
+  ScopedDev bval(c, (size_t)std::max<int64_t>(nnz, 1) * sizeof(T));
+  T* val = (T*)bval.p;
+  if (!val) return set_error(c, GM_E_NOMEM, "row-block values");
+  if (source == GM_COV_QUADRATURE || nnz == 0) {
+    s = pair_quadrature(c, nrows, c->s + row0, c->ux + row0, c->uy + row0, c->uz + row0, nullptr,
+                        qptr, (const int32_t*)qcol.p, nnz, val, false);
+    if (s != GM_OK) return s;
+  } else {
+    // per entry: si, sj, chord, distance (double), diagonal (int32), y, e
+    // (float), flag, position (int64)
+    const size_t per = 4 * 8 + 4 + 2 * 4 + 2 * 8;
+    ScopedDev bp(c, (size_t)(nnz + 1) * per + 64);
+    if (!bp.p) return set_error(c, GM_E_NOMEM, "row-block pair list");
+    double* psi = (double*)bp.p;
+    double* psj = psi + (nnz + 1);
+    double* pch = psj + (nnz + 1);
+    double* pdist = pch + (nnz + 1);
+    int64_t* flag = (int64_t*)(pdist + (nnz + 1));
+    int64_t* pos = flag + (nnz + 1);
+    float* y = (float*)(pos + (nnz + 1));
+    float* e = y + (nnz + 1);
+    int32_t* pdiag = (int32_t*)(e + (nnz + 1));
+    const int wb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nrows * 32, 256), 16 * sms));
+    GM_PROF(c, "k_chunk_pairs");
+    k_chunk_pairs<<<wb, 256, 0, st>>>(nrows, row0, qptr, (const int32_t*)qcol.p, c->s, c->ux,
+                                      c->uy, c->uz, psi, psj, pch, pdist, pdiag);
+    GM_LAUNCH_CHECK(c);
+    MlpIn in{psi, psj, pch, nnz, c->cfg.sigma2, c->cfg.outer_scale_pc};
+    s = mlp_forward(c, in, y, e);
+    if (s != GM_OK) return s;
+    const int pb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nnz, 256), 16 * sms));
+    GM_PROF(c, "k_chunk_apply");
+    k_chunk_apply<T><<<pb, 256, 0, st>>>(nnz, pdiag, pdist, y, e, c->cfg.surrogate_gate,
+                                         1.0 / c->cfg.cutoff_pc, c->cfg.taper, val, flag);
+    GM_LAUNCH_CHECK(c);
+    s = scan_i64(c, flag, pos, nnz);
+    if (s != GM_OK) return s;
+    int64_t nf = 0;
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(&nf, pos + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+    ScopedDev bf(c, (size_t)(nf + 1) * (8 + 4 * 8));
+    if (!bf.p) return set_error(c, GM_E_NOMEM, "row-block fallback list");
+    int64_t* fl = (int64_t*)bf.p;
+    double* fsi = (double*)(fl + (nf + 1));
+    double* fsj = fsi + (nf + 1);
+    double* fch = fsj + (nf + 1);
+    double* fK = fch + (nf + 1);
+    GM_PROF(c, "k_fallback_gather");
+    k_fallback_gather<<<pb, 256, 0, st>>>(nnz, flag, pos, psi, psj, pch, fl, fsi, fsj, fch);
+    GM_LAUNCH_CHECK(c);
+    s = pairlist_quadrature(c, nf, fsi, fsj, fch, fK);
+    if (s != GM_OK) return s;
+    GM_PROF(c, "k_chunk_fallback");
+    k_chunk_fallback<T><<<(int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nf, 256), 16 * sms)),
+                          256, 0, st>>>(nf, fl, pdiag, pdist, fK, 1.0 / c->cfg.cutoff_pc,
+                                        c->cfg.taper, val, c->d_flags);
+    GM_LAUNCH_CHECK(c);
+    if (fallback_out) *fallback_out = nf;
+  }
+  // results to the caller (host or device)
+  GM_CUDA_CHECK(c, cudaMemcpyAsync(rp_out, qptr, (size_t)(nrows + 1) * sizeof(int64_t),
+                                   cudaMemcpyDefault, st));
+  if (nnz > 0) {
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(col_out, qcol.p, (size_t)nnz * sizeof(int32_t),
+                                     cudaMemcpyDefault, st));
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(val_out, val, (size_t)nnz * sizeof(T), cudaMemcpyDefault,
+                                     st));
+  }
+  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+  return GM_OK;
+}
+
+}  // namespace gm
+
+extern "C" gm_status gm_cov_rows(gm_ctx* c, int64_t row0, int64_t nrows, int32_t source,
+                                 int64_t capacity, int64_t* row_ptr_out, int32_t* col_out,
+                                 void* val_out, int64_t* nnz_out, int64_t* fallback_out) {
+  if (!c || row0 < 0 || nrows < 1 || row0 + nrows > c->n || capacity < 0 || !row_ptr_out ||
+      !nnz_out || (capacity > 0 && (!col_out || !val_out)))
+    return GM_E_INVAL;
+  if (source != GM_COV_QUADRATURE && source != GM_COV_SURROGATE) return GM_E_INVAL;
+  if (c->n_fields > 1) return set_error(c, GM_E_STATE, "row blocks need a single-field context");
+  if (source == GM_COV_SURROGATE && !c->mlp_trained)
+    return set_error(c, GM_E_STATE, "surrogate source selected but not trained");
+  c->launches = 0;
+  gm_status st = c->cfg.precision == GM_PREC_FP32
+                     ? cov_rows_t<float>(c, row0, nrows, source, row_ptr_out, col_out, val_out,
+                                         capacity, nnz_out, fallback_out)
+                     : cov_rows_t<double>(c, row0, nrows, source, row_ptr_out, col_out, val_out,
+                                          capacity, nnz_out, fallback_out);
+  if (st == GM_OK) st = read_flags(c);
+  prof_collect(c);
+  c->stats.kernel_launches = c->launches;
+  return st;
+}

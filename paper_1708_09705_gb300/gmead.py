@@ -38,7 +38,7 @@ EXPORTS = ["gm_config_default", "gm_ep_init", "gm_ep_init_fields", "gm_build_cov
            "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
            "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries", "gm_predict_pairs",
            "gm_predict_sightlines", "gm_monotone_sample", "gm_pic_posterior",
-           "gm_pic_predict", "gm_set_mean_fn", "gm_learn_mean"]
+           "gm_pic_predict", "gm_set_mean_fn", "gm_learn_mean", "gm_cov_rows"]
 
 
 class GmError(RuntimeError):
@@ -110,6 +110,8 @@ def lib():
         L.gm_pic_predict.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
         L.gm_get_csr.argtypes = [vp, vp, vp, vp]
         L.gm_set_mean_fn.argtypes = [vp, vp, dbl, dbl]
+        L.gm_cov_rows.argtypes = [vp, i64, i64, i32, i64, vp, vp, vp, C.POINTER(i64),
+                                  C.POINTER(i64)]
         L.gm_learn_mean.argtypes = [vp, vp, vp, vp, dbl, dbl, i32, dbl, vp, vp,
                                     C.POINTER(dbl), C.POINTER(i32)]
         L.gm_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -141,7 +143,7 @@ def lib():
                   "gm_get_stats", "gm_profile", "gm_kernel_time", "gm_surrogate_set_params",
                   "gm_surrogate_get_params", "gm_surrogate_eval", "gm_surrogate_train",
                   "gm_surrogate_grad", "gm_get_probe_colours", "gm_get_entries",
-                  "gm_predict_pairs", "gm_set_mean_fn", "gm_learn_mean"):
+                  "gm_predict_pairs", "gm_set_mean_fn", "gm_learn_mean", "gm_cov_rows"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -189,13 +191,26 @@ def _torch_allocator(device_index):
     return Allocator(fa, ff, None), (fa, ff)
 
 
+def _ptr_any(a):
+    """Raw address of a contiguous numpy array or torch tensor (no copy)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise TypeError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("array must be contiguous")
+    return a.ctypes.data
+
+
 class Context:
     """Owns one gm_ctx.  Created by ep_init."""
 
-    def __init__(self, handle, n, keep):
+    def __init__(self, handle, n, keep, cfg=None):
         self._h = handle
         self.n = int(n)
         self._keep = keep
+        self.precision = cfg.precision if cfg is not None else PREC_FP64
+        self.cfg_source = cfg.cov_source if cfg is not None else COV_QUADRATURE
 
     def _check(self, st):
         if st != 0:
@@ -313,6 +328,30 @@ class Context:
                                         float(tol), th.ctypes.data, cov.ctypes.data,
                                         C.byref(lp), C.byref(it)))
         return dict(theta=th, cov_phi=cov, log_post=lp.value, iters=it.value)
+
+    def cov_rows(self, row0, nrows, source=None, out=None):
+        """Covariance rows row0 .. row0 + nrows - 1 (internal order) assembled
+        without a stored matrix; returns (row_ptr, col, val, fallback).  out:
+        optional (col, val) arrays (numpy or torch, host or device) with room."""
+        src = self.cfg_source if source is None else source
+        rp = np.empty(nrows + 1, dtype=np.int64)
+        nnz, fb = C.c_int64(0), C.c_int64(0)
+        if out is None:
+            st = lib().gm_cov_rows(self._h, int(row0), int(nrows), int(src), 0, rp.ctypes.data,
+                                   None, None, C.byref(nnz), C.byref(fb))
+            if st not in (0, 1):
+                self._check(st)
+            vdt = np.float32 if self.precision == PREC_FP32 else np.float64
+            col = np.empty(max(nnz.value, 1), dtype=np.int32)
+            val = np.empty(max(nnz.value, 1), dtype=vdt)
+            cap = nnz.value
+        else:
+            col, val = out
+            cap = col.numel() if hasattr(col, "numel") else col.size
+        self._check(lib().gm_cov_rows(self._h, int(row0), int(nrows), int(src), int(cap),
+                                      rp.ctypes.data, _ptr_any(col), _ptr_any(val),
+                                      C.byref(nnz), C.byref(fb)))
+        return rp, col[:nnz.value], val[:nnz.value], fb.value
 
     # ---- state
     def _pair_out(self, fn, out):
@@ -490,7 +529,7 @@ def ep_init(cfg: Config, l, b, s, obs, obs_sigma, stream=None, torch_alloc=True,
                                  None if fL0 is None else fL0.ctypes.data,
                                  None if fct is None else fct.ctypes.data, C.c_void_p(sptr),
                                  alloc_ptr)
-    ctx = Context(h, n, keep)
+    ctx = Context(h, n, keep, cfg)
     if st != 0:
         msg = L.gm_last_error(h).decode() if h else STATUS.get(st, str(st))
         ctx.close()

@@ -79,8 +79,12 @@ def test_surrogate_forward_matches_cpu(gm, n):
         assert np.median(np.abs(one_piece[:, 0] - ref[:, 0])) > 3 * np.median(err_y)
 
 
-def test_surrogate_gradients_match_oracle(gm):
-    """FP32 backward kernels against the FP64 backpropagation of the oracle."""
+@pytest.mark.parametrize("kernel", ["tc", "simt"])
+def test_surrogate_gradients_match_oracle(gm, monkeypatch, kernel):
+    """The training gradients -- tensor-core forward/backward/weight-gradient
+    kernel (two-piece BF16 operands, FP32 accumulation) or the FP32 CUDA-core
+    kernels -- against the FP64 backpropagation of the oracle."""
+    monkeypatch.setenv("GM_MLP_TRAIN", kernel)
     from synth import catalogue_subset, make_catalogue
     cat = catalogue_subset(make_catalogue("c1_plain_400", truth="mean"), np.arange(4))
     rng = np.random.default_rng(11)
