@@ -300,7 +300,7 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
              ("mixed_probed_deflated", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
                                             probe_factor=2.0, deflate=64, tc_products=3)),
              ("learned_fp32", dict(precision=gm.PREC_FP32, cg_tol=1e-6,
-                                   cov_source=gm.COV_SURROGATE))]
+                                   cov_source=gm.COV_SURROGATE, surrogate_gate=3e-5))]
     for name, kw in forms:
         cfg = gm.config_from_catalogue(cat, **kw)
         with gm.ep_init(cfg, D["l"], D["b"], D["s"], D["A_obs"], D["A_sigma"]) as ctx:
@@ -341,8 +341,9 @@ def forms_comparison(gm, torch, dev, n_sub, sweeps):
             "notes": "plain = exact variances (one solve per star); probed = colour classes "
                      "2 cutoffs apart share a solve; mixed = the variance panels' tensor-core "
                      "product with three BF16 products per step (K1 PD1 + K1 PD2 + K2 PD1) "
-                     "instead of six; learned = surrogate K with quadrature fallback at the "
-                     "gate"}
+                     "instead of six; learned = surrogate K (trained on the catalogue's own "
+                     "neighbour pairs) with quadrature fallback where the estimated error of "
+                     "the stored entry exceeds 3e-5, the gate at which it meets the 1e-3 bar"}
 
 
 def run_fields(a):
