@@ -229,7 +229,13 @@ def run_reference(a):
 
 
 # ---------------------------------------------------------------- GPU arm
-def roofline_for(name, launches, ms, st, cfg_prec, panel):
+# DRAM bytes (read + write) of one launch of the asynchronous tile product on
+# the 20,000-star workload at panel 4,640, from one ncu capture of that launch
+# (dram__bytes_read.sum + dram__bytes_write.sum); other shapes were not captured
+TC_ASYNC_TRAFFIC = {(20000, 4640): 1.853e9 + 0.349e9}
+
+
+def roofline_for(name, launches, ms, st, cfg_prec, panel, async_b=False):
     """Algorithmic work of one launch of the dominant kernel / its mean time."""
     pk = peaks()
     avg_s = ms / launches / 1e3
@@ -255,8 +261,9 @@ def roofline_for(name, launches, ms, st, cfg_prec, panel):
         peak = bf / 6.0
         groups = math.ceil(panel / 256)
         exe = st.get("tile_ksteps", 0) * 6 * 2.0 * 128 * 16 * 256 * groups
+        traffic = TC_ASYNC_TRAFFIC.get((n, panel)) if async_b else None
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "kernel": name,
+                "frac": ach / peak, "traffic": traffic, "kernel": name,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured) / 6 "
                                "BF16 MMAs per FP32-grade product",
                 "work_per_launch": f"2 x nnz x panel = {flops:.3e} flop",
@@ -477,7 +484,9 @@ def run_gpu(a):
     # right-hand sides per product launch (the panel may hold fewer columns
     # than there are solves when memory caps it)
     panel = st.get("variance_panel_width") or cfg.rhs_panel or (math.ceil(cols / 32) * 32)
-    roof = roofline_for(dom[0], dom[1][0], dom[1][1], st, a.precision, panel)
+    # the asynchronous variant is the one that splits the panel into BF16 planes
+    roof = roofline_for(dom[0], dom[1][0], dom[1][1], st, a.precision, panel,
+                        async_b="k_split3_planes" in kt)
     launches = int(sum(v[0] for v in kt.values()))
     total_ms = sum(v[1] for v in kt.values())
 
