@@ -809,7 +809,8 @@ __global__ void __launch_bounds__(128) k_mlp_train_tc(
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-  constexpr uint32_t cZ1 = 0, cZ2 = 64, cZ3 = 128, cOut = 192, cDH = 208, cW1 = 272, cW2 = 336,
+  // tensor-memory columns: Z1, Z2, Z3 at 0, 64, 128 (64 * layer), then the rest
+  constexpr uint32_t cZ1 = 0, cOut = 192, cDH = 208, cW1 = 272, cW2 = 336,
                      cW3 = 400, cW4 = 464;
   const uint32_t mb = smem_u32(&mbar);
   uint32_t phase = 0;
@@ -1044,8 +1045,9 @@ static gm_status grad_step(gm_ctx* c, int64_t n_data, int B, uint64_t seed, uint
                            const float* X, const float* Y, float lam, TrainBufs& tb,
                            bool direct) {
   const int blocks = (B + 127) / 128;
+  // tensor cores unless GM_MLP_TRAIN=simt (the FP32 CUDA-core kernels below)
   const char* env = std::getenv("GM_MLP_TRAIN");
-  if (env && env[0] == 't') {
+  if (!(env && env[0] == 's')) {
     // tensor cores: one CTA per tile of 128 samples, then the fixed-order sum
     GM_PROF(c, "k_mlp_pack");
     k_mlp_pack<<<16, 256, 0, c->stream>>>(c->mlp_params, c->mlp_img);
