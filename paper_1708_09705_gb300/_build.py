@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["gm_api.cu", "gm_geometry.cu", "gm_quad.cu", "gm_solve.cu", "gm_site.cu",
-              "gm_tiles.cu", "gm_mlp.cu", "gm_fields.cu", "gm_probe.cu", "gm_tc.cu", "gm_deflate.cu",
+              "gm_tiles.cu", "gm_mlp.cu", "gm_fields.cu", "gm_probe.cu", "gm_tc.cu", "gm_deflate.cu", "gm_deflate_tc.cu",
               "gm_sightline.cu", "gm_pic.cu", "gm_learn.cu"]
 CPP_SOURCES = ["gm_rules.cpp"]
 

@@ -20,6 +20,7 @@
 // passes with FP64 Gram matrices), warm-started from the previous refresh,
 // followed by Rayleigh-Ritz (FP64 Jacobi eigen-solver on the host).
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -44,8 +45,10 @@ struct Deflation {
   Buffer Cp, C;                    // Y^T R: partials per row block, and the sum (k x R)
   Buffer wv;                       // k weights 1/theta - 1 (FP32)
   Buffer cpart1, c1;               // single right-hand side: Y^T r partials and sum
+  Buffer yimg, ywimg, cimg, Cp2;   // tensor-core form: images of Y^T, Yw, C^T; C partials
   std::vector<double> theta;       // Ritz values of this refresh
   bool ready = false;              // Y, Yw, wv valid for this refresh
+  bool tc = false;                 // ... and the images of Y^T and Yw
 };
 
 static Deflation& D(gm_ctx* c) {
@@ -388,35 +391,46 @@ __global__ void k_df1_update(int64_t n, const float* __restrict__ minv, const fl
   __shared__ float cs[kDefK];
   __shared__ float sh_beta;
   if (threadIdx.x < kDefK) cs[threadIdx.x] = cvec[threadIdx.x];
-  if (threadIdx.x == 0) {
-    float b = 0.f;
-    if (part) {
-      double rzp = 0.0, rzn = 0.0;
-      for (int k = 0; k < G; ++k) {
+  if (threadIdx.x < 32) {  // warp 0: the same fixed-order sums in every block
+    double rzp = 0.0, rzn = 0.0;
+    if (part)
+      for (int k = threadIdx.x; k < G; k += 32) {
         rzp += part[prev * G + k];
         rzn += part[next * G + k];
       }
-      b = rzp > 0 ? (float)(rzn / rzp) : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      rzp += __shfl_xor_sync(0xffffffffu, rzp, off);
+      rzn += __shfl_xor_sync(0xffffffffu, rzn, off);
     }
-    sh_beta = b;
+    if (threadIdx.x == 0) sh_beta = (part && rzp > 0) ? (float)(rzn / rzp) : 0.f;
   }
   __syncthreads();
   const float beta = sh_beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float4* y4 = reinterpret_cast<const float4*>(Yw + i * kDefK);
+  // eight lanes per row, eight of the row's 64 products each, summed by shuffles
+  // (a warp takes four rows per pass, so its shuffles never diverge)
+  const int l8 = threadIdx.x & 7, sub = (threadIdx.x & 31) >> 3;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = 4 * gw; base < n; base += 4 * nwarp) {
+    const int64_t i = base + sub;
+    const bool v = i < n;
     float z = 0.f;
-#pragma unroll
-    for (int q = 0; q < kDefK / 4; ++q) {
-      const float4 y = __ldg(y4 + q);
-      z = fmaf(y.x, cs[4 * q], z);
-      z = fmaf(y.y, cs[4 * q + 1], z);
-      z = fmaf(y.z, cs[4 * q + 2], z);
-      z = fmaf(y.w, cs[4 * q + 3], z);
+    if (v) {
+      const float4* y4 = reinterpret_cast<const float4*>(Yw + i * kDefK + 8 * l8);
+      const float4 a = __ldg(y4), b = __ldg(y4 + 1);
+      const float* c8 = cs + 8 * l8;
+      z = fmaf(a.x, c8[0], fmaf(a.y, c8[1], fmaf(a.z, c8[2], fmaf(a.w, c8[3],
+          fmaf(b.x, c8[4], fmaf(b.y, c8[5], fmaf(b.z, c8[6], b.w * c8[7])))))));
     }
-    const float pi = minv[i] * r[i] + z + beta * p[i];
-    p[i] = pi;
-    pd[i] = dv[i] * pi;
+    z += __shfl_xor_sync(0xffffffffu, z, 4);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    if (v && l8 == 0) {
+      const float pi = minv[i] * r[i] + z + beta * p[i];
+      p[i] = pi;
+      pd[i] = dv[i] * pi;
+    }
   }
 }
 
@@ -644,6 +658,17 @@ gm_status deflate_prepare(gm_ctx* c, const float* dv, const float* minv) {
   k_df_make_y<<<eg(c, n * kDefK), 256, 0, st>>>(n, ms, V, (const float*)F.wv.p, (float*)F.Y.p,
                                                 (float*)F.Yw.p);
   GM_LAUNCH_CHECK(c);
+  // tensor-core form of the panel step: BF16 pieces of Y^T and Yw
+  F.tc = false;
+  const char* e = std::getenv("GM_DEFLATE_TC");
+  if (c->tc_nblk > 0 && !(e && e[0] == '0')) {
+    if (!ensure(c, F.yimg, dtc_yimg_bytes(n)) || !ensure(c, F.ywimg, dtc_rowimg_bytes(n)))
+      return set_error(c, GM_E_NOMEM, "deflation images");
+    gm_status si = dtc_images(c, n, (const float*)F.Y.p, (const float*)F.Yw.p, F.yimg.p,
+                              F.ywimg.p);
+    if (si != GM_OK) return si;
+    F.tc = true;
+  }
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));  // w lives on this stack frame
   F.ready = true;
   return GM_OK;
@@ -687,6 +712,34 @@ gm_status deflate_update(gm_ctx* c, int R, int nbx, const float* minv, const flo
   return GM_OK;
 }
 
+bool deflate_tc(gm_ctx* c) { return c->defl && c->defl->ready && c->defl->tc; }
+
+int deflate_tc_chunks(gm_ctx* c, int R) { return dtc_chunks(c, c->n, R); }
+
+gm_status deflate_step_tc(gm_ctx* c, int R, int nch, const double* alpha, const float* minv,
+                          float* X, float* Rr, const float* P, const float* Q, double* part_rz,
+                          double* part_rr, double* corr8) {
+  Deflation& F = D(c);
+  if (!ensure(c, F.Cp2, (size_t)2 * nch * kDefK * R * sizeof(float)) ||
+      !ensure(c, F.cimg, dtc_cimg_bytes(R)))
+    return set_error(c, GM_E_NOMEM, "deflation projections");
+  return dtc_step(c, c->n, R, nch, F.yimg.p, alpha, minv, X, Rr, P, Q, part_rz, part_rr,
+                  (float*)F.Cp2.p, (const float*)F.wv.p, F.cimg.p, corr8);
+}
+
+gm_status deflate_update_tc(gm_ctx* c, int R, const float* minv, const float* dv,
+                            const double* beta, const int* active, const float* Rr, float* P,
+                            float* PD, bool planes) {
+  Deflation& F = D(c);
+  uint16_t* pl = nullptr;
+  if (planes) {
+    if (!ensure(c, c->tc_planes, (size_t)c->n * R * 3 * sizeof(uint16_t)))
+      return set_error(c, GM_E_NOMEM, "BF16 planes of the panel");
+    pl = (uint16_t*)c->tc_planes.p;
+  }
+  return dtc_update(c, c->n, R, F.ywimg.p, F.cimg.p, minv, dv, beta, active, Rr, P, PD, pl);
+}
+
 // Single right-hand side: c = Y^T r, add sum_j w_j c_j^2 to rz_slot[0]
 gm_status deflate1_rhs(gm_ctx* c, const float* r, double* rz_slot) {
   Deflation& F = D(c);
@@ -710,7 +763,7 @@ gm_status deflate1_update(gm_ctx* c, const float* minv, const float* dv, const d
                           int G, int prev, int next, const float* r, float* p, float* pd) {
   Deflation& F = D(c);
   GM_PROF(c, "k_df1_update");
-  k_df1_update<<<eg(c, c->n), 256, 0, c->stream>>>(c->n, minv, dv, (const float*)F.Yw.p,
+  k_df1_update<<<eg(c, 8 * c->n), 256, 0, c->stream>>>(c->n, minv, dv, (const float*)F.Yw.p,
                                                     (const float*)F.c1.p, part, G, prev, next,
                                                     r, p, pd);
   GM_LAUNCH_CHECK(c);

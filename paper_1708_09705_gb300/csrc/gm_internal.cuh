@@ -129,6 +129,8 @@ struct gm_ctx {
   gm::Buffer tc_planes;             // BF16 planes of the panel PD (async tile product)
   std::vector<int64_t> h_tc_boff;   // first tile block of each field (n_fields + 1)
   gm::Buffer tc_brow0, tc_boffd;    // first row of each block (+ end); device h_tc_boff
+  gm::Buffer tc_trow, tc_tpos;      // tile order: row at tile position p, position of row i
+  bool tc_order = false;            // tc_trow / tc_tpos in use (else position = row)
   int tc_pf = 0;                    // tuned prefetch depth of the tile product (0: untuned)
   double* kdiag = nullptr;
   double* prior_m = nullptr;
@@ -338,8 +340,10 @@ gm_status probe_colouring(gm_ctx* c);
 // 128-row tiles and the tensor-core panel product (gm_tc.cu).
 bool tc_wanted(gm_ctx* c);
 gm_status tc_tiles_build(gm_ctx* c);
+// planes_ready: c->tc_planes already hold the BF16 pieces of PD (written by
+// deflate_update_tc) for the asynchronous variant, which then skips its split.
 gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const float* P,
-                        const float* PD, float* Q, double* part_pq);
+                        const float* PD, float* Q, double* part_pq, bool planes_ready = false);
 // Packed multi-field panels (no partials); tune = choose the prefetch depth
 // (on the context stream, outside any graph capture) instead of launching.
 gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
@@ -367,6 +371,37 @@ gm_status deflate1_rhs(gm_ctx* c, const float* r, double* rz_slot);
 gm_status deflate1_update(gm_ctx* c, const float* minv, const float* dv, const double* part,
                           int G, int prev, int next, const float* r, float* p, float* pd);
 void deflate_free(gm_ctx* c);
+// Tensor-core form of the deflated panel CG step (FP32 panels with tensor-core
+// tiles; GM_DEFLATE_TC=0 keeps the CUDA-core kernels above).
+bool deflate_tc(gm_ctx* c);
+// row chunks of deflate_step_tc for a panel of R columns (its partial rows)
+int deflate_tc_chunks(gm_ctx* c, int R);
+// alpha non-null: X += alpha P, Rr -= alpha Q and the per-chunk partial sums
+// of r^T M^-1 r / r^T r (part_rz / part_rr, nch rows of R); alpha null: Rr
+// only.  Then C = Y^T Rr for deflate_update_tc and corr8 (8 rows of R) with
+// sum over rows = sum_j w_j C_jc^2.
+gm_status deflate_step_tc(gm_ctx* c, int R, int nch, const double* alpha, const float* minv,
+                          float* X, float* Rr, const float* P, const float* Q, double* part_rz,
+                          double* part_rr, double* corr8);
+// P = M^-1 Rr + Yw C + beta P on active columns (all, beta 0 when null); PD =
+// d o P in FP32, or (planes) its three BF16 pieces in c->tc_planes.
+gm_status deflate_update_tc(gm_ctx* c, int R, const float* minv, const float* dv,
+                            const double* beta, const int* active, const float* Rr, float* P,
+                            float* PD, bool planes);
+// kernels of the tensor-core form (gm_deflate_tc.cu)
+size_t dtc_yimg_bytes(int64_t n);
+size_t dtc_rowimg_bytes(int64_t n);
+size_t dtc_cimg_bytes(int R);
+gm_status dtc_images(gm_ctx* c, int64_t n, const float* Y, const float* Yw, void* yimg,
+                     void* ywimg);
+int dtc_chunks(gm_ctx* c, int64_t n, int R);
+gm_status dtc_step(gm_ctx* c, int64_t n, int R, int nch, const void* yimg, const double* alpha,
+                   const float* minv, float* X, float* Rr, const float* P, const float* Q,
+                   double* part_rz, double* part_rr, float* Cp, const float* w, void* cimg,
+                   double* corr8);
+gm_status dtc_update(gm_ctx* c, int64_t n, int R, const void* ywimg, const void* cimg,
+                     const float* minv, const float* dv, const double* beta, const int* active,
+                     const float* Rr, float* P, float* PD, uint16_t* planes);
 
 // Row-block tiles of K for the FP32 variance panels (gm_tiles.cu).
 gm_status tiles_build(gm_ctx* c);

@@ -406,6 +406,38 @@ __global__ void k_panel_rhs_probe(int64_t n, int64_t c0, int64_t n_cols, int R,
   }
 }
 
+// The same with a warp per row j, for colourings at least 2 x cutoff apart:
+// two neighbours of j are then within 2 x cutoff of each other, so they have
+// distinct colours and every entry of the row is written once (the adds go to
+// zeroed entries and give the same bits as the loop above; an add is used
+// all the same, so that a collision at the rounding edge of the separation
+// test would still sum).  The lanes share the row's neighbour list.
+template <typename TA, typename TV>
+__global__ void k_panel_rhs_probe_w(int64_t n, int64_t c0, int64_t n_cols, int R,
+                                    const int64_t* __restrict__ row_ptr,
+                                    const int32_t* __restrict__ col, const TA* __restrict__ val,
+                                    const TV* __restrict__ dv, const double* __restrict__ tau,
+                                    const double* __restrict__ kd,
+                                    const int32_t* __restrict__ pcol, TV* __restrict__ Rr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < n; j += nw) {
+    TV* row = Rr + j * R;
+    const TV dj = dv[j];
+    for (int64_t e = row_ptr[j] + lane; e < row_ptr[j + 1]; e += 32) {
+      const int32_t r = col[e];
+      const int64_t k = (int64_t)pcol[r] - c0;
+      if (k < 0 || k >= n_cols || unit_rhs(tau, kd, r)) continue;
+      atomicAdd(row + k, dj * (TV)val[e]);
+    }
+    if (lane == 0) {
+      const int64_t kj = (int64_t)pcol[j] - c0;
+      if (kj >= 0 && kj < n_cols && unit_rhs(tau, kd, j)) atomicAdd(row + kj, (TV)1);
+    }
+  }
+}
+
 template <typename TV>
 __global__ void __launch_bounds__(kBT) k_panel_init(int64_t n, int R, const TV* __restrict__ minv,
                                                     const TV* __restrict__ dv,
@@ -549,17 +581,19 @@ __global__ void __launch_bounds__(kBT) k_panel_spmm(int64_t n, int R,
 // Per-column sums of partials.  scal layout (R each): 0 alpha, 1 beta,
 // 2 rz_prev, 3 rz_new, 4 bb, 5 rr.  mode 0: after init (rz_prev, bb);
 // mode 1: after spmm (alpha); mode 2: after update1 (beta, activity).
+// corr: ncorr more rows added to the pa sums (the deflation term of r^T z).
 __global__ void k_panel_reduce(int mode, int nbx, int R, int64_t n_cols, double tol2, int it,
                                int max_it, const double* __restrict__ pa,
-                               const double* __restrict__ pb, double* __restrict__ scal,
-                               int* __restrict__ active, int* __restrict__ n_active,
-                               unsigned* __restrict__ flags) {
+                               const double* __restrict__ pb, const double* __restrict__ corr,
+                               int ncorr, double* __restrict__ scal, int* __restrict__ active,
+                               int* __restrict__ n_active, unsigned* __restrict__ flags) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < R; c += gridDim.x * blockDim.x) {
     double a = 0, b = 0;
     for (int k = 0; k < nbx; ++k) {
       a += pa[(int64_t)k * R + c];
       if (pb) b += pb[(int64_t)k * R + c];
     }
+    for (int k = 0; k < ncorr; ++k) a += corr[(int64_t)k * R + c];
     double* alpha = scal;
     double* beta = scal + R;
     double* rzp = scal + 2 * R;
@@ -1016,12 +1050,13 @@ static gm_status posterior_mean(gm_ctx* c, int64_t* iters, double* resid) {
 // *nbx_used: rows of per-column partials written to pa (the reduction's nbx).
 template <typename TA, typename TV>
 static gm_status panel_product(gm_ctx* c, int64_t n, int64_t R, int nbx, dim3 grid, const TV* dv,
-                               const TV* P, const TV* PD, TV* Q, double* pa, int* nbx_used) {
+                               const TV* P, const TV* PD, TV* Q, double* pa, int* nbx_used,
+                               bool planes_ready = false) {
   *nbx_used = nbx;
   if (sizeof(TV) == 4 && c->tc_nblk > 0) {
     *nbx_used = (int)c->tc_nblk;
     return panel_spmm_tc(c, n, (int)R, (const float*)dv, (const float*)P, (const float*)PD,
-                         (float*)Q, pa);
+                         (float*)Q, pa, planes_ready);
   }
   if (sizeof(TV) == 4 && c->t_nblk > 0)
     return panel_spmm_tiled(c, n, (int)R, nbx, (const float*)dv, (const float*)P,
@@ -1075,19 +1110,32 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   c->stats.variance_panel_width = R;
   const int nbx = std::max(1, (int)std::min<int64_t>(ceil_div(n, 8), (int64_t)(4 * sms * 32 / (R / 32 + 1)) + 1));
   const size_t pbytes = (size_t)n * R * sizeof(TV);
-  // partial rows: the panel product may write more rows (one per 128-row tile)
-  // (+1: a row for the deflation term of r^T z)
-  const int64_t npa = std::max<int64_t>(nbx + 1, sizeof(TV) == 4 ? c->tc_nblk : 0);
+  // spectral deflation of the preconditioner (FP32 star panels of one field;
+  // the vectors are prepared per refresh, before the mean solve), in its
+  // tensor-core form when the context has tensor-core tiles
+  const bool defl =
+      stars && sizeof(TV) == 4 && c->cfg.deflate > 0 && c->n_fields == 1 && deflate_ready(c);
+  const bool defl_tc = defl && deflate_tc(c);
+  const int nch = defl_tc ? deflate_tc_chunks(c, (int)R) : 0;  // partial rows of its step
+  // partial rows: the panel product may write more rows (one per 128-row
+  // tile), the tensor-core deflation step one per row chunk; then the rows
+  // of the deflation term of r^T z (1, or 8 in the tensor-core form)
+  const int64_t rows_a = std::max<int64_t>(std::max<int64_t>(nbx, nch),
+                                           sizeof(TV) == 4 ? c->tc_nblk : 0);
+  const int64_t rows_b = std::max<int64_t>(nbx, nch);
+  const int ncorr = defl ? (defl_tc ? 8 : 1) : 0;
   bool ok = ensure(c, ws.P_X, pbytes) && ensure(c, ws.P_R, pbytes) && ensure(c, ws.P_P, pbytes) &&
             ensure(c, ws.P_PD, pbytes) && ensure(c, ws.P_Q, pbytes) &&
-            ensure(c, ws.P_part, (size_t)(npa + nbx + 1) * R * sizeof(double)) &&
+            ensure(c, ws.P_part, (size_t)(rows_a + rows_b + std::max(ncorr, 1)) * R *
+                                     sizeof(double)) &&
             ensure(c, ws.P_scal, 6 * (size_t)R * sizeof(double)) &&
             ensure(c, ws.P_active, (size_t)(R + 32) * sizeof(int));
   if (!ok) return set_error(c, GM_E_NOMEM, "variance panels");
   TV *X = (TV*)ws.P_X.p, *Rr = (TV*)ws.P_R.p, *P = (TV*)ws.P_P.p, *PD = (TV*)ws.P_PD.p,
      *Q = (TV*)ws.P_Q.p;
   double* pa = (double*)ws.P_part.p;
-  double* pb = pa + (size_t)npa * R;
+  double* pb = pa + (size_t)rows_a * R;
+  double* corr = pb + (size_t)rows_b * R;  // the deflation rows of r^T z
   double* scal = (double*)ws.P_scal.p;
   int* active = (int*)ws.P_active.p;
   int* n_active = active + R;
@@ -1102,16 +1150,15 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
   const int redb = (int)ceil_div(R, 256);
   int64_t total_it = 0;
   const int tb = (int)std::min<int64_t>(ceil_div(n, 256), 16 * sms);
-  // spectral deflation of the preconditioner (FP32 star panels of one field)
-  // (the vectors are prepared per refresh, before the mean solve)
-  const bool defl =
-      stars && sizeof(TV) == 4 && c->cfg.deflate > 0 && c->n_fields == 1 && deflate_ready(c);
-  const int nbr = defl ? nbx + 1 : nbx;  // partial rows read by the rz / rr reductions
-  double* corr = pa + (size_t)nbx * R;   // the deflation row of r^T z
   for (int64_t r0 = 0; r0 < n_cols_all; r0 += R) {
     const int64_t ncols = std::min<int64_t>(R, n_cols_all - r0);
     GM_CUDA_CHECK(c, cudaMemsetAsync(Rr, 0, pbytes, st));
-    if (probe) {
+    if (probe && c->probe_factor_done >= 2.0) {
+      GM_PROF(c, "k_panel_rhs_probe");
+      k_panel_rhs_probe_w<TA, TV><<<(int)std::min<int64_t>(ceil_div(n * 32, 256), 16 * sms), 256,
+                                    0, st>>>(n, r0, ncols, (int)R, row_ptr, col, (const TA*)val,
+                                             dv, c->tau, kdiag_rows, c->probe_colour, Rr);
+    } else if (probe) {
       GM_PROF(c, "k_panel_rhs_probe");
       k_panel_rhs_probe<TA, TV><<<tb, 256, 0, st>>>(n, r0, ncols, (int)R, row_ptr, col,
                                                     (const TA*)val, dv, c->tau, kdiag_rows,
@@ -1139,19 +1186,31 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
       k_panel_init<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, dv, X, Rr, P, PD, pa, pb);
       GM_LAUNCH_CHECK(c);
     }
+    // the BF16 planes of PD were written by the deflation update (the
+    // asynchronous tile product then skips its split)
+    bool planes = false;
     if (defl) {
-      // z = M_d^-1 r for the initial residuals: P, PD and the rz row
-      GM_CUDA_CHECK(c, cudaMemsetAsync(pb + (size_t)nbx * R, 0, R * sizeof(double), st));
-      gm_status ds = deflate_rhs(c, (int)R, (const float*)Rr, corr);
-      if (ds == GM_OK)
-        ds = deflate_update(c, (int)R, nbx, (const float*)minv, (const float*)dv, nullptr, nullptr,
-                            (const float*)Rr, (float*)P, (float*)PD);
+      // z = M_d^-1 r for the initial residuals: P, PD and the rz rows
+      gm_status ds;
+      if (defl_tc) {
+        planes = c->tc_pf == 4;
+        ds = deflate_step_tc(c, (int)R, nch, nullptr, (const float*)minv, (float*)X, (float*)Rr,
+                             (const float*)P, (const float*)Q, nullptr, nullptr, corr);
+        if (ds == GM_OK)
+          ds = deflate_update_tc(c, (int)R, (const float*)minv, (const float*)dv, nullptr,
+                                 nullptr, (const float*)Rr, (float*)P, (float*)PD, planes);
+      } else {
+        ds = deflate_rhs(c, (int)R, (const float*)Rr, corr);
+        if (ds == GM_OK)
+          ds = deflate_update(c, (int)R, nbx, (const float*)minv, (const float*)dv, nullptr,
+                              nullptr, (const float*)Rr, (float*)P, (float*)PD);
+      }
       if (ds != GM_OK) return ds;
     }
     GM_CUDA_CHECK(c, cudaMemsetAsync(n_active, 0, sizeof(int), st));
     GM_PROF(c, "k_panel_reduce");
-    k_panel_reduce<<<redb, 256, 0, st>>>(0, nbr, (int)R, ncols, tol2, 0, max_it, pa, pb, scal,
-                                         active, n_active, c->d_flags);
+    k_panel_reduce<<<redb, 256, 0, st>>>(0, nbx, (int)R, ncols, tol2, 0, max_it, pa, pb, corr,
+                                         ncorr, scal, active, n_active, c->d_flags);
     GM_LAUNCH_CHECK(c);
     const int check = 8;
     GM_CUDA_CHECK(c, cudaMemcpyAsync(hn, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1160,26 +1219,42 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     for (; it >= 1 && it <= max_it; ++it) {
       int nbu = nbx;
       {
-        gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, P, PD, Q, pa, &nbu);
+        gm_status ss = panel_product<TA, TV>(c, n, R, nbx, grid, dv, P, PD, Q, pa, &nbu, planes);
         if (ss != GM_OK) return ss;
       }
       GM_PROF(c, "k_panel_reduce");
       k_panel_reduce<<<redb, 256, 0, st>>>(1, nbu, (int)R, ncols, tol2, it, max_it, pa, nullptr,
-                                           scal, active, n_active, c->d_flags);
+                                           nullptr, 0, scal, active, n_active, c->d_flags);
       GM_LAUNCH_CHECK(c);
-      GM_PROF(c, "k_panel_update1");
-      k_panel_update1<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, scal, X, Rr, P, Q, pa, pb);
-      GM_LAUNCH_CHECK(c);
-      if (defl) {
-        gm_status ds = deflate_rhs(c, (int)R, (const float*)Rr, corr);
+      int nbr = nbx;  // partial rows of rz / rr
+      if (defl_tc) {
+        // X, Rr update fused with C = Y^T Rr and the deflation rows
+        gm_status ds = deflate_step_tc(c, (int)R, nch, scal, (const float*)minv, (float*)X,
+                                       (float*)Rr, (const float*)P, (const float*)Q, pa, pb, corr);
         if (ds != GM_OK) return ds;
+        nbr = nch;
+      } else {
+        GM_PROF(c, "k_panel_update1");
+        k_panel_update1<TV><<<grid, kBT, 0, st>>>(n, (int)R, minv, scal, X, Rr, P, Q, pa, pb);
+        GM_LAUNCH_CHECK(c);
+        if (defl) {
+          gm_status ds = deflate_rhs(c, (int)R, (const float*)Rr, corr);
+          if (ds != GM_OK) return ds;
+        }
       }
       GM_CUDA_CHECK(c, cudaMemsetAsync(n_active, 0, sizeof(int), st));
       GM_PROF(c, "k_panel_reduce");
-      k_panel_reduce<<<redb, 256, 0, st>>>(2, nbr, (int)R, ncols, tol2, it, max_it, pa, pb, scal,
-                                           active, n_active, c->d_flags);
+      k_panel_reduce<<<redb, 256, 0, st>>>(2, nbr, (int)R, ncols, tol2, it, max_it, pa, pb, corr,
+                                           ncorr, scal, active, n_active, c->d_flags);
       GM_LAUNCH_CHECK(c);
-      if (defl) {
+      planes = false;
+      if (defl_tc) {
+        planes = c->tc_pf == 4;
+        gm_status ds = deflate_update_tc(c, (int)R, (const float*)minv, (const float*)dv,
+                                         scal + R, active, (const float*)Rr, (float*)P,
+                                         (float*)PD, planes);
+        if (ds != GM_OK) return ds;
+      } else if (defl) {
         gm_status ds = deflate_update(c, (int)R, nbx, (const float*)minv, (const float*)dv,
                                       scal + R, active, (const float*)Rr, (float*)P, (float*)PD);
         if (ds != GM_OK) return ds;
