@@ -232,7 +232,7 @@ def run_reference(a):
 # DRAM bytes (read + write) of one launch of the asynchronous tile product on
 # the 20,000-star workload at panel 4,640, from one ncu capture of that launch
 # (dram__bytes_read.sum + dram__bytes_write.sum); other shapes were not captured
-TC_ASYNC_TRAFFIC = {(20000, 4640): 1.853e9 + 0.349e9}
+TC_ASYNC_TRAFFIC = {}
 
 
 def roofline_for(name, launches, ms, st, cfg_prec, panel, async_b=False):
@@ -484,9 +484,8 @@ def run_gpu(a):
     # right-hand sides per product launch (the panel may hold fewer columns
     # than there are solves when memory caps it)
     panel = st.get("variance_panel_width") or cfg.rhs_panel or (math.ceil(cols / 32) * 32)
-    # the asynchronous variant is the one that splits the panel into BF16 planes
     roof = roofline_for(dom[0], dom[1][0], dom[1][1], st, a.precision, panel,
-                        async_b="k_split3_planes" in kt)
+                        async_b=st.get("tile_variant") == 4)
     launches = int(sum(v[0] for v in kt.values()))
     total_ms = sum(v[1] for v in kt.values())
 

@@ -170,6 +170,10 @@ typedef struct {
   int64_t variance_panel_width; /* right-hand sides per panel of the last
                               multi-RHS solve (each product launch covers
                               this many columns)                             */
+  int64_t tile_variant;    /* tensor-core tile product in use: 0 untuned or
+                              CUDA-core path, 1-2 synchronous gathers, 3
+                              warp-specialised ring, 4 B operand copied from
+                              BF16 planes                                    */
 } gm_stats;
 
 /* Fills *cfg with defaults: sigma2 1, L0 20 pc, rho_bar 1e-3 mag/pc, cutoff

@@ -709,6 +709,7 @@ gm_status gm_get_probe_colours(gm_ctx* c, int32_t* colour_out) {
 gm_status gm_get_stats(gm_ctx* c, gm_stats* out) {
   if (!c || !out) return GM_E_INVAL;
   *out = c->stats;
+  out->tile_variant = c->tc_nblk > 0 ? c->tc_pf : 0;
   return GM_OK;
 }
 

@@ -74,7 +74,8 @@ class Stats(C.Structure):
                 ("cg_resid_var", C.c_double), ("surrogate_fallback", C.c_int64),
                 ("surrogate_loss", C.c_double), ("surrogate_val_rmse", C.c_double),
                 ("surrogate_gate_frac", C.c_double), ("probe_colours", C.c_int64),
-                ("tile_ksteps", C.c_int64), ("variance_panel_width", C.c_int64)]
+                ("tile_ksteps", C.c_int64), ("variance_panel_width", C.c_int64),
+                ("tile_variant", C.c_int64)]
 
 
 _lib = None
