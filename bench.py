@@ -264,6 +264,7 @@ def roofline_for(name, launches, ms, st, cfg_prec, panel, async_b=False):
         traffic = TC_ASYNC_TRAFFIC.get((n, panel)) if async_b else None
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": traffic, "kernel": name,
+                "variant": st.get("tile_variant"),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured) / 6 "
                                "BF16 MMAs per FP32-grade product",
                 "work_per_launch": f"2 x nnz x panel = {flops:.3e} flop",

@@ -133,8 +133,18 @@ __global__ void k_dtc_img_rows(int64_t n, int64_t nblk, const float* __restrict_
 }
 
 // ---------------------------------------------------------------- step
+// One producer thread's loads of a K-step.
+struct StepRegs {
+  float4 r[4], x[4], p[4], q[4];
+  float m[4];
+  int v;  // bit h: row h of the K-step is a row of the panel
+};
+
 // alpha null: C's partial rows of R only (X, R untouched, no rz / rr).
-__global__ void __launch_bounds__(kS1Threads, 3) k_dtc_step(
+// kPipe: two K-steps of loads in flight per producer (two CTAs per SM), else
+// one (three CTAs per SM).
+template <bool kPipe>
+__global__ void __launch_bounds__(kS1Threads, kPipe ? 2 : 3) k_dtc_step(
     int64_t n, int R, int kpc, const unsigned char* __restrict__ yimg,
     const double* __restrict__ alpha, const float* __restrict__ minv, float* __restrict__ X,
     float* __restrict__ Rr, const float* __restrict__ P, const float* __restrict__ Q,
@@ -193,12 +203,37 @@ __global__ void __launch_bounds__(kS1Threads, 3) k_dtc_step(
 #pragma unroll
     for (int e = 0; e < 4; ++e) a[e] = (upd && vcol) ? (float)alpha[col + e] : 0.f;
     int64_t issued = 0;
-    for (int64_t ks = 0; ks < nks; ++ks) {
+    // the loads of one K-step: the thread's four row segments of R (and X,
+    // P, Q when updating)
+    auto load = [&](int64_t ks, StepRegs& S) {
+      S.v = 0;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int64_t i = 16 * (ks0 + ks) + warp + 4 * h;
+        const bool vh = vcol && i < n;
+        S.v |= vh ? 1 << h : 0;
+        S.m[h] = 0.f;
+        S.r[h] = S.x[h] = S.p[h] = S.q[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (vh) {
+          const int64_t at = i * R + col;
+          S.r[h] = *reinterpret_cast<const float4*>(Rr + at);
+          if (upd) {
+            S.x[h] = *reinterpret_cast<const float4*>(X + at);
+            S.p[h] = __ldcs(reinterpret_cast<const float4*>(P + at));
+            S.q[h] = __ldcs(reinterpret_cast<const float4*>(Q + at));
+            S.m[h] = minv[i];
+          }
+        }
+      }
+    };
+    // update, partial sums, BF16 pieces of R' into stage ks % ring; false
+    // when a wait gave up
+    auto produce = [&](int64_t ks, const StepRegs& S) -> bool {
       const int s = (int)(ks % kS1Ring);
       const int64_t use = ks / kS1Ring;
       if (use > 0 && !tg::wait(tg::smem(&empty[s]), (uint32_t)((use - 1) & 1), abort_v)) {
         abort_flag = 1;
-        break;
+        return false;
       }
       unsigned char* sB = sm + s * kS1Stage;
       if (t == 0) {
@@ -207,42 +242,21 @@ __global__ void __launch_bounds__(kS1Threads, 3) k_dtc_step(
                      tg::smem(&fullA[s]));
         ++issued;
       }
-      // all loads of the thread's four rows first
-      float4 r[4], x[4], p[4], q[4];
-      float m[4];
-      bool v[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int64_t i = 16 * (ks0 + ks) + warp + 4 * h;
-        v[h] = vcol && i < n;
-        m[h] = 0.f;
-        r[h] = x[h] = p[h] = q[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (v[h]) {
-          const int64_t at = i * R + col;
-          r[h] = *reinterpret_cast<const float4*>(Rr + at);
-          if (upd) {
-            x[h] = *reinterpret_cast<const float4*>(X + at);
-            p[h] = __ldcs(reinterpret_cast<const float4*>(P + at));
-            q[h] = __ldcs(reinterpret_cast<const float4*>(Q + at));
-            m[h] = minv[i];
-          }
-        }
-      }
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
         const int kr = warp + 4 * h;
-        float rv[4] = {r[h].x, r[h].y, r[h].z, r[h].w};
-        if (upd && v[h]) {
+        float rv[4] = {S.r[h].x, S.r[h].y, S.r[h].z, S.r[h].w};
+        if (upd && (S.v >> h & 1)) {
           const int64_t at = (16 * (ks0 + ks) + kr) * R + col;
-          const float xv[4] = {x[h].x, x[h].y, x[h].z, x[h].w};
-          const float pv[4] = {p[h].x, p[h].y, p[h].z, p[h].w};
-          const float qv[4] = {q[h].x, q[h].y, q[h].z, q[h].w};
+          const float xv[4] = {S.x[h].x, S.x[h].y, S.x[h].z, S.x[h].w};
+          const float pv[4] = {S.p[h].x, S.p[h].y, S.p[h].z, S.p[h].w};
+          const float qv[4] = {S.q[h].x, S.q[h].y, S.q[h].z, S.q[h].w};
           float xn[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             xn[e] = xv[e] + a[e] * pv[e];
             rv[e] = rv[e] - a[e] * qv[e];
-            rz[e].add(rv[e] * (m[h] * rv[e]));
+            rz[e].add(rv[e] * (S.m[h] * rv[e]));
             rr[e].add(rv[e] * rv[e]);
           }
           *reinterpret_cast<float4*>(X + at) = make_float4(xn[0], xn[1], xn[2], xn[3]);
@@ -259,6 +273,25 @@ __global__ void __launch_bounds__(kS1Threads, 3) k_dtc_step(
       // them through the async proxy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tg::arrive(tg::smem(&fullB[s]));
+      return true;
+    };
+    if constexpr (kPipe) {
+      // two K-steps of loads in flight: the next step's loads are issued
+      // before this step's arithmetic and stores
+      StepRegs A, B;
+      if (nks > 0) load(0, A);
+      for (int64_t ks = 0; ks < nks; ks += 2) {
+        if (ks + 1 < nks) load(ks + 1, B);
+        if (!produce(ks, A) || ks + 1 >= nks) break;
+        if (ks + 2 < nks) load(ks + 2, A);
+        if (!produce(ks + 1, B)) break;
+      }
+    } else {
+      StepRegs A;
+      for (int64_t ks = 0; ks < nks; ++ks) {
+        load(ks, A);
+        if (!produce(ks, A)) break;
+      }
     }
     if (t == 0 && *abort_v) {  // bounded waits for the bulk copies still in flight
       for (int qq = 0; qq < kS1Ring; ++qq) {
@@ -578,25 +611,33 @@ gm_status dtc_images(gm_ctx* c, int64_t n, const float* Y, const float* Yw, void
 static gm_status dtc_attributes(gm_ctx* c) {
   static bool done = false;
   if (done) return GM_OK;
-  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_dtc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        kS1Smem));
+  for (auto k : {k_dtc_step<false>, k_dtc_step<true>}) {
+    GM_CUDA_CHECK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kS1Smem));
+    GM_CUDA_CHECK(c, cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          100));
+  }
   GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_dtc_update,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kU2Smem));
-  // all of the unified L1 / shared memory as shared: two CTAs per SM (the
-  // occupancy query otherwise assumes the default split and answers one)
-  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_dtc_step,
-                                        cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  // all of the unified L1 / shared memory as shared: the CTAs per SM that the
+  // registers allow
   GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_dtc_update,
                                         cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   done = true;
   return GM_OK;
 }
 
+// Two K-steps of loads in flight per producer (GM_DTC_PIPE=1) or one (=0).
+static bool dtc_pipe() {
+  const char* e = std::getenv("GM_DTC_PIPE");
+  return e ? e[0] == '1' : false;
+}
+
 // Row chunks of the step kernel for a panel of R columns: one wave of CTAs
 // at three resident per SM (125 registers x 160 threads and 72 KB of shared
-// memory each), at most 64.
+// memory each; two with the pipelined loads), at most 64.
 int dtc_chunks(gm_ctx* c, int64_t n, int R) {
-  constexpr int kPerSm = 3;
+  const int kPerSm = dtc_pipe() ? 2 : 3;
   const int64_t ncg = ceil_div(R, kS1Cols), nks = ceil_div(n, 16);
   int64_t nch = std::max<int64_t>(1, (int64_t)kPerSm * sm_count(c) / ncg);
   nch = std::min<int64_t>(std::min<int64_t>(nch, 64), std::max<int64_t>(nks, 1));
@@ -614,7 +655,8 @@ gm_status dtc_step(gm_ctx* c, int64_t n, int R, int nch, const void* yimg, const
   const int kpc = (int)ceil_div(std::max<int64_t>(nks, 1), nch);
   const int ncg = (int)ceil_div(R, kS1Cols);
   GM_PROF(c, "k_dtc_step");
-  k_dtc_step<<<dim3((unsigned)ncg, (unsigned)nch), kS1Threads, kS1Smem, c->stream>>>(
+  auto kern = dtc_pipe() ? k_dtc_step<true> : k_dtc_step<false>;
+  kern<<<dim3((unsigned)ncg, (unsigned)nch), kS1Threads, kS1Smem, c->stream>>>(
       n, R, kpc, (const unsigned char*)yimg, alpha, minv, X, Rr, P, Q, part_rz, part_rr, Cp,
       c->d_flags);
   GM_LAUNCH_CHECK(c);

@@ -131,7 +131,9 @@ struct gm_ctx {
   gm::Buffer tc_brow0, tc_boffd;    // first row of each block (+ end); device h_tc_boff
   gm::Buffer tc_trow, tc_tpos;      // tile order: row at tile position p, position of row i
   bool tc_order = false;            // tc_trow / tc_tpos in use (else position = row)
-  int tc_pf = 0;                    // tuned prefetch depth of the tile product (0: untuned)
+  int tc_pf = 0;                    // tuned variant of the tile product (0: untuned) for
+                                    // panels wider than one column group (and packed panels)
+  int tc_pf_narrow = 0;             // ... for panels of one column group (<= 256 columns)
   double* kdiag = nullptr;
   double* prior_m = nullptr;
 
@@ -344,6 +346,8 @@ gm_status tc_tiles_build(gm_ctx* c);
 // deflate_update_tc) for the asynchronous variant, which then skips its split.
 gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const float* P,
                         const float* PD, float* Q, double* part_pq, bool planes_ready = false);
+// the tile product's variant for a single panel of R columns (0: not yet tuned)
+int tc_variant(gm_ctx* c, int R);
 // Packed multi-field panels (no partials); tune = choose the prefetch depth
 // (on the context stream, outside any graph capture) instead of launching.
 gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,

@@ -1193,7 +1193,7 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
       // z = M_d^-1 r for the initial residuals: P, PD and the rz rows
       gm_status ds;
       if (defl_tc) {
-        planes = c->tc_pf == 4;
+        planes = tc_variant(c, (int)R) == 4;
         ds = deflate_step_tc(c, (int)R, nch, nullptr, (const float*)minv, (float*)X, (float*)Rr,
                              (const float*)P, (const float*)Q, nullptr, nullptr, corr);
         if (ds == GM_OK)
@@ -1249,7 +1249,7 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
       GM_LAUNCH_CHECK(c);
       planes = false;
       if (defl_tc) {
-        planes = c->tc_pf == 4;
+        planes = tc_variant(c, (int)R) == 4;
         gm_status ds = deflate_update_tc(c, (int)R, (const float*)minv, (const float*)dv,
                                          scal + R, active, (const float*)Rr, (float*)P,
                                          (float*)PD, planes);

@@ -243,6 +243,73 @@ __global__ void k_tc_ucol(int64_t nblk, const int64_t* __restrict__ bptr,
   }
 }
 
+// Union of the columns of one tile block's rows, as a bitmap over all n
+// columns in shared memory (CTA per block, warp per row, shared-memory
+// atomics).  Phase 0 writes the union's size; phase 1 writes the union in
+// increasing column order to ucol[bptr[b] ..] and, padded to whole K-steps
+// with its last column, to upad[16 kbase[b] ..].
+constexpr int kUnionMaxWords = 40960;  // 160 KB of bitmap: n <= 1,310,720
+
+__global__ void __launch_bounds__(256) k_tc_union(
+    int64_t n, int phase, const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+    const int64_t* __restrict__ brow0, const int32_t* __restrict__ trow,
+    int64_t* __restrict__ count, const int64_t* __restrict__ bptr,
+    const int64_t* __restrict__ kbase, int32_t* __restrict__ ucol, int32_t* __restrict__ upad) {
+  extern __shared__ uint32_t bm[];
+  __shared__ int64_t sh_off[256];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int nwords = (int)((n + 31) >> 5);
+  const int64_t b = blockIdx.x;
+  for (int w = t; w < nwords; w += 256) bm[w] = 0u;
+  __syncthreads();
+  for (int64_t p = brow0[b] + warp; p < brow0[b + 1]; p += 8) {
+    const int64_t i = trow ? (int64_t)trow[p] : p;
+    for (int64_t e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+      const int32_t j = col[e];
+      atomicOr(&bm[j >> 5], 1u << (j & 31));
+    }
+  }
+  __syncthreads();
+  // each thread owns a contiguous range of words
+  const int wpt = (nwords + 255) / 256;
+  const int w0 = min(t * wpt, nwords), w1 = min(w0 + wpt, nwords);
+  int64_t cnt = 0;
+  for (int w = w0; w < w1; ++w) cnt += __popc(bm[w]);
+  sh_off[t] = cnt;
+  __syncthreads();
+  // inclusive scan of the counts (Hillis-Steele over the block)
+  for (int d = 1; d < 256; d <<= 1) {
+    const int64_t v = t >= d ? sh_off[t - d] : 0;
+    __syncthreads();
+    sh_off[t] += v;
+    __syncthreads();
+  }
+  const int64_t total = sh_off[255];
+  if (phase == 0) {
+    if (t == 0) count[b] = total;
+    return;
+  }
+  int64_t k = sh_off[t] - cnt;  // exclusive offset
+  const int64_t u0 = bptr[b], s0 = kbase[b] * kTcK;
+  for (int w = w0; w < w1; ++w) {
+    uint32_t bits = bm[w];
+    while (bits) {
+      const int j = (w << 5) + __ffs(bits) - 1;
+      bits &= bits - 1;
+      ucol[u0 + k] = j;
+      upad[s0 + k] = j;
+      ++k;
+    }
+  }
+  // padding slots: the last union column
+  const int64_t slots = (kbase[b + 1] - kbase[b]) * kTcK;
+  if (total > 0) {
+    __syncthreads();
+    const int32_t last = ucol[u0 + total - 1];
+    for (int64_t q = total + t; q < slots; q += 256) upad[s0 + q] = last;
+  }
+}
+
 // Operand images: entry (i, j) of block b at union position q of j goes to
 // K-step kbase[b] + q / 16, column q % 16, row p - brow0[b] (p = the tile
 // position of row i), three pieces.
@@ -1129,55 +1196,106 @@ gm_status tc_tiles_build(gm_ctx* c) {
     }
   }
   const int32_t* tpos = c->tc_order ? (const int32_t*)c->tc_tpos.p : nullptr;
-  int64_t n_pad = 1024;
-  while (n_pad < nnz) n_pad <<= 1;
-  unsigned long long* keys = (unsigned long long*)dev_alloc(c, n_pad * sizeof(unsigned long long));
-  int64_t* flag = (int64_t*)dev_alloc(c, std::max<int64_t>(nnz, 1) * sizeof(int64_t));
-  int64_t* pos = (int64_t*)dev_alloc(c, (nnz + 1) * sizeof(int64_t));
-  if (!keys || !flag || !pos) return set_error(c, GM_E_NOMEM, "tensor-core tile keys");
   const int wb = (int)std::min<int64_t>(ceil_div(n * 32, 256), 32 * sms);
   const int eb = (int)std::min<int64_t>(ceil_div(nnz, 256), 16 * sms);
-  GM_PROF(c, "k_tc_keys");
-  k_tc_keys<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, nnz, n_pad, tb, tpos, keys);
-  GM_LAUNCH_CHECK(c);
-  gm_status s = sort_u64(c, keys, n_pad);
-  if (s != GM_OK) return s;
-  GM_PROF(c, "k_tc_flags");
-  k_tc_flags<<<eb, 256, 0, st>>>(nnz, keys, flag);
-  GM_LAUNCH_CHECK(c);
-  s = scan_i64(c, flag, pos, nnz);
-  if (s != GM_OK) return s;
-  int64_t U = 0;
-  GM_CUDA_CHECK(c, cudaMemcpyAsync(&U, pos + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
-  int32_t* ucol = (int32_t*)dev_alloc(c, std::max<int64_t>(U, 1) * sizeof(int32_t));
-  int32_t* ublk = (int32_t*)dev_alloc(c, std::max<int64_t>(U, 1) * sizeof(int32_t));
+  // union of each block's columns, K-step offsets and padded columns: by a
+  // bitmap per block when n fits shared memory, else by a sort of (block,
+  // column) keys over all entries (also with GM_TC_UNION=sort)
+  const int nwords = (int)ceil_div(n, 32);
+  const char* ue = std::getenv("GM_TC_UNION");
+  const bool bitmap = nwords <= kUnionMaxWords && !(ue && ue[0] == 's');
+  std::vector<int64_t> hb(nblk + 1, 0), hk(nblk + 1, 0);
+  int64_t U = 0, nks = 0;
+  int32_t* ucol = nullptr;
   int64_t* bptr = (int64_t*)dev_alloc(c, (nblk + 1) * sizeof(int64_t));
-  if (!ucol || !ublk || !bptr) return set_error(c, GM_E_NOMEM, "tensor-core tile union");
-  GM_PROF(c, "k_tc_unique");
-  k_tc_unique<<<eb, 256, 0, st>>>(nnz, keys, flag, pos, ucol, ublk);
-  GM_LAUNCH_CHECK(c);
-  GM_PROF(c, "k_tc_bptr");
-  k_tc_bptr<<<(int)std::min<int64_t>(ceil_div(U + 1, 256), 16 * sms), 256, 0, st>>>(U, nblk, ublk,
-                                                                                   bptr);
-  GM_LAUNCH_CHECK(c);
-  std::vector<int64_t> hb(nblk + 1), hk(nblk + 1, 0);
-  GM_CUDA_CHECK(c, cudaMemcpyAsync(hb.data(), bptr, (nblk + 1) * sizeof(int64_t),
-                                   cudaMemcpyDeviceToHost, st));
-  GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
-  for (int64_t b = 0; b < nblk; ++b) hk[b + 1] = hk[b] + ceil_div(hb[b + 1] - hb[b], kTcK);
-  const int64_t nks = hk[nblk];
-  if (!ensure(c, c->tc_kbase, (nblk + 1) * sizeof(int64_t)) ||
-      !ensure(c, c->tc_upad, std::max<int64_t>(nks, 1) * kTcK * sizeof(int32_t)) ||
-      !ensure(c, c->tc_img, std::max<int64_t>(nks, 1) * 3 * kTcA))
-    return set_error(c, GM_E_NOMEM, "tensor-core tiles");
+  if (!bptr) return set_error(c, GM_E_NOMEM, "tensor-core tile union");
+  const int32_t* trow = c->tc_order ? (const int32_t*)c->tc_trow.p : nullptr;
+  const size_t bm_smem = (size_t)nwords * sizeof(uint32_t);
+  if (bitmap) {
+    if (bm_smem > 48 * 1024)
+      GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_tc_union, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)bm_smem));
+    GM_PROF(c, "k_tc_union");
+    k_tc_union<<<(unsigned)nblk, 256, bm_smem, st>>>(n, 0, c->row_ptr, c->col,
+                                                     (const int64_t*)c->tc_brow0.p, trow, bptr,
+                                                     nullptr, nullptr, nullptr, nullptr);
+    GM_LAUNCH_CHECK(c);
+    std::vector<int64_t> hc(nblk);
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(hc.data(), bptr, nblk * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+    for (int64_t b = 0; b < nblk; ++b) {
+      hb[b + 1] = hb[b] + hc[b];
+      hk[b + 1] = hk[b] + ceil_div(hc[b], kTcK);
+    }
+    U = hb[nblk];
+    nks = hk[nblk];
+    ucol = (int32_t*)dev_alloc(c, std::max<int64_t>(U, 1) * sizeof(int32_t));
+    if (!ucol) return set_error(c, GM_E_NOMEM, "tensor-core tile union");
+    if (!ensure(c, c->tc_kbase, (nblk + 1) * sizeof(int64_t)) ||
+        !ensure(c, c->tc_upad, std::max<int64_t>(nks, 1) * kTcK * sizeof(int32_t)) ||
+        !ensure(c, c->tc_img, std::max<int64_t>(nks, 1) * 3 * kTcA))
+      return set_error(c, GM_E_NOMEM, "tensor-core tiles");
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(bptr, hb.data(), (nblk + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, st));
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(c->tc_kbase.p, hk.data(), (nblk + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, st));
+    GM_PROF(c, "k_tc_union");
+    k_tc_union<<<(unsigned)nblk, 256, bm_smem, st>>>(
+        n, 1, c->row_ptr, c->col, (const int64_t*)c->tc_brow0.p, trow, nullptr, bptr,
+        (const int64_t*)c->tc_kbase.p, ucol, (int32_t*)c->tc_upad.p);
+    GM_LAUNCH_CHECK(c);
+  } else {
+    int64_t n_pad = 1024;
+    while (n_pad < nnz) n_pad <<= 1;
+    ScopedDev kd(c, n_pad * sizeof(unsigned long long));
+    ScopedDev fd(c, std::max<int64_t>(nnz, 1) * sizeof(int64_t));
+    ScopedDev pd(c, (nnz + 1) * sizeof(int64_t));
+    if (!kd.p || !fd.p || !pd.p) return set_error(c, GM_E_NOMEM, "tensor-core tile keys");
+    unsigned long long* keys = (unsigned long long*)kd.p;
+    int64_t* flag = (int64_t*)fd.p;
+    int64_t* pos = (int64_t*)pd.p;
+    GM_PROF(c, "k_tc_keys");
+    k_tc_keys<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, nnz, n_pad, tb, tpos, keys);
+    GM_LAUNCH_CHECK(c);
+    gm_status s = sort_u64(c, keys, n_pad);
+    if (s != GM_OK) return s;
+    GM_PROF(c, "k_tc_flags");
+    k_tc_flags<<<eb, 256, 0, st>>>(nnz, keys, flag);
+    GM_LAUNCH_CHECK(c);
+    s = scan_i64(c, flag, pos, nnz);
+    if (s != GM_OK) return s;
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(&U, pos + nnz, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+    ucol = (int32_t*)dev_alloc(c, std::max<int64_t>(U, 1) * sizeof(int32_t));
+    ScopedDev ub(c, std::max<int64_t>(U, 1) * sizeof(int32_t));
+    if (!ucol || !ub.p) return set_error(c, GM_E_NOMEM, "tensor-core tile union");
+    int32_t* ublk = (int32_t*)ub.p;
+    GM_PROF(c, "k_tc_unique");
+    k_tc_unique<<<eb, 256, 0, st>>>(nnz, keys, flag, pos, ucol, ublk);
+    GM_LAUNCH_CHECK(c);
+    GM_PROF(c, "k_tc_bptr");
+    k_tc_bptr<<<(int)std::min<int64_t>(ceil_div(U + 1, 256), 16 * sms), 256, 0, st>>>(U, nblk,
+                                                                                     ublk, bptr);
+    GM_LAUNCH_CHECK(c);
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(hb.data(), bptr, (nblk + 1) * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st));
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
+    for (int64_t b = 0; b < nblk; ++b) hk[b + 1] = hk[b] + ceil_div(hb[b + 1] - hb[b], kTcK);
+    nks = hk[nblk];
+    if (!ensure(c, c->tc_kbase, (nblk + 1) * sizeof(int64_t)) ||
+        !ensure(c, c->tc_upad, std::max<int64_t>(nks, 1) * kTcK * sizeof(int32_t)) ||
+        !ensure(c, c->tc_img, std::max<int64_t>(nks, 1) * 3 * kTcA))
+      return set_error(c, GM_E_NOMEM, "tensor-core tiles");
+    GM_CUDA_CHECK(c, cudaMemcpyAsync(c->tc_kbase.p, hk.data(), (nblk + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, st));
+    GM_PROF(c, "k_tc_ucol");
+    k_tc_ucol<<<(int)std::min<int64_t>(nblk, 16 * sms), 256, 0, st>>>(
+        nblk, bptr, (const int64_t*)c->tc_kbase.p, ucol, (int32_t*)c->tc_upad.p);
+    GM_LAUNCH_CHECK(c);
+    GM_CUDA_CHECK(c, cudaStreamSynchronize(st));  // the scoped scratch is released here
+  }
   int64_t* kbase = (int64_t*)c->tc_kbase.p;
-  GM_CUDA_CHECK(c, cudaMemcpyAsync(kbase, hk.data(), (nblk + 1) * sizeof(int64_t),
-                                   cudaMemcpyHostToDevice, st));
-  GM_PROF(c, "k_tc_ucol");
-  k_tc_ucol<<<(int)std::min<int64_t>(nblk, 16 * sms), 256, 0, st>>>(nblk, bptr, kbase, ucol,
-                                                                    (int32_t*)c->tc_upad.p);
-  GM_LAUNCH_CHECK(c);
   GM_CUDA_CHECK(c, cudaMemsetAsync(c->tc_img.p, 0, (size_t)nks * 3 * kTcA, st));
   GM_PROF(c, "k_tc_fill");
   k_tc_fill<<<wb, 256, 0, st>>>(n, c->row_ptr, c->col, (const float*)c->val, bptr, kbase, ucol,
@@ -1186,11 +1304,7 @@ gm_status tc_tiles_build(gm_ctx* c) {
   GM_LAUNCH_CHECK(c);
   GM_CUDA_CHECK(c, cudaStreamSynchronize(st));
   dev_free_now(c, bptr, (nblk + 1) * sizeof(int64_t));
-  dev_free_now(c, ublk, std::max<int64_t>(U, 1) * sizeof(int32_t));
   dev_free_now(c, ucol, std::max<int64_t>(U, 1) * sizeof(int32_t));
-  dev_free_now(c, pos, (nnz + 1) * sizeof(int64_t));
-  dev_free_now(c, flag, std::max<int64_t>(nnz, 1) * sizeof(int64_t));
-  dev_free_now(c, keys, n_pad * sizeof(unsigned long long));
   c->tc_nblk = nblk;
   c->tc_nks = nks;
   c->stats.tile_ksteps = nks;
@@ -1254,12 +1368,12 @@ static gm_status launch_tc(gm_ctx* c, int pf, dim3 grid, int64_t n, int R, const
 // Variant of the tile product: 1, 2 = CTA-synchronous with gathers one or two
 // steps ahead, 3 = warp-specialised ring, 4 = B copied asynchronously from
 // BF16 planes of PD.  GM_TC_PREFETCH=1|2|3|4 pins it, else the fastest on the
-// context's first panel product (one timed launch each; the product is
-// idempotent: Q is overwritten).
+// context's first panel product of the width class whose slot `variant` is
+// (two timed launches each; the product is idempotent: Q is overwritten).
 static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv, const float* P,
                          const float* PD, float* Q, double* part_pq, TcPanels pk,
-                         int64_t pd_elems) {
-  if (c->tc_pf) return GM_OK;
+                         int64_t pd_elems, int& variant) {
+  if (variant) return GM_OK;
   // the planes are allocated here, before any graph capture of the products
   if (!ensure(c, c->tc_planes, (size_t)std::max<int64_t>(pd_elems, 1) * 3 * sizeof(uint16_t)))
     return set_error(c, GM_E_NOMEM, "BF16 planes of the panel");
@@ -1282,7 +1396,7 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
   if (const char* e = std::getenv("GM_TC_PREFETCH")) {
     const int v = std::atoi(e);
     if (v >= 1 && v <= 4) {
-      c->tc_pf = v;
+      variant = v;
       return GM_OK;
     }
   }
@@ -1307,7 +1421,7 @@ static gm_status tc_tune(gm_ctx* c, dim3 grid, int64_t n, int R, const float* dv
     }
     if (fastest < best) {
       best = fastest;
-      c->tc_pf = pf;
+      variant = pf;
     }
   }
   cudaEventDestroy(a);
@@ -1322,15 +1436,20 @@ gm_status panel_spmm_tc(gm_ctx* c, int64_t n, int R, const float* dv, const floa
   dim3 grid((unsigned)ceil_div(R, kTcCols), (unsigned)c->tc_nblk);
   const TcPanels pk{nullptr, nullptr, nullptr, nullptr,
                     c->tc_order ? (const int32_t*)c->tc_trow.p : nullptr};
-  gm_status s = tc_tune(c, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R);
+  // one column group (the deflation refresh's 64-column products) and wider
+  // panels are tuned apart: their grids differ by the number of groups
+  int& variant = R <= kTcCols ? c->tc_pf_narrow : c->tc_pf;
+  gm_status s = tc_tune(c, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R, variant);
   if (s != GM_OK) return s;
-  if (c->tc_pf != 4) GM_PROF(c, "k_panel_spmm_tc");  // variant 4 times its two kernels itself
-  s = launch_tc(c, c->tc_pf, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R, c->stream,
-                planes_ready && c->tc_pf == 4);
+  if (variant != 4) GM_PROF(c, "k_panel_spmm_tc");  // variant 4 times its two kernels itself
+  s = launch_tc(c, variant, grid, n, R, dv, P, PD, Q, part_pq, pk, n * (int64_t)R, c->stream,
+                planes_ready && variant == 4);
   if (s != GM_OK) return s;
   GM_LAUNCH_CHECK(c);
   return GM_OK;
 }
+
+int tc_variant(gm_ctx* c, int R) { return R <= kTcCols ? c->tc_pf_narrow : c->tc_pf; }
 
 // Packed multi-field panels: one CTA per (tile block, column group) item.
 gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
@@ -1340,7 +1459,7 @@ gm_status panel_spmm_tc_packed(gm_ctx* c, int64_t n_items, const int2* items,
   const TcPanels pk{blk_base, blk_width, (const int64_t*)c->tc_brow0.p, items,
                     c->tc_order ? (const int32_t*)c->tc_trow.p : nullptr};
   dim3 grid((unsigned)n_items);
-  if (tune) return tc_tune(c, grid, c->n, 0, dv, P, PD, Q, nullptr, pk, pd_elems);
+  if (tune) return tc_tune(c, grid, c->n, 0, dv, P, PD, Q, nullptr, pk, pd_elems, c->tc_pf);
   return launch_tc(c, c->tc_pf, grid, c->n, 0, dv, P, PD, Q, nullptr, pk, pd_elems, st);
 }
 

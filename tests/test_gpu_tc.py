@@ -68,3 +68,34 @@ def test_tensor_core_panel_product_matches_simt_and_fp64(gm, monkeypatch, probe)
     assert "k_split3_planes" in res["tc4"][2]
     np.testing.assert_allclose(res["tc4"][0], res["tc1"][0], rtol=0, atol=1e-6)
     np.testing.assert_allclose(res["tc4"][1], res["tc1"][1], rtol=1e-5, atol=0)
+
+
+def test_tile_union_and_order(gm, monkeypatch):
+    """The block unions built from per-block bitmaps equal those of the sort of
+    (block, column) keys (same K-steps, bit-identical posterior), and the
+    Morton order of the tile rows gives fewer K-steps than the cell order with
+    the same posterior to FP32 rounding."""
+    cat = catalogue_subset(make_catalogue("c2_plain_20k", truth="mean"), np.arange(3000))
+    out = {}
+    for name, union, order in [("bitmap", None, None), ("sort", "sort", None),
+                               ("rows", None, "rows")]:
+        for var, val in (("GM_TC_UNION", union), ("GM_TC_ORDER", order)):
+            if val:
+                monkeypatch.setenv(var, val)
+            else:
+                monkeypatch.delenv(var, raising=False)
+        cfg = gm.config_from_catalogue(cat, precision=gm.PREC_FP32, cg_tol=1e-6,
+                                       probe_factor=2.0)
+        with gm.ep_init(cfg, cat["l"], cat["b"], cat["s"], cat["A_obs"], cat["A_sigma"]) as ctx:
+            ctx.build_cov()
+            ctx.ep_sweep(2, 0.0)
+            mu, var = ctx.get_posterior()
+            out[name] = (mu, var, ctx.stats()["tile_ksteps"])
+    assert out["bitmap"][2] == out["sort"][2] > 0
+    np.testing.assert_array_equal(out["bitmap"][0], out["sort"][0])
+    np.testing.assert_array_equal(out["bitmap"][1], out["sort"][1])
+    print("tile K-steps: Morton order %d, cell order %d" % (out["bitmap"][2], out["rows"][2]))
+    assert out["bitmap"][2] < out["rows"][2]
+    rel = np.abs(out["bitmap"][1] - out["rows"][1]) / out["rows"][1]
+    assert rel.max() < 1e-3 and np.median(rel) < 1e-5
+    assert np.abs(out["bitmap"][0] - out["rows"][0]).max() < 1e-4
