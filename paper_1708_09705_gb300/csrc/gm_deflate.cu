@@ -97,8 +97,12 @@ __global__ void k_df_scale_out(int64_t n, const float* __restrict__ ms, const fl
     W[e] = ms[e / kDefK] * Q[e];
 }
 
-// Gp[rb][a][b] = sum over 64-row block rb of X[i][a] Z[i][b] (FP64); thread
-// tile 16 entries; the 64 x 64 row blocks of X and Z staged in shared memory.
+// Gp[rb][a][b] = sum over 64-row block rb of X[i][a] Z[i][b]; thread tile 16
+// entries; the 64 x 64 row blocks of X and Z staged in shared memory.  The
+// products of FP32 inputs are summed over the block's 64 rows in FP32 (about
+// 64 roundings, ~1e-6 relative at worst: well inside what Cholesky-QR run
+// twice and the Rayleigh-Ritz values need) and over blocks in FP64 (GB300's
+// FP64 pipe, not the data, bounded the all-FP64 form).
 __global__ void __launch_bounds__(256) k_df_gram(int64_t n, const float* __restrict__ X,
                                                  const float* __restrict__ Z,
                                                  double* __restrict__ Gp) {
@@ -113,17 +117,17 @@ __global__ void __launch_bounds__(256) k_df_gram(int64_t n, const float* __restr
   }
   __syncthreads();
   const int a = t >> 2, b0 = 16 * (t & 3);
-  double acc[16];
+  float acc[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int q = 0; q < 16; ++q) acc[q] = 0.f;
   for (int r = 0; r < 64; ++r) {
-    const double xa = xs[r][a];
+    const float xa = xs[r][a];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = fma(xa, (double)zs[r][b0 + q], acc[q]);
+    for (int q = 0; q < 16; ++q) acc[q] = fmaf(xa, zs[r][b0 + q], acc[q]);
   }
   double* out = Gp + (int64_t)blockIdx.x * kDefK * kDefK + a * kDefK + b0;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) out[q] = acc[q];
+  for (int q = 0; q < 16; ++q) out[q] = (double)acc[q];
 }
 
 // G = sum over row blocks of Gp (fixed order)
@@ -364,16 +368,24 @@ __global__ void __launch_bounds__(256) k_df1_part(int64_t n, const float* __rest
 
 // c = sum_b cpart[b] (in order); rz_slot[0] += sum_j w_j c_j^2.  One block of
 // 64 threads.
+// (Four threads per j sum every fourth partial row, then j's thread adds the
+// four in order: the same fixed order on every call.)
 __global__ void k_df1_corr(int nb, const double* __restrict__ cpart, const float* __restrict__ w,
                            float* __restrict__ cvec, double* __restrict__ rz_slot) {
+  __shared__ double sp[4][kDefK];
   __shared__ double sh[kDefK];
-  const int j = threadIdx.x;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += cpart[(int64_t)b * kDefK + j];
-  cvec[j] = (float)s;
-  sh[j] = (double)w[j] * s * s;
+  const int j = threadIdx.x & (kDefK - 1), part = threadIdx.x >> 6;
+  double s4 = 0.0;
+  for (int b = part; b < nb; b += 4) s4 += cpart[(int64_t)b * kDefK + j];
+  sp[part][j] = s4;
   __syncthreads();
-  if (j == 0) {
+  if (threadIdx.x < kDefK) {
+    const double s = ((sp[0][j] + sp[1][j]) + sp[2][j]) + sp[3][j];
+    cvec[j] = (float)s;
+    sh[j] = (double)w[j] * s * s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < kDefK; ++q) t += sh[q];
     rz_slot[0] += t;
@@ -615,7 +627,10 @@ gm_status deflate_prepare(gm_ctx* c, const float* dv, const float* minv) {
     GM_LAUNCH_CHECK(c);
     return GM_OK;
   };
-  const int iters = F.have_v ? kDefItersWarm : kDefIters;
+  // GM_DEFL_WARM overrides the warm-started step count (1-16)
+  int warm = kDefItersWarm;
+  if (const char* e = std::getenv("GM_DEFL_WARM")) warm = std::min(16, std::max(1, std::atoi(e)));
+  const int iters = F.have_v ? warm : kDefIters;
   for (int it = 0; it < iters; ++it) {
     gm_status s = apply(V, Wb);
     if (s != GM_OK) return s;
@@ -751,7 +766,7 @@ gm_status deflate1_rhs(gm_ctx* c, const float* r, double* rz_slot) {
   k_df1_part<<<nb, 256, 0, c->stream>>>(c->n, (const float*)F.Y.p, r, (double*)F.cpart1.p);
   GM_LAUNCH_CHECK(c);
   GM_PROF(c, "k_df1_corr");
-  k_df1_corr<<<1, kDefK, 0, c->stream>>>(nb, (const double*)F.cpart1.p, (const float*)F.wv.p,
+  k_df1_corr<<<1, 4 * kDefK, 0, c->stream>>>(nb, (const double*)F.cpart1.p, (const float*)F.wv.p,
                                          (float*)F.c1.p, rz_slot);
   GM_LAUNCH_CHECK(c);
   return GM_OK;

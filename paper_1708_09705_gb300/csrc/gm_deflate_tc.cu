@@ -141,10 +141,10 @@ struct StepRegs {
 };
 
 // alpha null: C's partial rows of R only (X, R untouched, no rz / rr).
-// kPipe: two K-steps of loads in flight per producer (two CTAs per SM), else
-// one (three CTAs per SM).
-template <bool kPipe>
-__global__ void __launch_bounds__(kS1Threads, kPipe ? 2 : 3) k_dtc_step(
+// Three CTAs per SM (registers and shared memory); a second K-step of loads
+// in flight per producer needed ~230 registers (one CTA per SM) or spilled
+// at two CTAs per SM, and was slower either way.
+__global__ void __launch_bounds__(kS1Threads, 3) k_dtc_step(
     int64_t n, int R, int kpc, const unsigned char* __restrict__ yimg,
     const double* __restrict__ alpha, const float* __restrict__ minv, float* __restrict__ X,
     float* __restrict__ Rr, const float* __restrict__ P, const float* __restrict__ Q,
@@ -275,23 +275,10 @@ __global__ void __launch_bounds__(kS1Threads, kPipe ? 2 : 3) k_dtc_step(
       tg::arrive(tg::smem(&fullB[s]));
       return true;
     };
-    if constexpr (kPipe) {
-      // two K-steps of loads in flight: the next step's loads are issued
-      // before this step's arithmetic and stores
-      StepRegs A, B;
-      if (nks > 0) load(0, A);
-      for (int64_t ks = 0; ks < nks; ks += 2) {
-        if (ks + 1 < nks) load(ks + 1, B);
-        if (!produce(ks, A) || ks + 1 >= nks) break;
-        if (ks + 2 < nks) load(ks + 2, A);
-        if (!produce(ks + 1, B)) break;
-      }
-    } else {
-      StepRegs A;
-      for (int64_t ks = 0; ks < nks; ++ks) {
-        load(ks, A);
-        if (!produce(ks, A)) break;
-      }
+    StepRegs A;
+    for (int64_t ks = 0; ks < nks; ++ks) {
+      load(ks, A);
+      if (!produce(ks, A)) break;
     }
     if (t == 0 && *abort_v) {  // bounded waits for the bulk copies still in flight
       for (int qq = 0; qq < kS1Ring; ++qq) {
@@ -419,6 +406,14 @@ __global__ void k_dtc_sum(int R, int ncg, int nparts, const float* __restrict__ 
 }
 
 // ---------------------------------------------------------------- update
+// One lane's loads of two row pairs of the update's epilogue.
+struct EpiRegs {
+  float4 r[2], p[2];
+  float m[2], d[2];
+  int64_t at[2];
+  int v;  // bit u: row pair u is a row of the panel
+};
+
 // beta null: P = M^-1 R' + Yw C on every column (the first residuals).
 // planes null: PD = d o P in FP32, else its three BF16 pieces, piece p at
 // planes + p * plane_elems (row-major like PD).
@@ -492,83 +487,88 @@ __global__ void __launch_bounds__(256, 2) k_dtc_update(
       abort_flag = 1;
     }
   }
+  // warp w: accumulator rows 32 (w mod 4) .., columns 64 (w div 4) .., staged
+  // through shared memory (the operand images are no longer needed) so that
+  // the global accesses go row by row: 16 lanes x 16 bytes per row.  The
+  // lane's rows are taken two pairs at a time, the loads of the next two
+  // pairs in flight while one pair-batch is written; the first batch's loads
+  // go out before the wait for the MMAs.
+  const int quad = warp & 3, half = warp >> 2;
+  const int sub = lane >> 4, cq = lane & 15;
+  const int cl = 64 * half + 4 * cq;  // the lane's four columns in the tile
+  const bool live = c0 + cl < R;      // R is a multiple of 32
+  float* stg = reinterpret_cast<float*>(smem_raw) + warp * (32 * kU2Stg);
+  auto load = [&](int bt, EpiRegs& E) {
+    E.v = 0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int rl = 4 * bt + 2 * u + sub;
+      const int64_t i = r0 + 32 * quad + rl;
+      E.at[u] = i * R + c0 + cl;
+      E.r[u] = E.p[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      E.m[u] = E.d[u] = 0.f;
+      if (i < n) {
+        E.v |= 1 << u;
+        E.r[u] = __ldcs(reinterpret_cast<const float4*>(Rr + E.at[u]));
+        if (beta) E.p[u] = *reinterpret_cast<const float4*>(P + E.at[u]);
+        E.m[u] = minv[i];
+        E.d[u] = dv[i];
+      }
+    }
+  };
+  auto store = [&](int bt, const EpiRegs& E) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!(E.v >> u & 1)) continue;
+      const int rl = 4 * bt + 2 * u + sub;
+      const float4 zv = *reinterpret_cast<const float4*>(stg + rl * kU2Stg + 4 * cq);
+      const float z4[4] = {zv.x, zv.y, zv.z, zv.w};
+      const float r4[4] = {E.r[u].x, E.r[u].y, E.r[u].z, E.r[u].w};
+      float p4[4] = {E.p[u].x, E.p[u].y, E.p[u].z, E.p[u].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float pn = fmaf(sh_be[cl + e], p4[e], fmaf(E.m[u], r4[e], z4[e]));
+        p4[e] = sh_act[cl + e] ? pn : p4[e];
+      }
+      *reinterpret_cast<float4*>(P + E.at[u]) = make_float4(p4[0], p4[1], p4[2], p4[3]);
+      float dp[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dp[e] = E.d[u] * p4[e];
+      if (planes) {
+        uint2 q1, q2, q3;
+        tg::split3x4(dp, q1, q2, q3);
+        *reinterpret_cast<uint2*>(planes + E.at[u]) = q1;
+        *reinterpret_cast<uint2*>(planes + plane_elems + E.at[u]) = q2;
+        *reinterpret_cast<uint2*>(planes + 2 * plane_elems + E.at[u]) = q3;
+      } else {
+        *reinterpret_cast<float4*>(PD + E.at[u]) = make_float4(dp[0], dp[1], dp[2], dp[3]);
+      }
+    }
+  };
+  EpiRegs A, B;
+  if (live) load(0, A);
   bool ok = tg::wait(tg::smem(&done), 0u, abort_v);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    // warp w: accumulator rows 32 (w mod 4) .., columns 64 (w div 4) .., staged
-    // through shared memory (the operand images are no longer needed) so that
-    // the global accesses go row by row: 16 lanes x 16 bytes per row
-    const int quad = warp & 3, half = warp >> 2;
-    float* stg = reinterpret_cast<float*>(smem_raw) + warp * (32 * kU2Stg);
 #pragma unroll 1
     for (int ch = 0; ch < 4; ++ch) {
-      const int cl = 64 * half + 16 * ch;
-      if (c0 + cl >= R) break;  // uniform over the warp; R is a multiple of 32
+      const int cc = 64 * half + 16 * ch;
+      if (c0 + cc >= R) break;  // uniform over the warp
       uint32_t z[16];
-      tg::ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cl, z);
+      tg::ld16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cc, z);
 #pragma unroll
       for (int v4 = 0; v4 < 4; ++v4)
         *reinterpret_cast<uint4*>(stg + lane * kU2Stg + 16 * ch + 4 * v4) =
             make_uint4(z[4 * v4], z[4 * v4 + 1], z[4 * v4 + 2], z[4 * v4 + 3]);
     }
     __syncwarp();
-    const int sub = lane >> 4, cq = lane & 15;
-    const int cl = 64 * half + 4 * cq;  // the lane's four columns in the tile
-    if (c0 + cl < R) {
-      float be[4];
-      int act[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        be[e] = sh_be[cl + e];
-        act[e] = sh_act[cl + e];
-      }
-      // rows two at a time; four pairs per batch with all loads first
+    if (live) {
 #pragma unroll 1
-      for (int rb = 0; rb < 32; rb += 8) {
-        float4 zv[4], rv[4], pv[4];
-        float mv[4], dvv[4];
-        int64_t at[4];
-        bool vr[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int rl = rb + 2 * u + sub;
-          const int64_t i = r0 + 32 * quad + rl;
-          vr[u] = i < n;
-          at[u] = i * R + c0 + cl;
-          zv[u] = *reinterpret_cast<const float4*>(stg + rl * kU2Stg + 4 * cq);
-          if (vr[u]) {
-            rv[u] = __ldcs(reinterpret_cast<const float4*>(Rr + at[u]));
-            pv[u] = beta ? *reinterpret_cast<const float4*>(P + at[u])
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-            mv[u] = minv[i];
-            dvv[u] = dv[i];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (!vr[u]) continue;
-          const float z4[4] = {zv[u].x, zv[u].y, zv[u].z, zv[u].w};
-          const float r4[4] = {rv[u].x, rv[u].y, rv[u].z, rv[u].w};
-          float p4[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float pn = fmaf(be[e], p4[e], fmaf(mv[u], r4[e], z4[e]));
-            p4[e] = act[e] ? pn : p4[e];
-          }
-          *reinterpret_cast<float4*>(P + at[u]) = make_float4(p4[0], p4[1], p4[2], p4[3]);
-          float dp[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) dp[e] = dvv[u] * p4[e];
-          if (planes) {
-            uint2 q1, q2, q3;
-            tg::split3x4(dp, q1, q2, q3);
-            *reinterpret_cast<uint2*>(planes + at[u]) = q1;
-            *reinterpret_cast<uint2*>(planes + plane_elems + at[u]) = q2;
-            *reinterpret_cast<uint2*>(planes + 2 * plane_elems + at[u]) = q3;
-          } else {
-            *reinterpret_cast<float4*>(PD + at[u]) = make_float4(dp[0], dp[1], dp[2], dp[3]);
-          }
-        }
+      for (int bt = 0; bt < 8; bt += 2) {
+        load(bt + 1, B);
+        store(bt, A);
+        if (bt + 2 < 8) load(bt + 2, A);
+        store(bt + 1, B);
       }
     }
   } else if (t == 0) {
@@ -611,12 +611,10 @@ gm_status dtc_images(gm_ctx* c, int64_t n, const float* Y, const float* Yw, void
 static gm_status dtc_attributes(gm_ctx* c) {
   static bool done = false;
   if (done) return GM_OK;
-  for (auto k : {k_dtc_step<false>, k_dtc_step<true>}) {
-    GM_CUDA_CHECK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          kS1Smem));
-    GM_CUDA_CHECK(c, cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                          100));
-  }
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_dtc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kS1Smem));
+  GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_dtc_step,
+                                        cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   GM_CUDA_CHECK(c, cudaFuncSetAttribute(k_dtc_update,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kU2Smem));
   // all of the unified L1 / shared memory as shared: the CTAs per SM that the
@@ -627,17 +625,12 @@ static gm_status dtc_attributes(gm_ctx* c) {
   return GM_OK;
 }
 
-// Two K-steps of loads in flight per producer (GM_DTC_PIPE=1) or one (=0).
-static bool dtc_pipe() {
-  const char* e = std::getenv("GM_DTC_PIPE");
-  return e ? e[0] == '1' : false;
-}
 
 // Row chunks of the step kernel for a panel of R columns: one wave of CTAs
-// at three resident per SM (125 registers x 160 threads and 72 KB of shared
-// memory each; two with the pipelined loads), at most 64.
+// at three resident per SM (at most 136 registers x 160 threads and 72 KB of
+// shared memory each), at most 64.
 int dtc_chunks(gm_ctx* c, int64_t n, int R) {
-  const int kPerSm = dtc_pipe() ? 2 : 3;
+  constexpr int kPerSm = 3;
   const int64_t ncg = ceil_div(R, kS1Cols), nks = ceil_div(n, 16);
   int64_t nch = std::max<int64_t>(1, (int64_t)kPerSm * sm_count(c) / ncg);
   nch = std::min<int64_t>(std::min<int64_t>(nch, 64), std::max<int64_t>(nks, 1));
@@ -655,8 +648,7 @@ gm_status dtc_step(gm_ctx* c, int64_t n, int R, int nch, const void* yimg, const
   const int kpc = (int)ceil_div(std::max<int64_t>(nks, 1), nch);
   const int ncg = (int)ceil_div(R, kS1Cols);
   GM_PROF(c, "k_dtc_step");
-  auto kern = dtc_pipe() ? k_dtc_step<true> : k_dtc_step<false>;
-  kern<<<dim3((unsigned)ncg, (unsigned)nch), kS1Threads, kS1Smem, c->stream>>>(
+  k_dtc_step<<<dim3((unsigned)ncg, (unsigned)nch), kS1Threads, kS1Smem, c->stream>>>(
       n, R, kpc, (const unsigned char*)yimg, alpha, minv, X, Rr, P, Q, part_rz, part_rr, Cp,
       c->d_flags);
   GM_LAUNCH_CHECK(c);
