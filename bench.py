@@ -232,7 +232,7 @@ def run_reference(a):
 # DRAM bytes (read + write) of one launch of the asynchronous tile product on
 # the 20,000-star workload at panel 4,640, from one ncu capture of that launch
 # (dram__bytes_read.sum + dram__bytes_write.sum); other shapes were not captured
-TC_ASYNC_TRAFFIC = {(20000, 4640): 1.665e9 + 0.350e9}
+TC_ASYNC_TRAFFIC = {(20000, 4640): 1.651e9 + 0.349e9}
 
 
 def roofline_for(name, launches, ms, st, cfg_prec, panel, async_b=False):

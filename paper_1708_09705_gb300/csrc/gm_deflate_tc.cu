@@ -385,18 +385,16 @@ __global__ void k_dtc_sum(int R, int ncg, int nparts, const float* __restrict__ 
     const int j8 = (int)(e / cols);
     const int c = (int)(e - j8 * cols);
     float v[8];
-#pragma unroll
-    for (int jj = 0; jj < 8; ++jj) v[jj] = 0.f;
-    // the partial rows in order; the eight j of a row are independent loads
-    if (c < R)
-      for (int q = 0; q < nparts; ++q) {
-        const float* row = Cp + ((int64_t)q * kDk + 8 * j8) * R + c;
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) v[jj] += row[(int64_t)jj * R];
-      }
     double corr = 0.0;
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) corr += (double)w[8 * j8 + jj] * (double)v[jj] * (double)v[jj];
+    for (int jj = 0; jj < 8; ++jj) {
+      const int j = 8 * j8 + jj;
+      float s = 0.f;
+      if (c < R)
+        for (int q = 0; q < nparts; ++q) s += Cp[((int64_t)q * kDk + j) * R + c];
+      v[jj] = s;
+      corr += (double)w[j] * (double)s * (double)s;
+    }
     if (c < R) corr8[(int64_t)j8 * R + c] = corr;
     uint4 p1, p2, p3;
     tg::split3x8(v, p1, p2, p3);

@@ -72,9 +72,9 @@ def test_tensor_core_panel_product_matches_simt_and_fp64(gm, monkeypatch, probe)
 
 def test_tile_union_and_order(gm, monkeypatch):
     """The block unions built from per-block bitmaps equal those of the sort of
-    (block, column) keys (same K-steps, bit-identical posterior), and the
-    Morton order of the tile rows gives fewer K-steps than the cell order with
-    the same posterior to FP32 rounding."""
+    (block, column) keys (same K-steps, bit-identical posterior), and the k-d
+    order of the tile rows gives fewer K-steps than the cell order with the
+    same posterior to FP32 rounding."""
     cat = catalogue_subset(make_catalogue("c2_plain_20k", truth="mean"), np.arange(3000))
     out = {}
     for name, union, order in [("bitmap", None, None), ("sort", "sort", None),
@@ -94,7 +94,7 @@ def test_tile_union_and_order(gm, monkeypatch):
     assert out["bitmap"][2] == out["sort"][2] > 0
     np.testing.assert_array_equal(out["bitmap"][0], out["sort"][0])
     np.testing.assert_array_equal(out["bitmap"][1], out["sort"][1])
-    print("tile K-steps: Morton order %d, cell order %d" % (out["bitmap"][2], out["rows"][2]))
+    print("tile K-steps: k-d order %d, cell order %d" % (out["bitmap"][2], out["rows"][2]))
     assert out["bitmap"][2] < out["rows"][2]
     rel = np.abs(out["bitmap"][1] - out["rows"][1]) / out["rows"][1]
     assert rel.max() < 1e-3 and np.median(rel) < 1e-5
