@@ -1100,8 +1100,12 @@ static gm_status panels(gm_ctx* c, int64_t n_rows, const int64_t* row_ptr, const
     size_t free_b = 0, tot_b = 0;
     cudaMemGetInfo(&free_b, &tot_b);
     // five panel arrays (+ three BF16 planes of PD for the tensor-core
-    // product) within half the free memory, at most 160 GB
-    double budget = std::min<double>(0.5 * (double)free_b, 160e9);
+    // product) within half of the free memory plus what this context's panel
+    // arrays already hold (they are reused or replaced), at most 160 GB: the
+    // width then stays the same from one refresh to the next
+    const size_t held = ws.P_X.bytes + ws.P_R.bytes + ws.P_P.bytes + ws.P_PD.bytes +
+                        ws.P_Q.bytes + (sizeof(TV) == 4 ? c->tc_planes.bytes : 0);
+    double budget = std::min<double>(0.5 * ((double)free_b + (double)held), 160e9);
     const double per = 5.0 * sizeof(TV) + (sizeof(TV) == 4 && c->tc_nblk > 0 ? 6.0 : 0.0);
     R = (int64_t)(budget / (per * (double)n));
   }
